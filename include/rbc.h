@@ -1,0 +1,150 @@
+/*
+ * rbc.h - C ABI of the GB300 Parareal fine propagator for 2D Rayleigh-Benard
+ * convection (Clarke, Davies, Ruprecht, Tobias, Oishi: "Performance of
+ * parallel-in-time integration for Rayleigh Benard Convection").
+ *
+ * Problem (Sec. 2.1, Eqs. 3-6): Oberbeck-Boussinesq equations, Prandtl number
+ * Pr, Rayleigh number Ra, periodic x in [0, Lx), z in [-1/2, 1/2], no-slip walls
+ * with T(-1/2) = 1, T(1/2) = 0; time in thermal-diffusion units.
+ * Discretisation (Sec. 3.2): Fourier modes in x, Chebyshev polynomials in z,
+ * products in grid space (3/2-rule padded), linear terms implicit (ultraspherical
+ * tau), nonlinear terms explicit, IMEX RK443 (Sec. 3.6).  Parareal (Sec. 3.1,
+ * Eq. 20) with the defect and Nusselt stopping norms (Sec. 3.7, Eq. 9).
+ *
+ * Conventions
+ *  - Every call returns rbc_status; nothing throws across the ABI.
+ *  - Device buffers are owned by the caller (any allocator); the library reads
+ *    and writes them on the stream passed in.  Handles own their operator
+ *    tables and their workspace (device memory allocated at create/reserve).
+ *  - Host arrays are owned by the caller and are copied before return.
+ *  - A handle is not re-entrant: one stream at a time per handle.
+ *  - Invalid arguments return RBC_EINVAL and change nothing.
+ *
+ * Spectral state layout (one time slice, "state"), 16*Nx*Nz bytes, FP64:
+ *    double X[2][Nz][Nx/2][2]
+ *    X[f][n][m][c]: field f (0 = temperature T, 1 = streamfunction psi),
+ *    Chebyshev index n (T_n(2z)), Fourier index m (k = 2 pi m / Lx; the Nyquist
+ *    mode is not stored), c = 0 real / 1 imaginary part.  The field value is
+ *    f(x, z) = sum_{|m| < Nx/2} sum_n fhat_m,n T_n(2z) exp(i k x) (real field,
+ *    fhat_{-m} = conj(fhat_m)).  The m = 0 slot of psi holds instead the
+ *    Chebyshev coefficients of the mean horizontal velocity U(z) (real).
+ *    u = d psi / dz (+ U), w = -d psi / dx.
+ * Native grid (set/get_state): x_i = Lx i / Nx, z_j = -cos(pi j/(Nz-1))/2,
+ *    arrays double g[Nz][Nx] (z-major, z ascending).
+ */
+#ifndef RBC_H
+#define RBC_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbc_s* rbc_t;
+typedef struct pr_s* parareal_t;
+
+typedef enum {
+  RBC_OK = 0,
+  RBC_EINVAL = -1,      /* bad argument (sizes, null pointers, dt <= 0, ...)  */
+  RBC_ENOMEM = -2,      /* device or host allocation failed                    */
+  RBC_ECUDA = -3,       /* a CUDA runtime call failed (see rbc_last_error)     */
+  RBC_EDIVERGED = -4,   /* a NaN/Inf appeared in a state (Sec. 3.6 warns that
+                           Parareal can be unstable with stable F and G)       */
+  RBC_ETIMEOUT = -5,    /* reserved: a bounded device-side wait gave up       */
+  RBC_ENOTCONVERGED = 1 /* Parareal reached max_iters without meeting tol      */
+} rbc_status;
+
+enum { RBC_FP64 = 0, RBC_MIXED = 1 };         /* rbc_opts.precision */
+enum { RBC_FIXED_T = 0 };                    /* rbc_opts.bc (Eq. 6) */
+enum { RBC_CRIT_FIXED = 0, RBC_CRIT_DEFECT = 1, RBC_CRIT_NU = 2 };
+
+typedef struct {
+  int precision;   /* RBC_FP64: every step in FP64.  RBC_MIXED: transforms and
+                      products in FP32, solves, RK combination, Parareal update
+                      and norms in FP64.                                        */
+  int bc;          /* RBC_FIXED_T only                                          */
+} rbc_opts;
+
+/* Text of the last error seen by this thread (static storage, never NULL). */
+const char* rbc_last_error(void);
+
+/* rbc_create: build a propagator for (Ra, Pr, Lx, Nx, Nz, dt) (Sec. 2.1 Eqs.
+ * 3-6 parameters, Sec. 3.2 resolution (Nx, Nz), Sec. 3.4 time step).  Builds
+ * the operator tables on the host in FP64 and uploads them to the current
+ * device.  Requirements: Nx a power of two, 4 <= Nx <= 1024, Nz even, 8 <= Nz <= 512,
+ * dt > 0, Pr > 0, Lx > 0, Ra >= 0; opts may be NULL (FP64).               */
+rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz, double dt,
+                      const rbc_opts* opts, rbc_t* out);
+void rbc_destroy(rbc_t h);
+
+/* Bytes of one spectral state (16*Nx*Nz) and of the workspace per batched
+ * state, for admission control by device memory.                          */
+size_t rbc_state_bytes(rbc_t h);
+size_t rbc_workspace_bytes_per_state(rbc_t h);
+
+/* Grow the workspace to hold at least B states (rbc_step_batch grows it on
+ * demand; call this first to keep allocation out of timed regions).        */
+rbc_status rbc_reserve(rbc_t h, int B);
+
+/* Native grid <-> spectral state.  h_T, h_u, h_w: host double[Nz][Nx]
+ * (h_u, h_w may be NULL = zero).  psi is recovered from w (psi_m = i w_m / k,
+ * m >= 1), U from the x-mean of u; the Nyquist column is dropped.  d_state is
+ * a device state buffer.  Synchronous.                                     */
+rbc_status rbc_set_state(rbc_t h, void* d_state, const double* h_T, const double* h_u,
+                         const double* h_w);
+rbc_status rbc_get_state(rbc_t h, const void* d_state, double* h_T, double* h_u, double* h_w);
+
+/* rbc_step_batch: the fine (or coarse) propagator F of Eq. 20 applied to B
+ * independent states at once (Sec. 3.1: the fine solves of all time slices
+ * run in parallel).  d_states: B contiguous device states, advanced in place
+ * by h_nsteps[b] RK443 steps each (host int[B], each >= 0; 0 leaves a state
+ * untouched; uneven counts are allowed).  d_nu_integral (device double[B],
+ * may be NULL) is overwritten with the trapezoid-rule integral over the run
+ * of Nu_V(t) (Eq. 9) for each state.  Asynchronous on `stream` (the step
+ * counts are copied before return); a NaN/Inf in a state is recorded in a
+ * device flag and reported by rbc_check_diverged.                          */
+rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps,
+                          double* d_nu_integral, cudaStream_t stream);
+
+/* Synchronises `stream`; RBC_EDIVERGED if any state of the batch went
+ * non-finite since the last rbc_step_batch, else RBC_OK.                   */
+rbc_status rbc_check_diverged(rbc_t h, cudaStream_t stream);
+
+/* rbc_nusselt: Nu_V (Eq. 9), Nu_b and Nu_t (Eqs. 10, 11) of one device state,
+ * written to host out[3].  Synchronous on `stream`.                         */
+rbc_status rbc_nusselt(rbc_t h, const void* d_state, double out[3], cudaStream_t stream);
+
+/* ||T||_{L2(Omega)} of one device state (exact in x and z), host out.       */
+rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream);
+
+/* Parareal (Sec. 3.1, Eq. 20).  fine and coarse share Ra, Pr, Lx; the coarse
+ * grid is no finer than the fine one.  [t0, t1] is cut into nslices equal
+ * slices; each slice must be a whole number of fine and of coarse steps
+ * (relative 1e-9), else RBC_EINVAL.  G = prolong o coarse o restrict, with
+ * restriction = truncation of the coefficient arrays and prolongation =
+ * zero padding.  criterion: RBC_CRIT_FIXED (max_iters iterations, the
+ * paper's practice, Sec. 3.7), RBC_CRIT_DEFECT (stop when
+ * max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k|| <= tol, L2 norm of T), RBC_CRIT_NU
+ * (stop when |Nu_k - Nu_{k-1}| / |Nu_k| <= tol, Nu_k = time average of Nu_V
+ * over the second half of the slices along the fine trajectories from U^k).
+ * The handles must outlive the Parareal handle.                            */
+rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, double t1, int nslices,
+                           int criterion, double tol, parareal_t* out);
+void parareal_destroy(parareal_t p);
+
+/* Run up to max_iters Parareal iterations from the device state d_U0.
+ * d_U: caller-owned device buffer of nslices+1 states; on return d_U[n] =
+ * U_n^k (d_U[0] = U0).  Host outputs: *k_done iterations performed,
+ * defects[k-1] = Defect_k, nus[k-1] = Nu_{k-1} (arrays of max_iters doubles,
+ * either may be NULL).  Returns RBC_OK when the criterion was met (always for
+ * RBC_CRIT_FIXED), RBC_ENOTCONVERGED when max_iters ran out, RBC_EDIVERGED on
+ * a non-finite state.  Synchronous on `stream` (one small D2H per iteration). */
+rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_iters,
+                            int* k_done, double* defects, double* nus, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBC_H */

@@ -1,0 +1,792 @@
+// Host runtime of the RBC Parareal library: operator assembly and UL
+// factorisation (FP64, once per grid and time step), workspace management,
+// the RK443 step loop, and the Parareal control flow (Eq. 20).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rbc_internal.h"
+
+using namespace rbc;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+rbc_status fail(rbc_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return fail(RBC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Dense N x N operators on Chebyshev-T coefficients (row-major).
+// Ultraspherical method (Olver & Townsend): conversions T -> C^(1) -> C^(2) ...
+// and derivatives T -> C^(lambda).
+// ---------------------------------------------------------------------------
+using Mat = std::vector<double>;
+
+Mat eye_like(int N) { return Mat((size_t)N * N, 0.0); }
+
+// T_n = (C1_n - C1_{n-2}) / 2 (n >= 2), T_1 = C1_1 / 2, T_0 = C1_0.
+Mat conv_T_C1(int N) {
+  Mat S = eye_like(N);
+  S[0] = 1.0;
+  for (int j = 1; j < N; ++j) S[(size_t)j * N + j] = 0.5;
+  for (int j = 0; j + 2 < N; ++j) S[(size_t)j * N + j + 2] = -0.5;
+  return S;
+}
+
+// C^(l)_n = l/(n+l) (C^(l+1)_n - C^(l+1)_{n-2}).
+Mat conv_C(int l, int N) {
+  Mat S = eye_like(N);
+  for (int j = 0; j < N; ++j) {
+    S[(size_t)j * N + j] = (double)l / (j + l);
+    if (j + 2 < N) S[(size_t)j * N + j + 2] = -(double)l / (j + l + 2);
+  }
+  return S;
+}
+
+// d^l T_n / ds^l = 2^(l-1) (l-1)! n C^(l)_{n-l}.
+Mat deriv(int l, int N) {
+  Mat D = eye_like(N);
+  double c = std::ldexp(1.0, l - 1);
+  for (int i = 2; i < l; ++i) c *= i;
+  for (int j = 0; j + l < N; ++j) D[(size_t)j * N + j + l] = c * (j + l);
+  return D;
+}
+
+Mat matmul(const Mat& A, const Mat& B, int N) {
+  Mat C = eye_like(N);
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < N; ++k) {
+      const double a = A[(size_t)i * N + k];
+      if (a == 0.0) continue;
+      for (int j = 0; j < N; ++j) C[(size_t)i * N + j] += a * B[(size_t)k * N + j];
+    }
+  return C;
+}
+
+// Values and derivatives (orders 0..Q) of T_0..T_{N-1} at s, by the
+// three-term recurrence T_{n+1} = 2 s T_n - T_{n-1} differentiated q times:
+// T^(q)_{n+1} = 2 s T^(q)_n + 2 q T^(q-1)_n - T^(q)_{n-1}.
+void cheb_eval(double s, int N, int Q, std::vector<double>& out) {
+  out.assign((size_t)(Q + 1) * N, 0.0);
+  auto at = [&](int q, int n) -> double& { return out[(size_t)q * N + n]; };
+  at(0, 0) = 1.0;
+  if (N > 1) {
+    at(0, 1) = s;
+    if (Q >= 1) at(1, 1) = 1.0;
+  }
+  for (int n = 1; n + 1 < N; ++n)
+    for (int q = 0; q <= Q; ++q)
+      at(q, n + 1) = 2.0 * s * at(q, n) + (q > 0 ? 2.0 * q * at(q - 1, n) : 0.0) - at(q, n - 1);
+}
+
+// Exact interpolation on N Chebyshev-Lobatto points with angles theta_j:
+// W[n][j] = 2/(N-1) * T_n(s_j) / (c_n c_j), c = 2 at the end points/indices.
+Mat lobatto_interp(int N, const std::vector<double>& theta) {
+  Mat W = eye_like(N);
+  for (int n = 0; n < N; ++n)
+    for (int j = 0; j < N; ++j) {
+      const double cn = (n == 0 || n == N - 1) ? 2.0 : 1.0;
+      const double cj = (j == 0 || j == N - 1) ? 2.0 : 1.0;
+      W[(size_t)n * N + j] = 2.0 / (N - 1) * std::cos(n * theta[j]) / (cn * cj);
+    }
+  return W;
+}
+
+// ---------------------------------------------------------------------------
+// UL factorisation of a parity-split stage matrix: D dense boundary rows on
+// top, then tau rows whose nonzeros lie in columns r-D .. r+D (dominant
+// derivative term on the diagonal).  Eliminating columns n-1 .. D from the
+// bottom creates no fill; what remains is a D x D dense block and a lower
+// band.  No pivoting; the residual is checked after factoring.
+// ---------------------------------------------------------------------------
+struct UL {
+  int n = 0, D = 0;
+  std::vector<double> multB, multD, Dinv, Lb, invd;  // [c][D], [c][D], [D*D], [r][D], [r]
+};
+
+bool ul_factor(Mat A, int n, int D, UL& f, std::string& why) {
+  f.n = n;
+  f.D = D;
+  f.multB.assign((size_t)n * D, 0.0);
+  f.multD.assign((size_t)n * D, 0.0);
+  f.Lb.assign((size_t)n * D, 0.0);
+  f.invd.assign(n, 0.0);
+  f.Dinv.assign(D * D, 0.0);
+  auto a = [&](int r, int c) -> double& { return A[(size_t)r * n + c]; };
+  for (int c = n - 1; c >= D; --c) {
+    const double piv = a(c, c);
+    if (piv == 0.0 || !std::isfinite(piv)) {
+      why = "zero pivot";
+      return false;
+    }
+    for (int r = 0; r < c; ++r) {
+      const double v = a(r, c);
+      if (v == 0.0) continue;
+      if (r >= D && r < c - D) {
+        why = "band structure violated";
+        return false;
+      }
+      const double mult = v / piv;
+      for (int q = std::max(0, c - D); q < c; ++q) a(r, q) -= mult * a(c, q);
+      a(r, c) = 0.0;
+      if (r < D)
+        f.multD[(size_t)c * D + r] = mult;
+      else
+        f.multB[(size_t)c * D + (r - (c - D))] = mult;
+    }
+  }
+  for (int r = D; r < n; ++r) {
+    for (int q = 0; q < r - D; ++q)
+      if (a(r, q) != 0.0) {
+        why = "lower band structure violated";
+        return false;
+      }
+    for (int j = 0; j < D; ++j) f.Lb[(size_t)r * D + j] = a(r, r - D + j);
+    f.invd[r] = 1.0 / a(r, r);
+  }
+  if (D == 1) {
+    f.Dinv[0] = 1.0 / a(0, 0);
+  } else {
+    const double det = a(0, 0) * a(1, 1) - a(0, 1) * a(1, 0);
+    if (det == 0.0) {
+      why = "singular boundary block";
+      return false;
+    }
+    f.Dinv[0] = a(1, 1) / det;
+    f.Dinv[1] = -a(0, 1) / det;
+    f.Dinv[2] = -a(1, 0) / det;
+    f.Dinv[3] = a(0, 0) / det;
+  }
+  return true;
+}
+
+// Host mirror of the device solve, for the residual check.
+void ul_solve(const UL& f, std::vector<double>& y, std::vector<double>& x) {
+  const int n = f.n, D = f.D;
+  for (int c = n - 1; c >= D; --c) {
+    for (int j = 0; j < D; ++j) {
+      const int r = c - D + j;
+      if (r >= D) y[r] -= f.multB[(size_t)c * D + j] * y[c];
+    }
+    for (int r = 0; r < D; ++r) y[r] -= f.multD[(size_t)c * D + r] * y[c];
+  }
+  x.assign(n, 0.0);
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) x[r] += f.Dinv[r * D + c] * y[c];
+  for (int r = D; r < n; ++r) {
+    double s = y[r];
+    for (int j = 0; j < D; ++j) s -= f.Lb[(size_t)r * D + j] * x[r - D + j];
+    x[r] = s * f.invd[r];
+  }
+}
+
+double ul_residual(const Mat& A, const UL& f, unsigned seed) {
+  const int n = f.n;
+  std::vector<double> b(n), y, x;
+  unsigned s = seed * 2654435761u + 12345u;
+  for (int i = 0; i < n; ++i) {
+    s = s * 1664525u + 1013904223u;
+    b[i] = (double)(s >> 8) / (double)(1u << 24) - 0.5;
+  }
+  y = b;
+  ul_solve(f, y, x);
+  double rmax = 0.0, amax = 0.0, xmax = 0.0, bmax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = -b[i], arow = 0.0;
+    for (int j = 0; j < n; ++j) {
+      r += A[(size_t)i * n + j] * x[j];
+      arow += std::fabs(A[(size_t)i * n + j]);
+    }
+    rmax = std::max(rmax, std::fabs(r));
+    amax = std::max(amax, arow);
+    xmax = std::max(xmax, std::fabs(x[i]));
+    bmax = std::max(bmax, std::fabs(b[i]));
+  }
+  return rmax / (amax * xmax + bmax);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Handle.
+// ---------------------------------------------------------------------------
+struct rbc_s {
+  Grid g{};
+  rbc_opts opts{};
+  int device = 0;
+  double max_residual = 0.0;
+  double* d_tables = nullptr;
+  Tables t{};
+  int cap = 0;
+  void* d_work = nullptr;
+  Work w{};
+  double* d_scratch = nullptr;   // set/get state and diagnostics, independent of B
+  int last_B = 0;
+};
+
+struct pr_s {
+  rbc_t fine = nullptr, coarse = nullptr;
+  double t0 = 0, t1 = 0;
+  int N = 0, nf = 0, nc = 0, criterion = 0;
+  double tol = 0;
+  double* d_F = nullptr;      // N fine states: F(U_n^k)
+  double* d_Uold = nullptr;   // N+1 fine states: previous iterate
+  double* d_Gold = nullptr;   // N coarse states: G_coarse(restrict(U_n^k))
+  double* d_C = nullptr;      // 1 coarse state
+  double* d_I = nullptr;      // N doubles: Nu_V integrals of the F sweep
+  double* d_norm = nullptr;   // 2N doubles
+};
+
+extern "C" const char* rbc_last_error(void) { return g_err; }
+
+static rbc_status upload_tables(rbc_t h) {
+  const Grid& g = h->g;
+  const int N = g.Nz, Mz = g.Mz, nq = g.nq, nm = g.nm;
+  std::vector<double> buf;
+  std::vector<size_t> offs;
+  auto add = [&](const std::vector<double>& v) {
+    size_t o = buf.size();
+    o = (o + 1) & ~(size_t)1;   // 16-byte alignment for double2 loads
+    buf.resize(o);
+    buf.insert(buf.end(), v.begin(), v.end());
+    offs.push_back(o);
+  };
+
+  // ---- z transforms at the padded Lobatto points s_j = cos(pi j/(Mz-1)) ----
+  std::vector<double> zinv((size_t)4 * Mz * N), ev;
+  std::vector<double> thp(Mz);
+  for (int j = 0; j < Mz; ++j) thp[j] = M_PI * j / (Mz - 1);
+  for (int j = 0; j < Mz; ++j) {
+    cheb_eval(std::cos(thp[j]), N, 3, ev);
+    for (int q = 0; q < 4; ++q)
+      for (int n = 0; n < N; ++n) zinv[((size_t)q * Mz + j) * N + n] = ev[(size_t)q * N + n];
+  }
+  Mat Wfull = lobatto_interp(Mz, thp);
+  std::vector<double> zfwd((size_t)N * Mz), cc(Mz, 0.0);
+  for (int n = 0; n < N; ++n)
+    for (int j = 0; j < Mz; ++j) zfwd[(size_t)n * Mz + j] = Wfull[(size_t)n * Mz + j];
+  for (int j = 0; j < Mz; ++j)
+    for (int n = 0; n < Mz; n += 2) cc[j] += Wfull[(size_t)n * Mz + j] * 2.0 / (1.0 - (double)n * n);
+  std::vector<double> tw((size_t)2 * g.Mx);
+  for (int t = 0; t < g.Mx; ++t) {
+    tw[2 * t] = std::cos(2.0 * M_PI * t / g.Mx);
+    tw[2 * t + 1] = -std::sin(2.0 * M_PI * t / g.Mx);
+  }
+
+  // ---- ultraspherical operators ----
+  const Mat S0 = conv_T_C1(N);
+  const Mat S2 = matmul(conv_C(1, N), S0, N);
+  const Mat C32 = matmul(conv_C(3, N), conv_C(2, N), N);
+  const Mat S4 = matmul(C32, S2, N);
+  const Mat D2 = deriv(2, N);
+  const Mat S4D2 = matmul(C32, D2, N);
+  const Mat D4 = deriv(4, N);
+  auto el = [&](const Mat& M, int r, int c) -> double { return (c < N) ? M[(size_t)r * N + c] : 0.0; };
+  // structural check: row j couples only columns j, j+2, ..., j+2*lam
+  auto check_band = [&](const Mat& M, int rows, int lam) -> bool {
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < N; ++c) {
+        const double v = M[(size_t)r * N + c];
+        if (v != 0.0 && (c < r || c > r + 2 * lam || ((c - r) & 1))) return false;
+      }
+    return true;
+  };
+  if (!check_band(S2, N - 2, 2) || !check_band(D2, N - 2, 2) || !check_band(S4, N - 4, 4) ||
+      !check_band(S4D2, N - 4, 4) || !check_band(D4, N - 4, 4))
+    return fail(RBC_EINVAL, "operator band structure check failed");
+
+  std::vector<double> s2((size_t)2 * nq * 3, 0.0), s4((size_t)2 * nq * 5, 0.0), mp((size_t)2 * nq * 5 * nm, 0.0);
+  for (int p = 0; p < 2; ++p)
+    for (int t = 0; t < nq; ++t) {
+      const int r = 2 * t + p;
+      for (int j = 0; j < 3; ++j)
+        if (r < N - 2) s2[(p * nq + t) * 3 + j] = el(S2, r, 2 * (t + j) + p);
+      for (int j = 0; j < 5; ++j)
+        if (r < N - 4) s4[(p * nq + t) * 5 + j] = el(S4, r, 2 * (t + j) + p);
+      for (int m = 0; m < nm; ++m) {
+        const double k = g.kfac * m;
+        for (int j = 0; j < 5; ++j)
+          if (r < N - 4) {
+            const int c = 2 * (t + j) + p;
+            mp[((size_t)(p * nq + t) * 5 + j) * nm + m] = 4.0 * el(S4D2, r, c) - k * k * el(S4, r, c);
+          }
+      }
+    }
+
+  // ---- stage matrices and their UL factors ----
+  const double hdt = 0.5 * g.dt;
+  auto layout = [&](std::vector<double>& dst, const std::vector<double>& src, int p, int rows, int D, int nmod,
+                    int mi) {
+    for (int c = 0; c < rows; ++c)
+      for (int j = 0; j < D; ++j) dst[((size_t)(p * rows + c) * D + j) * nmod + mi] = src[(size_t)c * D + j];
+  };
+  std::vector<double> Tb((size_t)2 * nq * nm), Td(Tb.size()), TDi((size_t)2 * nm), TL(Tb.size()), Ti(Tb.size());
+  std::vector<double> Pb((size_t)2 * nq * 2 * nm), Pd(Pb.size()), PDi((size_t)2 * 4 * nm), PL(Pb.size()),
+      Pi((size_t)2 * nq * nm);
+  std::vector<double> Ub((size_t)2 * nq), Ud(Ub.size()), UDi(2), UL_(Ub.size()), Ui(Ub.size());
+  double worst = 0.0;
+  std::string why;
+  for (int p = 0; p < 2; ++p) {
+    for (int m = 0; m < nm; ++m) {
+      const double k = g.kfac * m;
+      // temperature: BC row (all ones), tau rows of S2 - h (4 D2 - k^2 S2)
+      Mat A((size_t)nq * nq, 0.0);
+      for (int q = 0; q < nq; ++q) A[q] = 1.0;
+      for (int t = 0; t + 1 < nq; ++t)
+        for (int q = 0; q < nq; ++q) {
+          const int r = 2 * t + p, c = 2 * q + p;
+          A[(size_t)(1 + t) * nq + q] = el(S2, r, c) - hdt * (4.0 * el(D2, r, c) - k * k * el(S2, r, c));
+        }
+      UL f;
+      if (!ul_factor(A, nq, 1, f, why)) return fail(RBC_EINVAL, "T system m=%d p=%d: %s", m, p, why.c_str());
+      worst = std::max(worst, ul_residual(A, f, 17 * m + p));
+      layout(Tb, f.multB, p, nq, 1, nm, m);
+      layout(Td, f.multD, p, nq, 1, nm, m);
+      layout(TL, f.Lb, p, nq, 1, nm, m);
+      for (int r = 0; r < nq; ++r) Ti[(size_t)(p * nq + r) * nm + m] = f.invd[r];
+      TDi[(size_t)p * nm + m] = f.Dinv[0];
+      if (m == 0) {
+        // mean flow: S2 - h 4 Pr D2
+        Mat U((size_t)nq * nq, 0.0);
+        for (int q = 0; q < nq; ++q) U[q] = 1.0;
+        for (int t = 0; t + 1 < nq; ++t)
+          for (int q = 0; q < nq; ++q) {
+            const int r = 2 * t + p, c = 2 * q + p;
+            U[(size_t)(1 + t) * nq + q] = el(S2, r, c) - hdt * 4.0 * g.Pr * el(D2, r, c);
+          }
+        UL fu;
+        if (!ul_factor(U, nq, 1, fu, why)) return fail(RBC_EINVAL, "U system p=%d: %s", p, why.c_str());
+        worst = std::max(worst, ul_residual(U, fu, 99 + p));
+        layout(Ub, fu.multB, p, nq, 1, 1, 0);
+        layout(Ud, fu.multD, p, nq, 1, 1, 0);
+        layout(UL_, fu.Lb, p, nq, 1, 1, 0);
+        for (int r = 0; r < nq; ++r) Ui[(size_t)p * nq + r] = fu.invd[r];
+        UDi[p] = fu.Dinv[0];
+      } else {
+        // streamfunction: BC rows (ones, n^2), tau rows of M - h L in C^(4)
+        Mat P((size_t)nq * nq, 0.0);
+        for (int q = 0; q < nq; ++q) {
+          const double n = 2 * q + p;
+          P[q] = 1.0;
+          P[(size_t)nq + q] = n * n;
+        }
+        for (int t = 0; t + 2 < nq; ++t)
+          for (int q = 0; q < nq; ++q) {
+            const int r = 2 * t + p, c = 2 * q + p;
+            const double M = 4.0 * el(S4D2, r, c) - k * k * el(S4, r, c);
+            const double L =
+                g.Pr * (16.0 * el(D4, r, c) - 8.0 * k * k * el(S4D2, r, c) + k * k * k * k * el(S4, r, c));
+            P[(size_t)(2 + t) * nq + q] = M - hdt * L;
+          }
+        UL fp;
+        if (!ul_factor(P, nq, 2, fp, why)) return fail(RBC_EINVAL, "psi system m=%d p=%d: %s", m, p, why.c_str());
+        worst = std::max(worst, ul_residual(P, fp, 31 * m + p));
+        layout(Pb, fp.multB, p, nq, 2, nm, m);
+        layout(Pd, fp.multD, p, nq, 2, nm, m);
+        layout(PL, fp.Lb, p, nq, 2, nm, m);
+        for (int r = 0; r < nq; ++r) Pi[(size_t)(p * nq + r) * nm + m] = fp.invd[r];
+        for (int e = 0; e < 4; ++e) PDi[((size_t)p * 4 + e) * nm + m] = fp.Dinv[e];
+      }
+    }
+  }
+  h->max_residual = worst;
+  if (!(worst < 1e-9)) return fail(RBC_EINVAL, "stage solve residual %.3e too large (unpivoted UL)", worst);
+
+  // ---- norms and native grid transforms ----
+  std::vector<double> gram((size_t)N * N, 0.0);
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b)
+      if (((a + b) & 1) == 0)
+        gram[(size_t)a * N + b] = 1.0 / (1.0 - (double)(a + b) * (a + b)) + 1.0 / (1.0 - (double)(a - b) * (a - b));
+  std::vector<double> twn((size_t)2 * g.Nx);
+  for (int t = 0; t < g.Nx; ++t) {
+    twn[2 * t] = std::cos(2.0 * M_PI * t / g.Nx);
+    twn[2 * t + 1] = -std::sin(2.0 * M_PI * t / g.Nx);
+  }
+  std::vector<double> thn(N);  // native s_j = -cos(pi j/(N-1)) = cos(pi (N-1-j)/(N-1))
+  for (int j = 0; j < N; ++j) thn[j] = M_PI * (N - 1 - j) / (N - 1);
+  std::vector<double> Vn((size_t)N * N), Vn1((size_t)N * N);
+  for (int j = 0; j < N; ++j) {
+    cheb_eval(std::cos(thn[j]), N, 1, ev);
+    for (int n = 0; n < N; ++n) {
+      Vn[(size_t)j * N + n] = ev[n];
+      Vn1[(size_t)j * N + n] = ev[(size_t)N + n];
+    }
+  }
+  Mat Wn = lobatto_interp(N, thn);
+
+  add(zinv); add(zfwd); add(cc); add(tw); add(s2); add(s4); add(mp);
+  add(Tb); add(Td); add(TDi); add(TL); add(Ti);
+  add(Pb); add(Pd); add(PDi); add(PL); add(Pi);
+  add(Ub); add(Ud); add(UDi); add(UL_); add(Ui);
+  add(gram); add(twn); add(Vn); add(Vn1); add(Wn);
+  CK(cudaMalloc(&h->d_tables, buf.size() * sizeof(double)));
+  CK(cudaMemcpy(h->d_tables, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
+  const double* b = h->d_tables;
+  int i = 0;
+  Tables& T = h->t;
+  T.zinv = b + offs[i++];
+  T.zfwd = b + offs[i++];
+  T.cc = b + offs[i++];
+  T.tw = reinterpret_cast<const double2*>(b + offs[i++]);
+  T.s2 = b + offs[i++];
+  T.s4 = b + offs[i++];
+  T.mp = b + offs[i++];
+  T.T_multB = b + offs[i++]; T.T_multD = b + offs[i++]; T.T_Dinv = b + offs[i++]; T.T_Lb = b + offs[i++]; T.T_invd = b + offs[i++];
+  T.P_multB = b + offs[i++]; T.P_multD = b + offs[i++]; T.P_Dinv = b + offs[i++]; T.P_Lb = b + offs[i++]; T.P_invd = b + offs[i++];
+  T.U_multB = b + offs[i++]; T.U_multD = b + offs[i++]; T.U_Dinv = b + offs[i++]; T.U_Lb = b + offs[i++]; T.U_invd = b + offs[i++];
+  T.gram = b + offs[i++];
+  T.twn = reinterpret_cast<const double2*>(b + offs[i++]);
+  T.Vn = b + offs[i++];
+  T.Vn1 = b + offs[i++];
+  T.Wn = b + offs[i++];
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz, double dt, const rbc_opts* opts,
+                                 rbc_t* out) {
+  if (!out) return fail(RBC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (Nx < 4 || Nx > 1024 || (Nx & 1) || Nz < 8 || Nz > 512 || (Nz & 1))
+    return fail(RBC_EINVAL, "need even Nx in [4, 1024] and even Nz in [8, 512]");
+  if (!(dt > 0) || !(Pr > 0) || !(Lx > 0) || !(Ra >= 0) || !std::isfinite(Ra) || !std::isfinite(dt))
+    return fail(RBC_EINVAL, "need dt > 0, Pr > 0, Lx > 0, Ra >= 0");
+  rbc_opts o{RBC_FP64, RBC_FIXED_T};
+  if (opts) o = *opts;
+  if (o.precision != RBC_FP64) return fail(RBC_EINVAL, "precision mode %d not available", o.precision);
+  if (o.bc != RBC_FIXED_T) return fail(RBC_EINVAL, "boundary condition %d not available", o.bc);
+  // padded x length 3 Nx / 2 must be 3 * 2^p for the FFT
+  int Mx = 3 * Nx / 2, r = Mx / 3;
+  if (Mx % 3 || (r & (r - 1))) return fail(RBC_EINVAL, "Nx must be a power of two (3/2-padded FFT length 3*2^p)");
+  rbc_t h = new (std::nothrow) rbc_s();
+  if (!h) return fail(RBC_ENOMEM, "host allocation");
+  h->opts = o;
+  cudaGetDevice(&h->device);
+  Grid& g = h->g;
+  g.Nx = Nx;
+  g.Nz = Nz;
+  g.nm = Nx / 2;
+  g.Mx = Mx;
+  g.Mz = 3 * Nz / 2;
+  g.nq = Nz / 2;
+  g.Ra = Ra;
+  g.Pr = Pr;
+  g.Lx = Lx;
+  g.dt = dt;
+  g.kfac = 2.0 * M_PI / Lx;
+  rbc_status s = upload_tables(h);
+  if (s == RBC_OK) {
+    cudaError_t e = configure_kernels(g);
+    if (e != cudaSuccess) s = fail(RBC_ECUDA, "configure: %s", cudaGetErrorString(e));
+  }
+  if (s == RBC_OK) {
+    const size_t scratch = (size_t)3 * Nz * Nx + (size_t)3 * Nz * g.nm * 2 + 64;
+    if (cudaMalloc(&h->d_scratch, scratch * sizeof(double)) != cudaSuccess) s = fail(RBC_ENOMEM, "scratch");
+  }
+  if (s != RBC_OK) {
+    rbc_destroy(h);
+    return s;
+  }
+  *out = h;
+  return RBC_OK;
+}
+
+extern "C" void rbc_destroy(rbc_t h) {
+  if (!h) return;
+  cudaFree(h->d_tables);
+  cudaFree(h->d_work);
+  cudaFree(h->d_scratch);
+  delete h;
+}
+
+extern "C" size_t rbc_state_bytes(rbc_t h) { return h ? state_doubles(h->g) * sizeof(double) : 0; }
+
+static size_t work_doubles_per_state(const Grid& g) {
+  const size_t S = state_doubles(g);
+  return 6 * S + z_doubles(g) + q_doubles(g) + g.Mz + 4;   // Xs, F, R[4], Z, Q, wT, ints + nu
+}
+
+extern "C" size_t rbc_workspace_bytes_per_state(rbc_t h) {
+  return h ? work_doubles_per_state(h->g) * sizeof(double) : 0;
+}
+
+extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
+  if (!h || B < 0) return fail(RBC_EINVAL, "bad handle or B");
+  if (B <= h->cap) return RBC_OK;
+  const Grid& g = h->g;
+  const size_t S = state_doubles(g);
+  const size_t tot = (size_t)B * work_doubles_per_state(g) + 64;
+  void* p = nullptr;
+  if (cudaMalloc(&p, tot * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RBC_ENOMEM, "workspace for %d states (%zu bytes)", B, tot * sizeof(double));
+  }
+  cudaFree(h->d_work);
+  h->d_work = p;
+  h->cap = B;
+  double* d = static_cast<double*>(p);
+  Work& w = h->w;
+  w.Xs = d; d += (size_t)B * S;
+  w.F = d; d += (size_t)B * S;
+  w.R = d; d += (size_t)B * 4 * S;
+  w.Z = d; d += (size_t)B * z_doubles(g);
+  w.Q = d; d += (size_t)B * q_doubles(g);
+  w.wT = d; d += (size_t)B * g.Mz;
+  w.nu = d; d += B;
+  w.small = d; d += 16;
+  int* ip = reinterpret_cast<int*>(d);
+  w.nsteps = ip; ip += B;
+  w.flags = ip; ip += B;
+  w.step = ip;
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_set_state(rbc_t h, void* d_state, const double* h_T, const double* h_u, const double* h_w) {
+  if (!h || !d_state || !h_T) return fail(RBC_EINVAL, "null argument");
+  const Grid& g = h->g;
+  const size_t n = (size_t)g.Nz * g.Nx;
+  double* gd = h->d_scratch;
+  double* modes = gd + 3 * n;
+  CK(cudaMemcpy(gd, h_T, n * sizeof(double), cudaMemcpyHostToDevice));
+  if (h_u) CK(cudaMemcpy(gd + n, h_u, n * sizeof(double), cudaMemcpyHostToDevice));
+  else CK(cudaMemset(gd + n, 0, n * sizeof(double)));
+  if (h_w) CK(cudaMemcpy(gd + 2 * n, h_w, n * sizeof(double), cudaMemcpyHostToDevice));
+  else CK(cudaMemset(gd + 2 * n, 0, n * sizeof(double)));
+  CK(launch_set_state(g, h->t, gd, gd + n, gd + 2 * n, modes, static_cast<double*>(d_state), 0));
+  CK(cudaStreamSynchronize(0));
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_get_state(rbc_t h, const void* d_state, double* h_T, double* h_u, double* h_w) {
+  if (!h || !d_state) return fail(RBC_EINVAL, "null argument");
+  const Grid& g = h->g;
+  const size_t n = (size_t)g.Nz * g.Nx;
+  double* gd = h->d_scratch;
+  double* modes = gd + 3 * n;
+  CK(launch_get_state(g, h->t, static_cast<const double*>(d_state), modes, gd, gd + n, gd + 2 * n, 0));
+  CK(cudaStreamSynchronize(0));
+  if (h_T) CK(cudaMemcpy(h_T, gd, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (h_u) CK(cudaMemcpy(h_u, gd + n, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (h_w) CK(cudaMemcpy(h_w, gd + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps, double* d_nu_integral,
+                                     cudaStream_t stream) {
+  if (!h || B < 0 || (B > 0 && (!d_states || !h_nsteps))) return fail(RBC_EINVAL, "null argument or B < 0");
+  if (B == 0) return RBC_OK;
+  int maxs = 0;
+  for (int b = 0; b < B; ++b) {
+    if (h_nsteps[b] < 0) return fail(RBC_EINVAL, "negative step count");
+    maxs = std::max(maxs, h_nsteps[b]);
+  }
+  rbc_status s = rbc_reserve(h, B);
+  if (s != RBC_OK) return s;
+  const Work& w = h->w;
+  double* X = static_cast<double*>(d_states);
+  double* nu = d_nu_integral ? d_nu_integral : w.nu;
+  CK(cudaMemcpyAsync(w.nsteps, h_nsteps, (size_t)B * sizeof(int), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(w.step, 0, sizeof(int), stream));
+  CK(cudaMemsetAsync(w.flags, 0, (size_t)B * sizeof(int), stream));
+  CK(cudaMemsetAsync(nu, 0, (size_t)B * sizeof(double), stream));
+  h->last_B = B;
+  for (int st = 0; st < maxs; ++st) {
+    for (int stage = 1; stage <= 4; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
+    CK(launch_advance(w, stream));
+  }
+  if (maxs > 0) CK(launch_nu_final(h->g, h->t, w, X, B, nu, stream));
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_check_diverged(rbc_t h, cudaStream_t stream) {
+  if (!h) return fail(RBC_EINVAL, "null handle");
+  CK(cudaStreamSynchronize(stream));
+  if (h->last_B == 0) return RBC_OK;
+  std::vector<int> f(h->last_B);
+  CK(cudaMemcpy(f.data(), h->w.flags, f.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int v : f)
+    if (v) return fail(RBC_EDIVERGED, "non-finite state");
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_nusselt(rbc_t h, const void* d_state, double out[3], cudaStream_t stream) {
+  if (!h || !d_state || !out) return fail(RBC_EINVAL, "null argument");
+  rbc_status s = rbc_reserve(h, 1);
+  if (s != RBC_OK) return s;
+  CK(launch_nusselt(h->g, h->t, h->w, static_cast<const double*>(d_state), h->w.small, stream));
+  CK(cudaMemcpyAsync(out, h->w.small, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream) {
+  if (!h || !d_state || !out) return fail(RBC_EINVAL, "null argument");
+  rbc_status s = rbc_reserve(h, 1);
+  if (s != RBC_OK) return s;
+  CK(launch_l2_diff(h->g, h->t, static_cast<const double*>(d_state), nullptr, 1, h->w.small, stream));
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, h->w.small, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  *out = std::sqrt(v);
+  return RBC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Parareal (Sec. 3.1, Eq. 20).
+// ---------------------------------------------------------------------------
+static bool whole_steps(double len, double dt, int* n) {
+  const double q = len / dt;
+  const double r = std::round(q);
+  if (r < 1 || std::fabs(q - r) > 1e-9 * r) return false;
+  *n = (int)r;
+  return true;
+}
+
+extern "C" void parareal_destroy(parareal_t p) {
+  if (!p) return;
+  cudaFree(p->d_F);
+  cudaFree(p->d_Uold);
+  cudaFree(p->d_Gold);
+  cudaFree(p->d_C);
+  cudaFree(p->d_I);
+  cudaFree(p->d_norm);
+  delete p;
+}
+
+extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, double t1, int nslices, int criterion,
+                                      double tol, parareal_t* out) {
+  if (!out) return fail(RBC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!fine || !coarse || nslices < 1 || !(t1 > t0)) return fail(RBC_EINVAL, "bad handles, slices or interval");
+  if (criterion < RBC_CRIT_FIXED || criterion > RBC_CRIT_NU || !(tol >= 0)) return fail(RBC_EINVAL, "bad criterion");
+  const Grid &gf = fine->g, &gc = coarse->g;
+  if (gc.Nx > gf.Nx || gc.Nz > gf.Nz) return fail(RBC_EINVAL, "coarse grid finer than fine grid");
+  if (gc.Ra != gf.Ra || gc.Pr != gf.Pr || gc.Lx != gf.Lx) return fail(RBC_EINVAL, "Ra, Pr, Lx differ");
+  const double len = (t1 - t0) / nslices;
+  int nf = 0, nc = 0;
+  if (!whole_steps(len, gf.dt, &nf)) return fail(RBC_EINVAL, "slice length is not a whole number of fine steps");
+  if (!whole_steps(len, gc.dt, &nc)) return fail(RBC_EINVAL, "slice length is not a whole number of coarse steps");
+  pr_s* p = new (std::nothrow) pr_s();
+  if (!p) return fail(RBC_ENOMEM, "host allocation");
+  p->fine = fine;
+  p->coarse = coarse;
+  p->t0 = t0;
+  p->t1 = t1;
+  p->N = nslices;
+  p->nf = nf;
+  p->nc = nc;
+  p->criterion = criterion;
+  p->tol = tol;
+  const size_t Sf = state_doubles(gf) * sizeof(double), Sc = state_doubles(gc) * sizeof(double);
+  const int N = nslices;
+  bool ok = cudaMalloc(&p->d_F, N * Sf) == cudaSuccess && cudaMalloc(&p->d_Uold, (N + 1) * Sf) == cudaSuccess &&
+            cudaMalloc(&p->d_Gold, N * Sc) == cudaSuccess && cudaMalloc(&p->d_C, Sc) == cudaSuccess &&
+            cudaMalloc(&p->d_I, N * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&p->d_norm, 2 * (N + 1) * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    parareal_destroy(p);
+    return fail(RBC_ENOMEM, "Parareal buffers");
+  }
+  rbc_status s = rbc_reserve(fine, N);
+  if (s == RBC_OK) s = rbc_reserve(coarse, 1);
+  if (s != RBC_OK) {
+    parareal_destroy(p);
+    return s;
+  }
+  *out = p;
+  return RBC_OK;
+}
+
+extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_iters, int* k_done,
+                                       double* defects, double* nus, cudaStream_t stream) {
+  if (!p || !d_U0 || !d_U || max_iters < 1) return fail(RBC_EINVAL, "bad arguments");
+  rbc_t F = p->fine, G = p->coarse;
+  const Grid &gf = F->g, &gc = G->g;
+  const size_t Sf = state_doubles(gf), Sc = state_doubles(gc);
+  const int N = p->N;
+  double* U = static_cast<double*>(d_U);
+  std::vector<int> ncv(1, p->nc);
+  if (k_done) *k_done = 0;
+  CK(cudaMemcpyAsync(U, d_U0, Sf * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  // k = 0: serial coarse sweep U_{n+1}^0 = G(U_n^0)
+  for (int n = 0; n < N; ++n) {
+    CK(launch_restrict(gf, gc, U + n * Sf, p->d_C, stream));
+    rbc_status s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, stream);
+    if (s != RBC_OK) return s;
+    CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Sc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CK(launch_prolong(gf, gc, p->d_C, U + (n + 1) * Sf, stream));
+  }
+  std::vector<int> nfv(N, p->nf);
+  std::vector<double> I(N), nrm(2 * (N + 1));
+  double nu_prev = 0.0;
+  const int n_half = N / 2;
+  const double win = (p->t1 - p->t0) * (double)(N - n_half) / N;
+  rbc_status result = (p->criterion == RBC_CRIT_FIXED) ? RBC_OK : RBC_ENOTCONVERGED;
+  for (int k = 1; k <= max_iters; ++k) {
+    // fine sweep on slices n >= k-1 (earlier slices are already exact)
+    const int n0 = k - 1;
+    CK(cudaMemcpyAsync(p->d_F + n0 * Sf, U + n0 * Sf, (size_t)(N - n0) * Sf * sizeof(double),
+                       cudaMemcpyDeviceToDevice, stream));
+    rbc_status s = rbc_step_batch(F, p->d_F + n0 * Sf, N - n0, nfv.data(), p->d_I + n0, stream);
+    if (s != RBC_OK) return s;
+    s = rbc_check_diverged(F, stream);
+    if (s != RBC_OK) return s;
+    CK(cudaMemcpyAsync(p->d_Uold, U, (size_t)(N + 1) * Sf * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    // serial correction sweep
+    for (int n = 0; n < N; ++n) {
+      if (n <= k - 1) {
+        // U_n unchanged since the last iteration: G(U_n) = Gold_n exactly
+        CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_Gold + n * Sc, p->d_Gold + n * Sc, U + (n + 1) * Sf,
+                          stream));
+        continue;
+      }
+      CK(launch_restrict(gf, gc, U + n * Sf, p->d_C, stream));
+      s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, stream);
+      if (s != RBC_OK) return s;
+      CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_C, p->d_Gold + n * Sc, U + (n + 1) * Sf, stream));
+      CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Sc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    }
+    s = rbc_check_diverged(G, stream);
+    if (s != RBC_OK) return s;
+    // Defect_k = max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k||  (L2 of T)
+    CK(launch_l2_diff(gf, F->t, U, p->d_Uold, N + 1, p->d_norm, stream));
+    CK(launch_l2_diff(gf, F->t, U, nullptr, N + 1, p->d_norm + N + 1, stream));
+    CK(cudaMemcpyAsync(nrm.data(), p->d_norm, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(I.data(), p->d_I, N * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    double defect = 0.0;
+    for (int n = 1; n <= N; ++n) {
+      if (!std::isfinite(nrm[n]) || !std::isfinite(nrm[N + 1 + n])) return fail(RBC_EDIVERGED, "non-finite iterate");
+      if (nrm[N + 1 + n] > 0) defect = std::max(defect, std::sqrt(nrm[n] / nrm[N + 1 + n]));
+    }
+    double nu = 0.0;
+    for (int n = n_half; n < N; ++n) nu += I[n];
+    nu /= win;
+    if (defects) defects[k - 1] = defect;
+    if (nus) nus[k - 1] = nu;
+    if (k_done) *k_done = k;
+    if (p->criterion == RBC_CRIT_DEFECT && defect <= p->tol) return RBC_OK;
+    if (p->criterion == RBC_CRIT_NU && k >= 2 && std::fabs(nu - nu_prev) <= p->tol * std::fabs(nu)) return RBC_OK;
+    nu_prev = nu;
+  }
+  return result;
+}

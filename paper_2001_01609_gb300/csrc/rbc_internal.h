@@ -1,0 +1,94 @@
+// Internal types shared by the host runtime (rbc_host.cpp) and the CUDA
+// kernels (rbc_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+#include "../../include/rbc.h"
+
+namespace rbc {
+
+// Grid and physical parameters, passed to kernels by value.
+struct Grid {
+  int Nx, Nz;     // native resolution (Fourier points, Chebyshev points)
+  int nm;         // Fourier modes kept, m = 0 .. nm-1 (nm = Nx/2, Nyquist dropped)
+  int Mx, Mz;     // 3/2-padded product grid (uniform x, Chebyshev-Lobatto z)
+  int nq;         // coefficients per Chebyshev parity (Nz/2)
+  double Ra, Pr, Lx, dt;
+  double kfac;    // 2 pi / Lx, k_m = kfac * m
+};
+
+// Device-resident operator tables (built on the host in FP64 once per grid/dt).
+// Parity-split tables are laid out [p][row][j][m] so that threads with
+// consecutive Fourier index m read consecutive addresses.
+struct Tables {
+  const double* zinv;   // [4][Mz][Nz]  d^q T_n / ds^q at the padded Lobatto points, q = 0..3
+  const double* zfwd;   // [Nz][Mz]     padded Lobatto values -> T coefficients n < Nz
+  const double* cc;     // [Mz]         Clenshaw-Curtis weights on the padded points
+  const double2* tw;    // [Mx]         exp(-2 pi i t / Mx)
+  const double* s2;     // [2][nq][3]   C^(2) conversion S1 S0, tau row t, columns q = t..t+2
+  const double* s4;     // [2][nq][5]   C^(4) conversion S3 S2 S1 S0, columns q = t..t+4
+  const double* mp;     // [2][nq][5][nm] psi mass operator lap_k in C^(4)
+  // UL factors of the stage matrices (M - dt/2 L) with boundary rows on top.
+  // T: D = 1, [2][nq][1][nm]; P (psi, m >= 1): D = 2, [2][nq][2][nm];
+  // U (mean flow, m = 0): D = 1, [2][nq][1][1].  Dinv: [2][D*D][nmod];
+  // invd (reciprocal diagonal): [2][nq][nmod] for every system.
+  const double *T_multB, *T_multD, *T_Dinv, *T_Lb, *T_invd;
+  const double *P_multB, *P_multD, *P_Dinv, *P_Lb, *P_invd;
+  const double *U_multB, *U_multD, *U_Dinv, *U_Lb, *U_invd;
+  const double* gram;   // [Nz][Nz]  int_{-1}^{1} T_a T_b ds
+  // native grid transforms
+  const double2* twn;   // [Nx]      exp(-2 pi i t / Nx)
+  const double* Vn;     // [Nz][Nz]  T_n(s_j) at the native points
+  const double* Vn1;    // [Nz][Nz]  T_n'(s_j)
+  const double* Wn;     // [Nz][Nz]  native values -> T coefficients (exact interpolation)
+};
+
+// Per-call workspace pointers (capacity >= B states).
+struct Work {
+  double* Xs;      // stage state, B states
+  double* F;       // explicit-term coefficients, B states
+  double* R;       // RK accumulators, [B][4] states (tau rows in the coefficient slots)
+  double* Z;       // z-inverse output, [B][9][Mz][nm] complex
+  double* Q;       // row-kernel output, [B][2][Mz][nm] complex
+  double* wT;      // [B][Mz] x-mean of w T
+  int* nsteps;     // [B]
+  int* step;       // [1] step counter of the running batch
+  int* flags;      // [B] non-finite flags
+  double* nu;      // [B] internal Nu integral when the caller passes none
+  double* small;   // [16] scalars
+};
+
+#ifdef __CUDACC__
+#define RBC_HD __host__ __device__
+#else
+#define RBC_HD
+#endif
+RBC_HD inline size_t state_doubles(const Grid& g) { return (size_t)2 * g.Nz * g.nm * 2; }
+RBC_HD inline size_t z_doubles(const Grid& g) { return (size_t)9 * g.Mz * g.nm * 2; }
+RBC_HD inline size_t q_doubles(const Grid& g) { return (size_t)2 * g.Mz * g.nm * 2; }
+
+// ---- launchers (rbc_kernels.cu) ----
+cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* X, int B, int stage,
+                         double* nu, cudaStream_t s);
+cudaError_t launch_explicit(const Grid& g, const Tables& t, const Work& w, const double* X, int B,
+                            bool all_active, cudaStream_t s);
+cudaError_t launch_advance(const Work& w, cudaStream_t s);
+cudaError_t launch_nu_final(const Grid& g, const Tables& t, const Work& w, const double* X, int B,
+                            double* nu, cudaStream_t s);
+cudaError_t launch_nusselt(const Grid& g, const Tables& t, const Work& w, const double* X, double* out3,
+                           cudaStream_t s);
+cudaError_t launch_l2_diff(const Grid& g, const Tables& t, const double* A, const double* Bm, int nst,
+                           double* out, cudaStream_t s);
+cudaError_t launch_set_state(const Grid& g, const Tables& t, const double* gT, const double* gu,
+                             const double* gw, double* scratch, double* X, cudaStream_t s);
+cudaError_t launch_get_state(const Grid& g, const Tables& t, const double* X, double* scratch, double* gT,
+                             double* gu, double* gw, cudaStream_t s);
+cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const double* Xf, double* Xc, cudaStream_t s);
+cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, const double* Gnew,
+                           const double* Gold, double* Uout, cudaStream_t s);
+cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, cudaStream_t s);
+size_t rows_smem_bytes(const Grid& g);
+cudaError_t configure_kernels(const Grid& g);
+
+}  // namespace rbc

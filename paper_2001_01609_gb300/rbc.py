@@ -1,0 +1,207 @@
+"""Thin ctypes binding of librbc.so (the C ABI declared in include/rbc.h).
+
+Argument marshalling only: every step of the propagator, the Parareal update and
+the norms runs in the CUDA library.  PyTorch provides device memory and streams.
+There is no CPU fallback: if the library is missing, every entry point raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librbc.so")
+
+RBC_OK, RBC_EINVAL, RBC_ENOMEM, RBC_ECUDA, RBC_EDIVERGED, RBC_ETIMEOUT, RBC_ENOTCONVERGED = 0, -1, -2, -3, -4, -5, 1
+RBC_FP64, RBC_MIXED = 0, 1
+CRIT_FIXED, CRIT_DEFECT, CRIT_NU = 0, 1, 2
+
+EXPORTS = [
+    "rbc_last_error", "rbc_create", "rbc_destroy", "rbc_state_bytes", "rbc_workspace_bytes_per_state",
+    "rbc_reserve", "rbc_set_state", "rbc_get_state", "rbc_step_batch", "rbc_check_diverged", "rbc_nusselt",
+    "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate",
+]
+
+
+class RBCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rbc status {status}: {msg}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("bc", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load librbc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} not found: build it with paper_2001_01609_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "rbc_last_error": (ctypes.c_char_p, []),
+        "rbc_create": (I, [D, D, D, I, I, D, ctypes.POINTER(_Opts), ctypes.POINTER(P)]),
+        "rbc_destroy": (None, [P]),
+        "rbc_state_bytes": (S, [P]),
+        "rbc_workspace_bytes_per_state": (S, [P]),
+        "rbc_reserve": (I, [P, I]),
+        "rbc_set_state": (I, [P, P, PD, PD, PD]),
+        "rbc_get_state": (I, [P, P, PD, PD, PD]),
+        "rbc_step_batch": (I, [P, P, I, PI, P, P]),
+        "rbc_check_diverged": (I, [P, P]),
+        "rbc_nusselt": (I, [P, P, PD, P]),
+        "rbc_l2_temperature": (I, [P, P, PD, P]),
+        "parareal_create": (I, [P, P, D, D, I, I, D, ctypes.POINTER(P)]),
+        "parareal_destroy": (None, [P]),
+        "parareal_iterate": (I, [P, P, P, I, PI, PD, PD, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, allow=()):
+    if status != RBC_OK and status not in allow:
+        raise RBCError(status, load().rbc_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+class Propagator:
+    """F (or G) of Eq. 20 on one grid: rbc_create(Ra, Pr, Lx, Nx, Nz, dt)."""
+
+    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, precision=RBC_FP64):
+        lib = load()
+        self.Ra, self.Pr, self.Lx, self.Nx, self.Nz, self.dt = Ra, Pr, Lx, Nx, Nz, dt
+        self.precision = precision
+        h = ctypes.c_void_p()
+        opts = _Opts(precision, 0)
+        _check(lib.rbc_create(Ra, Pr, Lx, Nx, Nz, dt, ctypes.byref(opts), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rbc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def state_shape(self):
+        return (2, self.Nz, self.Nx // 2, 2)
+
+    @property
+    def state_bytes(self):
+        return load().rbc_state_bytes(self.h)
+
+    @property
+    def workspace_bytes_per_state(self):
+        return load().rbc_workspace_bytes_per_state(self.h)
+
+    def new_states(self, B, device="cuda"):
+        import torch
+        return torch.zeros((B,) + self.state_shape, dtype=torch.float64, device=device)
+
+    def reserve(self, B):
+        _check(load().rbc_reserve(self.h, B))
+
+    def set_state(self, state, T, u=None, w=None):
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        _check(load().rbc_set_state(self.h, _ptr(state), _dptr(T), _dptr(u), _dptr(w)))
+
+    def get_state(self, state):
+        shp = (self.Nz, self.Nx)
+        T, u, w = np.empty(shp), np.empty(shp), np.empty(shp)
+        _check(load().rbc_get_state(self.h, _ptr(state), _dptr(T), _dptr(u), _dptr(w)))
+        return T, u, w
+
+    def step_batch(self, states, nsteps, nu=None, stream=None):
+        """Advance states (B, *state_shape) in place; nsteps int or sequence of B ints."""
+        B = states.shape[0]
+        ns = np.full(B, nsteps, dtype=np.int32) if np.isscalar(nsteps) else np.ascontiguousarray(nsteps, np.int32)
+        assert ns.shape == (B,)
+        nup = _ptr(nu) if nu is not None else None
+        _check(load().rbc_step_batch(self.h, _ptr(states), B, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     nup, _stream(stream)))
+
+    def check_diverged(self, stream=None):
+        return _check(load().rbc_check_diverged(self.h, _stream(stream)), allow=(RBC_EDIVERGED,))
+
+    def nusselt(self, state, stream=None):
+        out = np.zeros(3)
+        _check(load().rbc_nusselt(self.h, _ptr(state), _dptr(out), _stream(stream)))
+        return tuple(out)
+
+    def l2_temperature(self, state, stream=None):
+        out = np.zeros(1)
+        _check(load().rbc_l2_temperature(self.h, _ptr(state), _dptr(out), _stream(stream)))
+        return float(out[0])
+
+
+def coarse_dt(slice_length, dt_requested):
+    """Largest dt <= dt_requested dividing the slice into whole steps (ceil the count)."""
+    n = int(np.ceil(slice_length / dt_requested - 1e-9))
+    return slice_length / n, n
+
+
+class Parareal:
+    """Parareal (Eq. 20) over [t0, t1] with nslices slices of F = fine, G = coarse."""
+
+    def __init__(self, fine, coarse, t0, t1, nslices, criterion=CRIT_FIXED, tol=0.0):
+        lib = load()
+        self.fine, self.coarse, self.nslices = fine, coarse, nslices
+        self.t0, self.t1 = t0, t1
+        h = ctypes.c_void_p()
+        _check(lib.parareal_create(fine.h, coarse.h, t0, t1, nslices, criterion, tol, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().parareal_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self, U0, U, max_iters, stream=None):
+        """Returns (status, k_done, defects[k], nus[k]); U (nslices+1 states) receives U^k."""
+        k = ctypes.c_int(0)
+        de = np.zeros(max_iters)
+        nu = np.zeros(max_iters)
+        st = load().parareal_iterate(self.h, _ptr(U0), _ptr(U), max_iters, ctypes.byref(k), _dptr(de), _dptr(nu),
+                                     _stream(stream))
+        _check(st, allow=(RBC_ENOTCONVERGED, RBC_EDIVERGED))
+        return st, k.value, de[: k.value], nu[: k.value]

@@ -1,0 +1,237 @@
+"""Parity of the CUDA propagator and Parareal (through the C ABI) with the FP64 oracle.
+
+Tolerance: 1e-10 relative for FP64 runs (the all-FP64 target); a few steps on
+small grids are held to 1e-11.  Max-norm over all spectral coefficients,
+relative to the largest coefficient.
+"""
+import numpy as np
+import pytest
+
+from layout import from_abi, max_rel_diff, to_abi
+from oracle.parareal import parareal as oracle_parareal
+from oracle.rbc import RBC, prolong, restrict
+from paper_2001_01609_gb300.inputs import initial_temperature
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::DeprecationWarning")]
+
+
+@pytest.fixture(scope="module")
+def rbc():
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc as r
+    r.load()
+    assert torch.cuda.is_available()
+    return r
+
+
+def put(states, b, X):
+    states[b].copy_(torch.from_numpy(to_abi(X)))
+
+
+def get(states, b):
+    return from_abi(states[b].cpu().numpy())
+
+
+def developed_state(o, seed, amp=0.3, steps=3):
+    """A nonlinear state: strong seeded perturbation, a few oracle steps."""
+    X = o.from_grid(initial_temperature(o.Nx, o.Nz, seed=seed, amplitude=amp, Lx=o.Lx))
+    for _ in range(steps):
+        X, _ = o.step(X)
+    return X
+
+
+@pytest.mark.parametrize("Nx,Nz", [(64, 32), (16, 10), (8, 18)])
+def test_set_state_matches_oracle_transform(rbc, Nx, Nz):
+    o = RBC(1e4, 1.0, 2.0, Nx, Nz, 1e-3)
+    F = rbc.Propagator(1e4, 1.0, 2.0, Nx, Nz, 1e-3)
+    Tg = initial_temperature(Nx, Nz, seed=4, amplitude=0.2)
+    g = np.random.default_rng(1)
+    ug, wg = g.standard_normal((Nz, Nx)), g.standard_normal((Nz, Nx))
+    st = F.new_states(1)
+    F.set_state(st[0], Tg, ug, wg)
+    ref = o.from_grid(Tg, ug, wg)
+    assert max_rel_diff(get(st, 0), ref) < 1e-12
+    T2, u2, w2 = F.get_state(st[0])
+    To, uo, wo = o.to_grid(ref)
+    for a, b in ((T2, To), (u2, uo), (w2, wo)):
+        assert np.abs(a - b).max() < 1e-11 * max(1.0, np.abs(b).max())
+
+
+@pytest.mark.parametrize("Nx,Nz,Ra", [(16, 18, 1e5), (32, 16, 3e4), (8, 10, 2e5), (64, 32, 1e6)])
+def test_few_steps_match_oracle(rbc, Nx, Nz, Ra):
+    dt = 2e-4
+    o = RBC(Ra, 1.0, 2.0, Nx, Nz, dt)
+    X0 = developed_state(o, seed=Nx + Nz)
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt)
+    st = F.new_states(1)
+    put(st, 0, X0)
+    nu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F.step_batch(st, 4, nu)
+    assert F.check_diverged() == rbc.RBC_OK
+    ref, integ = o.run(X0, 4)
+    assert max_rel_diff(get(st, 0), ref) < 1e-11
+    assert abs(nu.item() - integ) < 1e-11 * abs(integ)
+
+
+def test_config0_single_slice_parity_over_1000_steps(rbc):
+    """Ra = 1e4, 64 x 32, dt = 1e-3, seeded IC (seed 0): one slice of t in [0, 1]."""
+    o = RBC(1e4, 1.0, 2.0, 64, 32, 1e-3)
+    Tg = initial_temperature(64, 32, seed=0)
+    F = rbc.Propagator(1e4, 1.0, 2.0, 64, 32, 1e-3)
+    st = F.new_states(1)
+    F.set_state(st[0], Tg)
+    X0 = o.from_grid(Tg)
+    assert max_rel_diff(get(st, 0), X0) < 1e-13
+    nu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F.step_batch(st, 1000, nu)
+    ref, integ = o.run(X0, 1000)
+    assert max_rel_diff(get(st, 0), ref) < 1e-10
+    assert abs(nu.item() - integ) < 1e-10 * abs(integ)
+    nv = F.nusselt(st[0])
+    no = o.nusselt(ref)
+    assert np.allclose(nv, no, rtol=1e-10, atol=0)
+
+
+def test_batched_uneven_steps_equal_solo_runs_and_oracle(rbc):
+    Nx, Nz, Ra, dt = 32, 18, 5e4, 5e-4
+    o = RBC(Ra, 1.0, 2.0, Nx, Nz, dt)
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt)
+    Xs = [developed_state(o, seed=s, steps=1) for s in range(4)]
+    nsteps = [7, 0, 3, 5]
+    st = F.new_states(4)
+    for b, X in enumerate(Xs):
+        put(st, b, X)
+    nu = torch.zeros(4, dtype=torch.float64, device="cuda")
+    F.step_batch(st, nsteps, nu)
+    for b, X in enumerate(Xs):
+        solo = F.new_states(1)
+        put(solo, 0, X)
+        nus = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F.step_batch(solo, nsteps[b], nus)
+        assert torch.equal(solo[0], st[b])                 # batch-invariant, bitwise
+        assert nus.item() == nu[b].item()
+        ref, integ = o.run(X, nsteps[b])
+        assert max_rel_diff(get(st, b), ref) < 1e-11
+        assert abs(nu[b].item() - integ) <= 1e-11 * max(abs(integ), 1e-30)
+    assert torch.equal(st[1].cpu(), torch.from_numpy(to_abi(Xs[1])))   # 0 steps: untouched
+
+
+def test_nusselt_and_l2_match_oracle(rbc):
+    o = RBC(2e5, 1.0, 2.0, 32, 24, 1e-3)
+    X = developed_state(o, seed=7, amp=0.5, steps=4)
+    F = rbc.Propagator(2e5, 1.0, 2.0, 32, 24, 1e-3)
+    st = F.new_states(1)
+    put(st, 0, X)
+    assert np.allclose(F.nusselt(st[0]), o.nusselt(X), rtol=1e-12, atol=1e-13)
+    assert abs(F.l2_temperature(st[0]) - o.l2_T(X)) < 1e-12 * o.l2_T(X)
+
+
+def test_conduction_state_stays_exact(rbc):
+    # exact conduction coefficients (T = 1/2 - z, nothing else): at Ra = 1e8 any
+    # roundoff in the m >= 1 modes would grow, so the state is set spectrally
+    F = rbc.Propagator(1e8, 1.0, 2.0, 64, 32, 1e-4)
+    st = F.new_states(1)
+    st[0, 0, 0, 0, 0] = 0.5
+    st[0, 0, 1, 0, 0] = -0.5
+    before = st.clone()
+    F.step_batch(st, 20)
+    assert (st - before).abs().max().item() < 1e-14
+    nv, nb, nt = F.nusselt(st[0])
+    assert abs(nv - 1) < 1e-13 and abs(nb - 1) < 1e-12 and abs(nt - 1) < 1e-12
+
+
+def test_config1_full_size_batched_launch_sampled_slices(rbc):
+    """Ra = 1e6, 256 x 64, 32 slices in one launch; slices 0 and 31 checked."""
+    Nx, Nz, Ra, dt = 256, 64, 1e6, 2e-4
+    o = RBC(Ra, 1.0, 2.0, Nx, Nz, dt)
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt)
+    B = 32
+    st = F.new_states(B)
+    for b in range(B):
+        F.set_state(st[b], initial_temperature(Nx, Nz, seed=100 + b, amplitude=0.3))
+    X0 = {b: get(st, b) for b in (0, B - 1)}
+    F.step_batch(st, 3)
+    assert F.check_diverged() == rbc.RBC_OK
+    for b, X in X0.items():
+        ref, _ = o.run(X, 3)
+        assert max_rel_diff(get(st, b), ref) < 1e-10
+
+
+def test_nonfinite_state_is_reported(rbc):
+    F = rbc.Propagator(1e4, 1.0, 2.0, 16, 16, 1e-3)
+    st = F.new_states(2)
+    F.set_state(st[0], initial_temperature(16, 16, seed=0))
+    F.set_state(st[1], initial_temperature(16, 16, seed=1))
+    st[1, 0, 3, 2, 0] = float("nan")
+    F.step_batch(st, 2)
+    assert F.check_diverged() == rbc.RBC_EDIVERGED
+    assert torch.isfinite(st[0]).all()
+    F.step_batch(st[:1], 1)
+    assert F.check_diverged() == rbc.RBC_OK
+
+
+def test_empty_batch_and_zero_steps(rbc):
+    F = rbc.Propagator(1e4, 1.0, 2.0, 16, 16, 1e-3)
+    st = F.new_states(2)
+    F.set_state(st[0], initial_temperature(16, 16, seed=0))
+    before = st.clone()
+    F.step_batch(st[:0], 3)
+    F.step_batch(st, [0, 0])
+    assert torch.equal(st, before)
+
+
+def parareal_case():
+    Ra, Nf, Zf, Nc, Zc = 3e4, 32, 16, 16, 8
+    dtf, dtc, N, T = 2e-3, 4e-3, 4, 0.064
+    return Ra, Nf, Zf, Nc, Zc, dtf, dtc, N, T
+
+
+def test_parareal_matches_oracle_and_is_exact_on_first_k_slices(rbc):
+    Ra, Nf, Zf, Nc, Zc, dtf, dtc, N, T = parareal_case()
+    fo, co = RBC(Ra, 1.0, 2.0, Nf, Zf, dtf), RBC(Ra, 1.0, 2.0, Nc, Zc, dtc)
+    nf, nc = int(round(T / N / dtf)), int(round(T / N / dtc))
+    U0 = fo.from_grid(initial_temperature(Nf, Zf, seed=0, amplitude=0.3))
+    K = 3
+    ores = oracle_parareal(U0, N, lambda U: fo.run(U, nf), lambda U: prolong(co.run(restrict(U, Nc, Zc), nc)[0], Nf, Zf),
+                           K, lambda a, b: fo.l2_T(a - b) / fo.l2_T(a), nu_window=(N // 2, T / 2))
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nf, Zf, dtf)
+    G = rbc.Propagator(Ra, 1.0, 2.0, Nc, Zc, dtc)
+    P = rbc.Parareal(F, G, 0.0, T, N)
+    u0 = F.new_states(1)
+    put(u0, 0, U0)
+    U = F.new_states(N + 1)
+    st, k, defects, nus = P.iterate(u0[0], U, K)
+    assert st == rbc.RBC_OK and k == K
+    for n in range(N + 1):
+        assert max_rel_diff(get(U, n), ores["U"][n]) < 1e-10
+    np.testing.assert_allclose(defects, ores["defects"], rtol=1e-8)
+    np.testing.assert_allclose(nus, ores["nus"], rtol=1e-10)
+    # exactness: U_n^K equals the GPU serial fine solution bitwise for n <= K
+    ser = F.new_states(1)
+    put(ser, 0, U0)
+    for n in range(1, K + 1):
+        F.step_batch(ser, nf)
+        assert torch.equal(ser[0], U[n]), n
+
+
+def test_parareal_stopping_criteria(rbc):
+    Ra, Nf, Zf, Nc, Zc, dtf, dtc, N, T = parareal_case()
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nf, Zf, dtf)
+    G = rbc.Propagator(Ra, 1.0, 2.0, Nc, Zc, dtc)
+    u0 = F.new_states(1)
+    F.set_state(u0[0], initial_temperature(Nf, Zf, seed=0, amplitude=0.3))
+    U = F.new_states(N + 1)
+    st, k, d, nus = rbc.Parareal(F, G, 0.0, T, N).iterate(u0[0], U, 4)
+    tol = d[1] * 1.0001
+    expect = 1 + min(i for i in range(len(d)) if d[i] <= tol)
+    Pd = rbc.Parareal(F, G, 0.0, T, N, rbc.CRIT_DEFECT, tol)
+    st2, k2, d2, _ = Pd.iterate(u0[0], U, 4)
+    assert st2 == rbc.RBC_OK and k2 == expect
+    np.testing.assert_array_equal(d2, d[:k2])          # deterministic rerun
+    Pn = rbc.Parareal(F, G, 0.0, T, N, rbc.CRIT_NU, 1e-30)
+    st3, k3, _, _ = Pn.iterate(u0[0], U, 2)
+    assert st3 == rbc.RBC_ENOTCONVERGED and k3 == 2
+    with pytest.raises(rbc.RBCError):
+        rbc.Parareal(F, G, 0.0, T * 1.0001, N)          # not a whole number of steps
