@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Benchmark of the batched Parareal hot path on one GB300 (or N, weak scaling).
+
+A step is one pass of the whole hot path over one batch: one call of
+parareal_iterate with max_iters = 1, i.e. the serial coarse sweep, the batched
+fine sweep of all time slices, the serial coarse correction sweep with the
+Parareal update (Eq. 20) and the defect/Nusselt norms.
+
+Workload (default): Ra = 1e6, Pr = 1, Lx/Lz = 2, fine 256 x 64 (Fourier x
+Chebyshev), coarse 128 x 32, 32 time slices of 3125 fine steps each, all FP64,
+seeded noise initial condition.  The fine and coarse time steps are the largest
+stable ones of a halving ladder (the configured 2e-4 / 2e-3 blow up in the
+initial plume burst); the configured number of fine steps per slice is kept.
+
+value: fine DOF-steps per second, DOF = 2 Nx Nz per slice (psi and T), counted
+over the fine sweep of all slices, divided by the wall time of the whole step.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Parareal time-to-tol vs serial fine on 1 GB300; DOF-steps/s; p50/p99 latency"
+UNIT = "DOF-steps/s"
+
+# Workloads.  dt values: largest stable on the halving ladder from the
+# configured values (oracle survey: the configured steps blow up at t ~ 0.015).
+WORKLOADS = {
+    "rbc_ra1e6_256x64_32slices_fp64": dict(
+        Ra=1e6, Pr=1.0, Lx=2.0, Nx=256, Nz=64, Nxc=128, Nzc=32, dt=1.25e-5, dtc_target=1.5625e-5,
+        slices=32, steps_per_slice=3125, seed=1),
+    "rbc_ra1e4_64x32_4slices_fp64": dict(
+        Ra=1e4, Pr=1.0, Lx=2.0, Nx=64, Nz=32, Nxc=32, Nzc=16, dt=1e-3, dtc_target=5e-3,
+        slices=4, steps_per_slice=1000, seed=0),
+}
+DEFAULT = "rbc_ra1e6_256x64_32slices_fp64"
+
+
+def derived(w):
+    slice_len = w["steps_per_slice"] * w["dt"]
+    nc = max(1, int(round(slice_len / w["dtc_target"])))
+    return dict(slice_len=slice_len, t_end=w["slices"] * slice_len, nc=nc, dtc=slice_len / nc,
+                dof=2 * w["Nx"] * w["Nz"])
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, one host thread, bounded sample.
+# --------------------------------------------------------------------------
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle.rbc import RBC
+from paper_2001_01609_gb300.inputs import initial_temperature
+w = {w!r}
+o = RBC(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"])
+X = o.from_grid(initial_temperature(w["Nx"], w["Nz"], seed=w["seed"], Lx=w["Lx"]))
+X, _ = o.step(X)
+t0 = time.perf_counter(); n = 0
+while True:
+    X, _ = o.step(X); n += 1
+    el = time.perf_counter() - t0
+    if el > {budget} or n >= {max_steps}:
+        break
+print(json.dumps(dict(steps=n, seconds=el)))
+"""
+
+
+def cpu_oracle_rate(w, budget_s=12.0, max_steps=100000):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = CPU_SNIPPET.format(root=ROOT, w=w, budget=budget_s, max_steps=max_steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    rate = 2 * w["Nx"] * w["Nz"] * d["steps"] / d["seconds"]
+    return rate, d
+
+
+# --------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# --------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=mx, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# --------------------------------------------------------------------------
+def run_gb300(args, w):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, d = cpu_oracle_rate(w)       # before any CUDA work in this process
+        cpu = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
+                   sample=f"oracle fine propagator, one slice, {d['steps']} RK443 steps of the "
+                          f"{w['Nx']}x{w['Nz']} grid in {d['seconds']:.1f} s on one host thread")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2001_01609_gb300 import build
+    if local == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2001_01609_gb300 import rbc
+    from paper_2001_01609_gb300.inputs import initial_temperature
+
+    dv = derived(w)
+    F = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"])
+    G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dv["dtc"])
+    N = w["slices"]
+    P = rbc.Parareal(F, G, 0.0, dv["t_end"], N)
+    stream = torch.cuda.current_stream()
+    U0 = F.new_states(1)
+    Th = initial_temperature(w["Nx"], w["Nz"], seed=w["seed"] + rank, Lx=w["Lx"])
+    F.set_state(U0[0], Th)
+    U = F.new_states(N + 1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+
+    def one_step():
+        st, k, de, nu = P.iterate(U0[0], U, 1)
+        if st == rbc.RBC_EDIVERGED:
+            raise RuntimeError("diverged")
+        return de, nu
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device())
+    times = []
+    launches0 = rbc.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    F.profile(True)
+    for _ in range(args.steps):
+        flush.zero_()                                         # L2 flush between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        de, nu = one_step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    prof = F.profile_read()
+    F.profile(False)
+    ck = clocks.stop()
+    gpu_launches = rbc.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    tot = torch.tensor([sum(times)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    t_total = tot.item()
+    fine_dof_steps = N * w["steps_per_slice"] * dv["dof"]
+    value = world * fine_dof_steps * args.steps / t_total
+
+    # e2e through the public API with host buffers: H2D of the initial state from
+    # pinned memory, the Parareal iteration, D2H of the last slice state.
+    U0h = U0.cpu().pin_memory()
+    outh = torch.empty_like(U[N], device="cpu").pin_memory()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        U0.copy_(U0h, non_blocking=True)
+        one_step()
+        outh.copy_(U[N], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    et = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_value = world * fine_dof_steps * args.steps / et.item()
+
+    # roofline of the dominant kernel (largest summed time); FP64 work is
+    # bound by the FP64 pipe: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz.
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pk = prof[dom]
+    avg_s = pk["ms"] / 1e3 / max(1, pk["launches"])
+    flops_per = pk["flops"] / max(1, pk["launches"])
+    peak_fp64 = 152 * 4 * 2070e6 / 1e12
+    achieved = flops_per / avg_s / 1e12
+    roofline = dict(bound="alu", achieved=achieved, peak=peak_fp64, unit="TFLOP/s", frac=achieved / peak_fp64,
+                    traffic=None, kernel=dom, peak_source="derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz",
+                    bytes_per_launch=pk["bytes"] / max(1, pk["launches"]),
+                    kernel_share={k: prof[k]["ms"] / max(1e-30, sum(v["ms"] for v in prof.values()))
+                                  for k in prof})
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=1e3 * t_total / args.steps, higher_is_better=True, scaling="weak",
+                    vs_baseline=None, dtype="f64", data="synthetic",
+                    config=dict(workload=args.workload, Ra=w["Ra"], grid=f"{w['Nx']}x{w['Nz']}",
+                                coarse_grid=f"{w['Nxc']}x{w['Nzc']}", slices=N,
+                                fine_steps_per_slice=w["steps_per_slice"], coarse_steps_per_slice=dv["nc"],
+                                dt=w["dt"], dt_coarse=dv["dtc"], t_end=dv["t_end"], dof_per_slice=dv["dof"],
+                                step="one Parareal iteration (coarse sweep, batched fine sweep, correction, norms)",
+                                l2="flushed between timed steps (256 MB write)",
+                                parallelism=f"{world} independent problems" if world > 1 else "single GPU"),
+                    e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(U0h.numel() * 8),
+                             d2h_bytes_per_step=int(outh.numel() * 8)),
+                    gpu_launches=int(gpu_launches), roofline=roofline, cpu_baseline=cpu, clocks=ck,
+                    defect=float(de[-1]) if len(de) else None, nu=float(nu[-1]) if len(nu) else None)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, d = cpu_oracle_rate(w, budget_s=4.0)
+        if i >= args.warmup:
+            rates.append((rate, d))
+    total_steps = sum(d["steps"] for _, d in rates)
+    total_s = sum(d["seconds"] for _, d in rates)
+    value = 2 * w["Nx"] * w["Nz"] * total_steps / total_s
+    cpu = dict(value=value, unit=UNIT, cores=1, kind="oracle",
+               sample=f"per step: oracle fine propagator, one slice of the {w['Nx']}x{w['Nz']} grid, "
+                      f"RK443 steps for ~4 s on one host thread")
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=int(os.environ.get("WORLD_SIZE", "1")),
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, Ra=w["Ra"], grid=f"{w['Nx']}x{w['Nz']}", dt=w["dt"]),
+                cpu_baseline=cpu, e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gb300(args, w)
+
+
+if __name__ == "__main__":
+    main()

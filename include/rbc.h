@@ -144,6 +144,24 @@ void parareal_destroy(parareal_t p);
 rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_iters,
                             int* k_done, double* defects, double* nus, cudaStream_t stream);
 
+/* ---- Instrumentation (outside the paper's method) ----
+ * Kernel kinds of one RK443 stage: z-inverse transform, row kernel (x-FFTs and
+ * products), z-forward transform, stage solve. */
+enum { RBC_KERNEL_ZINV = 0, RBC_KERNEL_ROWS = 1, RBC_KERNEL_ZFWD = 2, RBC_KERNEL_SOLVE = 3, RBC_NKERNELS = 4 };
+
+/* rbc_profile(h, 1) starts recording a CUDA event pair on the launching stream
+ * around every stage kernel that h launches and clears the totals; (h, 0)
+ * stops recording.  rbc_profile_read synchronises the device and returns, per
+ * kernel kind, the summed event time (ms), the launch count, and the
+ * algorithmic FP operations and DRAM bytes of those launches (each operand
+ * read once, each result written once, all B slices active).  Any of the
+ * output arrays may be NULL. */
+rbc_status rbc_profile(rbc_t h, int enable);
+rbc_status rbc_profile_read(rbc_t h, double ms[4], long long launches[4], double flops[4], double bytes[4]);
+
+/* Number of CUDA kernels this library has launched in this process. */
+unsigned long long rbc_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -240,6 +240,15 @@ struct rbc_s {
   Work w{};
   double* d_scratch = nullptr;   // set/get state and diagnostics, independent of B
   int last_B = 0;
+  Prof prof;
+  // one captured RK443 step (4 stages + step counter), replayed per step
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_graph = nullptr;
+  const void* graph_X = nullptr;
+  const void* graph_nu = nullptr;
+  int graph_B = -1;
+  void* graph_work = nullptr;
+  bool use_graphs = true;
 };
 
 struct pr_s {
@@ -511,6 +520,9 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
 
 extern "C" void rbc_destroy(rbc_t h) {
   if (!h) return;
+  for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+  if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   cudaFree(h->d_tables);
   cudaFree(h->d_work);
   cudaFree(h->d_scratch);
@@ -556,8 +568,39 @@ extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
   w.nsteps = ip; ip += B;
   w.flags = ip; ip += B;
   w.step = ip;
+  w.prof = &h->prof;
   return RBC_OK;
 }
+
+extern "C" rbc_status rbc_profile(rbc_t h, int enable) {
+  if (!h) return fail(RBC_EINVAL, "null handle");
+  Prof& p = h->prof;
+  if (enable) {
+    CK(p.fold());
+    for (int k = 0; k < RBC_NKERNELS; ++k) {
+      p.ms[k] = p.flops[k] = p.bytes[k] = 0.0;
+      p.launches[k] = 0;
+    }
+  }
+  p.on = enable != 0;
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_profile_read(rbc_t h, double ms[4], long long launches[4], double flops[4],
+                                       double bytes[4]) {
+  if (!h) return fail(RBC_EINVAL, "null handle");
+  Prof& p = h->prof;
+  CK(p.fold());
+  for (int k = 0; k < RBC_NKERNELS; ++k) {
+    if (ms) ms[k] = p.ms[k];
+    if (launches) launches[k] = p.launches[k];
+    if (flops) flops[k] = p.flops[k];
+    if (bytes) bytes[k] = p.bytes[k];
+  }
+  return RBC_OK;
+}
+
+extern "C" unsigned long long rbc_launch_count(void) { return launches_so_far(); }
 
 extern "C" rbc_status rbc_set_state(rbc_t h, void* d_state, const double* h_T, const double* h_u, const double* h_w) {
   if (!h || !d_state || !h_T) return fail(RBC_EINVAL, "null argument");
@@ -589,6 +632,41 @@ extern "C" rbc_status rbc_get_state(rbc_t h, const void* d_state, double* h_T, d
   return RBC_OK;
 }
 
+// Capture one RK443 step of this (states, B, nu) binding on the handle's own
+// stream; the kernels read the step counter from device memory, so the same
+// graph serves every step of the batch.
+static rbc_status ensure_step_graph(rbc_t h, double* X, int B, double* nu) {
+  if (h->step_graph && h->graph_X == X && h->graph_B == B && h->graph_nu == nu && h->graph_work == h->d_work)
+    return RBC_OK;
+  if (h->step_graph) {
+    cudaGraphExecDestroy(h->step_graph);
+    h->step_graph = nullptr;
+  }
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t gr = nullptr;
+  const unsigned long long before = launches_so_far();
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage) e = launch_stage(h->g, h->t, h->w, X, B, stage, nu, h->cap_stream);
+  if (e == cudaSuccess) e = launch_advance(h->w, h->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &gr);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return fail(RBC_ECUDA, "step graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  if (launches_so_far() - before != (unsigned long long)kStepKernels)
+    return fail(RBC_ECUDA, "step graph: unexpected kernel count");
+  add_launches(~0ull - (unsigned long long)kStepKernels + 1ull);   // captured, not executed
+  e = cudaGraphInstantiate(&h->step_graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(RBC_ECUDA, "step graph instantiate: %s", cudaGetErrorString(e));
+  h->graph_X = X;
+  h->graph_B = B;
+  h->graph_nu = nu;
+  h->graph_work = h->d_work;
+  return RBC_OK;
+}
+
 extern "C" rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps, double* d_nu_integral,
                                      cudaStream_t stream) {
   if (!h || B < 0 || (B > 0 && (!d_states || !h_nsteps))) return fail(RBC_EINVAL, "null argument or B < 0");
@@ -608,9 +686,17 @@ extern "C" rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* 
   CK(cudaMemsetAsync(w.flags, 0, (size_t)B * sizeof(int), stream));
   CK(cudaMemsetAsync(nu, 0, (size_t)B * sizeof(double), stream));
   h->last_B = B;
-  for (int st = 0; st < maxs; ++st) {
-    for (int stage = 1; stage <= 4; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
-    CK(launch_advance(w, stream));
+  const bool graphs = h->use_graphs && !h->prof.on && maxs >= 2;
+  if (graphs) {
+    rbc_status gs = ensure_step_graph(h, X, B, nu);
+    if (gs != RBC_OK) return gs;
+    for (int st = 0; st < maxs; ++st) CK(cudaGraphLaunch(h->step_graph, stream));
+    add_launches((unsigned long long)maxs * kStepKernels);
+  } else {
+    for (int st = 0; st < maxs; ++st) {
+      for (int stage = 1; stage <= 4; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
+      CK(launch_advance(w, stream));
+    }
   }
   if (maxs > 0) CK(launch_nu_final(h->g, h->t, w, X, B, nu, stream));
   return RBC_OK;

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
+#include <vector>
 
 #include "../../include/rbc.h"
 
@@ -44,6 +45,23 @@ struct Tables {
   const double* Wn;     // [Nz][Nz]  native values -> T coefficients (exact interpolation)
 };
 
+// Optional per-kernel CUDA-event timing (host side).  Event pairs come from a
+// pool; when it runs out, the stream is synchronised and the elapsed times are
+// folded into the totals so that the pool can be reused.
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // 2 per record
+  std::vector<int> kind;         // kind of each recorded pair
+  size_t used = 0;
+  double ms[4] = {0, 0, 0, 0};
+  long long launches[4] = {0, 0, 0, 0};
+  double flops[4] = {0, 0, 0, 0};
+  double bytes[4] = {0, 0, 0, 0};
+  cudaError_t fold();
+  void begin(int k, cudaStream_t s);
+  void end(int k, cudaStream_t s, double fl, double by);
+};
+
 // Per-call workspace pointers (capacity >= B states).
 struct Work {
   double* Xs;      // stage state, B states
@@ -57,6 +75,7 @@ struct Work {
   int* flags;      // [B] non-finite flags
   double* nu;      // [B] internal Nu integral when the caller passes none
   double* small;   // [16] scalars
+  Prof* prof;      // timing, or nullptr
 };
 
 #ifdef __CUDACC__
@@ -89,6 +108,9 @@ cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, con
                            const double* Gold, double* Uout, cudaStream_t s);
 cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, cudaStream_t s);
 size_t rows_smem_bytes(const Grid& g);
+unsigned long long launches_so_far();
+void add_launches(unsigned long long n);   // kernels launched through a replayed graph
+constexpr int kStepKernels = 17;           // 4 stages x 4 kernels + step counter
 cudaError_t configure_kernels(const Grid& g);
 
 }  // namespace rbc

@@ -14,6 +14,9 @@
 //            buoyancy coupling), RK accumulator updates, Nu_V accumulation.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+#include <cmath>
 #include <cstdint>
 
 #include "rbc_internal.h"
@@ -56,74 +59,99 @@ __device__ __forceinline__ bool slice_active(const int* nsteps, const int* step,
 }
 
 // ---------------------------------------------------------------------------
-// z inverse transform (k_zinv).  Thread per (slice, padded row j, mode m).
-// psi-slot operators V, VD, VD^2, VD^3 (d/ds) and T-slot V, VD; the epilogue
-// forms, with d/dz = 2 d/ds and d/dx = ik:
+// z inverse transform (k_zinv).  Thread per (slice, padded row j < ceil(Mz/2),
+// mode m).  Even/odd split: the padded points are symmetric, s_{Mz-1-j} = -s_j,
+// and T_n^(q)(-s) = (-1)^(n+q) T_n^(q)(s), so the sums E, O over even and odd n
+// at s_j give f^(q)(s_j) = E + O and f^(q)(-s_j) = (-1)^q (E - O): half the
+// multiply-adds of evaluating both rows.  psi-slot operators V, VD, VD^2, VD^3
+// (d/ds) and T-slot V, VD; the epilogue forms, with d/dz = 2 d/ds, d/dx = ik:
 //   u = d_z psi (m = 0: U),  w = -ik psi,  d_x omega, d_z omega (omega = -lap psi,
 //   m = 0: omega = -U'),  d_x u,  d_z u,  T,  d_x T,  d_z T.
 // Output Z[b][field][j][m] (complex), fields in that order.
 // ---------------------------------------------------------------------------
-__global__ void k_zinv(Grid g, const double* __restrict__ Bz, const double* __restrict__ X, size_t S,
-                       double* __restrict__ Z, int B, const int* nsteps, const int* step) {
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long per = (long)g.Mz * g.nm;
-  if (idx >= per * B) return;
-  const int b = (int)(idx / per);
-  if (!slice_active(nsteps, step, b)) return;
-  const int rem = (int)(idx - (long)b * per);
-  const int j = rem / g.nm, m = rem - j * g.nm;
-  const double* Xb = X + (size_t)b * S;
-  const double* b0 = Bz + (size_t)(0 * g.Mz + j) * g.Nz;
-  const double* b1 = Bz + (size_t)(1 * g.Mz + j) * g.Nz;
-  const double* b2 = Bz + (size_t)(2 * g.Mz + j) * g.Nz;
-  const double* b3 = Bz + (size_t)(3 * g.Mz + j) * g.Nz;
-  double2 p0 = {0, 0}, p1 = {0, 0}, p2 = {0, 0}, p3 = {0, 0}, t0 = {0, 0}, t1 = {0, 0};
-  for (int n = 0; n < g.Nz; ++n) {
-    const double2 xp = ld2(Xb + soff(g, 1, n, m));
-    const double2 xt = ld2(Xb + soff(g, 0, n, m));
-    const double v0 = __ldg(b0 + n), v1 = __ldg(b1 + n), v2 = __ldg(b2 + n), v3 = __ldg(b3 + n);
-    p0.x = fma(v0, xp.x, p0.x); p0.y = fma(v0, xp.y, p0.y);
-    p1.x = fma(v1, xp.x, p1.x); p1.y = fma(v1, xp.y, p1.y);
-    p2.x = fma(v2, xp.x, p2.x); p2.y = fma(v2, xp.y, p2.y);
-    p3.x = fma(v3, xp.x, p3.x); p3.y = fma(v3, xp.y, p3.y);
-    t0.x = fma(v0, xt.x, t0.x); t0.y = fma(v0, xt.y, t0.y);
-    t1.x = fma(v1, xt.x, t1.x); t1.y = fma(v1, xt.y, t1.y);
-  }
-  const double k = g.kfac * m;
-  double2 u, w, dxo, dzo, dxu, dzu, T, dxT, dzT;
+__device__ __forceinline__ void zinv_store(const Grid& g, double* Zb, int j, int m, double k, const double2* P,
+                                           double2 t0, double2 t1) {
+  double2 u, w, dxo, dzo, dxu, dzu, dxT;
   if (m == 0) {
-    u = make_double2(p0.x, 0.0);
+    u = make_double2(P[0].x, 0.0);
     w = make_double2(0.0, 0.0);
     dxo = make_double2(0.0, 0.0);
-    dzo = make_double2(-4.0 * p2.x, 0.0);
+    dzo = make_double2(-4.0 * P[2].x, 0.0);
     dxu = make_double2(0.0, 0.0);
-    dzu = make_double2(2.0 * p1.x, 0.0);
-    T = t0;
+    dzu = make_double2(2.0 * P[1].x, 0.0);
     dxT = make_double2(0.0, 0.0);
-    dzT = 2.0 * t1;
   } else {
-    u = 2.0 * p1;
-    w = -k * times_i(p0);                             // -ik psi
-    const double2 om = (k * k) * p0 - 4.0 * p2;       // omega = -(4 psi'' - k^2 psi)
+    u = 2.0 * P[1];
+    w = -k * times_i(P[0]);                            // -ik psi
+    const double2 om = (k * k) * P[0] - 4.0 * P[2];    // omega = -(4 psi'' - k^2 psi)
     dxo = k * times_i(om);
-    dzo = (2.0 * k * k) * p1 - 8.0 * p3;              // -(8 psi''' - 2 k^2 psi')
+    dzo = (2.0 * k * k) * P[1] - 8.0 * P[3];           // -(8 psi''' - 2 k^2 psi')
     dxu = k * times_i(u);
-    dzu = 4.0 * p2;
-    T = t0;
+    dzu = 4.0 * P[2];
     dxT = k * times_i(t0);
-    dzT = 2.0 * t1;
   }
   const size_t fs = (size_t)g.Mz * g.nm * 2;
-  double* zb = Z + (size_t)b * 9 * fs + ((size_t)j * g.nm + m) * 2;
+  double* zb = Zb + ((size_t)j * g.nm + m) * 2;
   st2(zb + 0 * fs, u);
   st2(zb + 1 * fs, w);
   st2(zb + 2 * fs, dxo);
   st2(zb + 3 * fs, dzo);
   st2(zb + 4 * fs, dxu);
   st2(zb + 5 * fs, dzu);
-  st2(zb + 6 * fs, T);
+  st2(zb + 6 * fs, t0);
   st2(zb + 7 * fs, dxT);
-  st2(zb + 8 * fs, dzT);
+  st2(zb + 8 * fs, 2.0 * t1);
+}
+
+__global__ void k_zinv(Grid g, const double* __restrict__ Bz, const double* __restrict__ X, size_t S,
+                       double* __restrict__ Z, int B, const int* nsteps, const int* step) {
+  const int Mh = (g.Mz + 1) / 2;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per = (long)Mh * g.nm;
+  if (idx >= per * B) return;
+  const int b = (int)(idx / per);
+  if (!slice_active(nsteps, step, b)) return;
+  const int rem = (int)(idx - (long)b * per);
+  const int j = rem / g.nm, m = rem - j * g.nm;
+  const double* Xb = X + (size_t)b * S;
+  const double* bq[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bq[q] = Bz + (size_t)(q * g.Mz + j) * g.Nz;
+  double2 E[6], O[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) E[q] = O[q] = make_double2(0.0, 0.0);
+  for (int n = 0; n < g.Nz; n += 2) {                  // Nz is even
+#pragma unroll
+    for (int par = 0; par < 2; ++par) {
+      const double2 xp = ld2(Xb + soff(g, 1, n + par, m));
+      const double2 xt = ld2(Xb + soff(g, 0, n + par, m));
+      double2* A = par ? O : E;
+      double v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = __ldg(bq[q] + n + par);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        A[q].x = fma(v[q], xp.x, A[q].x);
+        A[q].y = fma(v[q], xp.y, A[q].y);
+      }
+      A[4].x = fma(v[0], xt.x, A[4].x);
+      A[4].y = fma(v[0], xt.y, A[4].y);
+      A[5].x = fma(v[1], xt.x, A[5].x);
+      A[5].y = fma(v[1], xt.y, A[5].y);
+    }
+  }
+  const double k = g.kfac * m;
+  double* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
+  double2 P[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) P[q] = E[q] + O[q];
+  zinv_store(g, Zb, j, m, k, P, E[4] + O[4], E[5] + O[5]);
+  const int jr = g.Mz - 1 - j;
+  if (jr != j) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) P[q] = ((q & 1) ? -1.0 : 1.0) * (E[q] - O[q]);
+    zinv_store(g, Zb, jr, m, k, P, E[4] - O[4], -1.0 * (E[5] - O[5]));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -279,46 +307,96 @@ __global__ void __launch_bounds__(256) k_rows(Grid g, const double2* __restrict_
 
 // ---------------------------------------------------------------------------
 // z forward transform (k_zfwd): F[b][f][n][m] = sum_j W[n][j] Q[b][f][j][m], n < Nz.
+// W[n][Mz-1-j] = (-1)^n W[n][j] (symmetric points), so with the folds
+// Ev_j = Q_j + Q_{Mz-1-j}, Od_j = Q_j - Q_{Mz-1-j} (the middle row, for odd Mz,
+// once in Ev) F_n = sum_{j < ceil(Mz/2)} W[n][j] (n even ? Ev : Od)_j.  Block per
+// (slice, field, tile of tm modes): folds staged in shared memory once, reused
+// by every n.
 // ---------------------------------------------------------------------------
 __global__ void k_zfwd(Grid g, const double* __restrict__ W, const double* __restrict__ Q, double* __restrict__ F,
-                       size_t S, int B, const int* nsteps, const int* step) {
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long per = 2L * g.Nz * g.nm;
-  if (idx >= per * B) return;
-  const int b = (int)(idx / per);
-  if (!slice_active(nsteps, step, b)) return;
-  int rem = (int)(idx - (long)b * per);
-  const int m = rem % g.nm;
-  rem /= g.nm;
-  const int n = rem % g.Nz, f = rem / g.Nz;
+                       size_t S, int B, int tm, const int* nsteps, const int* step) {
+  extern __shared__ double2 fold[];                    // [2][Mh][tm]
+  const int Mh = (g.Mz + 1) / 2;
+  const int mt = (g.nm + tm - 1) / tm;
+  const int b = blockIdx.x / (2 * mt);
+  const int rem = blockIdx.x - b * 2 * mt;
+  const int f = rem / mt, m0 = (rem - f * mt) * tm;
+  if (b >= B || !slice_active(nsteps, step, b)) return;
   const size_t qs = (size_t)g.Mz * g.nm * 2;
-  const double* q = Q + (size_t)(b * 2 + f) * qs + (size_t)m * 2;
-  const double* wr = W + (size_t)n * g.Mz;
-  double2 acc = {0.0, 0.0};
-  for (int jz = 0; jz < g.Mz; ++jz) {
-    const double wv = __ldg(wr + jz);
-    const double2 v = ld2(q + (size_t)jz * g.nm * 2);
-    acc.x = fma(wv, v.x, acc.x);
-    acc.y = fma(wv, v.y, acc.y);
+  const double* q = Q + (size_t)(b * 2 + f) * qs;
+  for (int it = threadIdx.x; it < Mh * tm; it += blockDim.x) {
+    const int jh = it / tm, mi = it - jh * tm, m = m0 + mi;
+    double2 ev = {0.0, 0.0}, od = {0.0, 0.0};
+    if (m < g.nm) {
+      const double2 a = ld2(q + ((size_t)jh * g.nm + m) * 2);
+      const int jr = g.Mz - 1 - jh;
+      if (jr != jh) {
+        const double2 c = ld2(q + ((size_t)jr * g.nm + m) * 2);
+        ev = a + c;
+        od = a - c;
+      } else {
+        ev = a;
+      }
+    }
+    fold[(size_t)jh * tm + mi] = ev;
+    fold[(size_t)(Mh + jh) * tm + mi] = od;
   }
-  st2(F + (size_t)b * S + soff(g, f, n, m), acc);
+  __syncthreads();
+  const int ng = blockDim.x / tm;
+  const int mi = threadIdx.x % tm, n0 = threadIdx.x / tm;
+  const int m = m0 + mi;
+  if (m >= g.nm) return;
+  for (int n = n0; n < g.Nz; n += ng) {
+    const double2* src = fold + (size_t)((n & 1) ? Mh : 0) * tm + mi;
+    const double* wr = W + (size_t)n * g.Mz;
+    double2 acc = {0.0, 0.0};
+    for (int jh = 0; jh < Mh; ++jh) {
+      const double wv = __ldg(wr + jh);
+      const double2 v = src[(size_t)jh * tm];
+      acc.x = fma(wv, v.x, acc.x);
+      acc.y = fma(wv, v.y, acc.y);
+    }
+    st2(F + (size_t)b * S + soff(g, f, n, m), acc);
+  }
 }
 
+static int zfwd_tile(const Grid& g) {
+  const int Mh = (g.Mz + 1) / 2;
+  int tm = 32;
+  while (tm > 4 && (size_t)2 * Mh * tm * 16 > 200 * 1024) tm >>= 1;
+  return tm;
+}
+static size_t zfwd_smem(const Grid& g) { return (size_t)2 * ((g.Mz + 1) / 2) * zfwd_tile(g) * 16; }
+
 // ---------------------------------------------------------------------------
-// Stage solve (k_solve).
+// Stage solve (k_solve).  Thread per (slice, Fourier mode m, Chebyshev parity
+// p, real/imaginary part c): the stage matrices are real, so the real and the
+// imaginary parts are independent systems, except for the implicit buoyancy
+// coupling -i k Pr Ra T, which feeds the imaginary part of T into the real
+// part of psi and the real part into the imaginary one; the two parts of one
+// mode sit on adjacent lanes and exchange T through memory after a warp
+// barrier.  T first, then psi (m >= 1) or the mean flow U (m = 0).  The stage
+// right-hand side is assembled in chunks of CH tau rows whose loads are issued
+// together; the elimination vectors live in this thread's shared-memory
+// columns, so the sequential recurrences never wait on global memory.
 // ---------------------------------------------------------------------------
 enum { KT = 0, KP = 1, KU = 2 };
+constexpr int CH = 4;
 
-// One parity-split system of one field for one (slice, m, p).
+// One parity-split system of one field for one (slice, m, p, c).
 //   tau row t (full row 2t+p) of (M - dt/2 L) X_i = r_i, boundary rows on top;
-//   r_i = M X_0 + dt sum_{j<i} (aE_ij F_j + aI_ij L X_j) kept in accumulators:
-//   R_i complete when stage i starts; dt L X_i = 2 (M X_i - r_i).
+//   r_i = M X_0 + dt sum_{j<i} (aE_ij F_j + aI_ij L X_j) is kept in
+//   accumulators R_l (complete for l = i when stage i starts), and
+//   dt L X_i = 2 (M X_i - r_i) feeds the later accumulators.
+// ycol/rcol: this thread's shared-memory columns, element q at [q * ld].
 template <int KIND>
-__device__ bool solve_system(const Grid& g, const Tables& tb, int stage, int p, int m, const double* X0, double* Xo,
-                             const double* Fc, double* R, size_t S) {
+__device__ bool solve_system(const Grid& g, const Tables& tb, int stage, int p, int m, int c,
+                             const double* __restrict__ X0, double* __restrict__ Xo,
+                             const double* __restrict__ Fc, double* __restrict__ R, size_t S, double* ycol,
+                             double* rcol, int ld) {
   constexpr int D = (KIND == KP) ? 2 : 1;
   constexpr int LAM = 2 * D;
-  const int nq = g.nq;
+  const int nq = g.nq, nt = nq - D;
   const int f = (KIND == KT) ? 0 : 1;
   const int nmod = (KIND == KU) ? 1 : g.nm;
   const int mi = (KIND == KU) ? 0 : m;
@@ -327,8 +405,8 @@ __device__ bool solve_system(const Grid& g, const Tables& tb, int stage, int p, 
   const double* Dinv = (KIND == KT) ? tb.T_Dinv : (KIND == KP) ? tb.P_Dinv : tb.U_Dinv;
   const double* Lb = (KIND == KT) ? tb.T_Lb : (KIND == KP) ? tb.P_Lb : tb.U_Lb;
   const double* invd = (KIND == KT) ? tb.T_invd : (KIND == KP) ? tb.P_invd : tb.U_invd;
-  auto tix = [&](int c, int jj) { return ((size_t)(p * nq + c) * D + jj) * nmod + mi; };
-  auto co = [&](int n) { return soff(g, f, n, m); };
+  auto tix = [&](int cc, int jj) { return ((size_t)(p * nq + cc) * D + jj) * nmod + mi; };
+  auto co = [&](int n) { return soff(g, f, n, m) + c; };
   auto tapF = [&](int t, int jj) -> double {
     return (KIND == KP) ? __ldg(tb.s4 + (p * nq + t) * 5 + jj) : __ldg(tb.s2 + (p * nq + t) * 3 + jj);
   };
@@ -338,116 +416,163 @@ __device__ bool solve_system(const Grid& g, const Tables& tb, int stage, int p, 
   };
   const double fsign = (KIND == KP) ? 1.0 : -1.0;
   const double dt = g.dt;
-  const double cpl = 0.5 * dt * g.Pr * g.Ra * (g.kfac * m);
-  double* Ri = R + (size_t)(stage - 1) * S;
+  // + dt/2 (-i k Pr Ra) S4 T_i: real part gets +k.. Im(S4 T), imaginary part -k.. Re(S4 T)
+  const double cpl = (c == 0 ? 1.0 : -1.0) * 0.5 * dt * g.Pr * g.Ra * (g.kfac * m);
+  const double aEi = dt * c_AE[stage][stage - 1];
 
-  // pass 1: right-hand side rows, backward elimination of the upper band
-  double2 pend[D];
-  double2 bd[D];
-  for (int jj = 0; jj < D; ++jj) {
-    pend[jj] = make_double2(0.0, 0.0);
-    bd[jj] = make_double2(0.0, 0.0);
-  }
-  for (int c = nq - 1; c >= D; --c) {
-    const int t = c - D;
-    double2 fv = {0.0, 0.0};
-    for (int jj = 0; jj <= LAM; ++jj) {
-      const int q = t + jj;
-      if (q < nq) fv = fv + tapF(t, jj) * ld2(Fc + co(2 * q + p));
+  // phase 1: right-hand side of every tau row, accumulator updates for later stages
+  for (int t0 = 0; t0 < nt; t0 += CH) {
+    double Fw[CH + LAM], Xw[CH + LAM], Tw[CH + 4], Ri[CH], Rl[3][CH];
+#pragma unroll
+    for (int j = 0; j < CH + LAM; ++j) {
+      const int q = t0 + j;
+      Fw[j] = (q < nq) ? __ldg(Fc + co(2 * q + p)) : 0.0;
+      Xw[j] = (stage == 1 && q < nq) ? __ldg(X0 + co(2 * q + p)) : 0.0;
     }
-    fv = fsign * fv;
-    const size_t ro = co(2 * t + p);
-    double2 r;
-    if (stage == 1) {
-      double2 mx = {0.0, 0.0};
-      for (int jj = 0; jj <= LAM; ++jj) {
-        const int q = t + jj;
-        if (q < nq) mx = mx + tapM(t, jj) * ld2(X0 + co(2 * q + p));
-      }
-      r = mx + (dt * c_AE[1][0]) * fv;
-      for (int l = 2; l <= 4; ++l) st2(R + (size_t)(l - 1) * S + ro, mx + (dt * c_AE[l][0]) * fv);
-    } else {
-      r = ld2(Ri + ro) + (dt * c_AE[stage][stage - 1]) * fv;
-      for (int l = stage + 1; l <= 4; ++l) {
-        double* Rl = R + (size_t)(l - 1) * S + ro;
-        st2(Rl, ld2(Rl) + (dt * c_AE[l][stage - 1]) * fv);
-      }
-    }
-    st2(Ri + ro, r);
-    double2 bv = r;
     if (KIND == KP) {
-      double2 st = {0.0, 0.0};
-      for (int jj = 0; jj <= 4; ++jj) {
-        const int q = t + jj;
-        if (q < nq) st = st + __ldg(tb.s4 + (p * nq + t) * 5 + jj) * ld2(Xo + soff(g, 0, 2 * q + p, m));
+#pragma unroll
+      for (int j = 0; j < CH + 4; ++j) {
+        const int q = t0 + j;
+        Tw[j] = (q < nq) ? Xo[soff(g, 0, 2 * q + p, m) + (1 - c)] : 0.0;
       }
-      bv.x += cpl * st.y;                               // + dt/2 (-i k Pr Ra) S4 T_i
-      bv.y -= cpl * st.x;
     }
-    const double2 bc = bv + pend[0];
-    st2(Xo + co(2 * c + p), bc);
-    for (int jj = 0; jj < D - 1; ++jj) pend[jj] = pend[jj + 1] - __ldg(multB + tix(c, D - 1 - jj)) * bc;
-    pend[D - 1] = -__ldg(multB + tix(c, 0)) * bc;
-    for (int r2 = 0; r2 < D; ++r2) bd[r2] = bd[r2] - __ldg(multD + tix(c, r2)) * bc;
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc) {
+      const int t = t0 + cc;
+      const size_t ro = co(2 * (t < nt ? t : 0) + p);
+      Ri[cc] = (stage > 1 && t < nt) ? R[(size_t)(stage - 1) * S + ro] : 0.0;
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        Rl[l][cc] = (stage > 1 && t < nt && l + 2 > stage) ? R[(size_t)(l + 1) * S + ro] : 0.0;
+    }
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc) {
+      const int t = t0 + cc;
+      if (t >= nt) break;
+      double fv = 0.0;
+#pragma unroll
+      for (int jj = 0; jj <= LAM; ++jj) fv = fma(tapF(t, jj), Fw[cc + jj], fv);
+      fv *= fsign;
+      const size_t ro = co(2 * t + p);
+      double r;
+      if (stage == 1) {
+        double mx = 0.0;
+#pragma unroll
+        for (int jj = 0; jj <= LAM; ++jj) mx = fma(tapM(t, jj), Xw[cc + jj], mx);
+        r = fma(dt * c_AE[1][0], fv, mx);
+#pragma unroll
+        for (int l = 2; l <= 4; ++l) R[(size_t)(l - 1) * S + ro] = fma(dt * c_AE[l][0], fv, mx);
+      } else {
+        r = fma(aEi, fv, Ri[cc]);
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+          if (l + 2 > stage) R[(size_t)(l + 1) * S + ro] = fma(dt * c_AE[l + 2][stage - 1], fv, Rl[l][cc]);
+      }
+      rcol[t * ld] = r;
+      double bv = r;
+      if (KIND == KP) {
+        double st = 0.0;
+#pragma unroll
+        for (int jj = 0; jj <= 4; ++jj) st = fma(__ldg(tb.s4 + (p * nq + t) * 5 + jj), Tw[cc + jj], st);
+        bv = fma(cpl, st, bv);
+      }
+      ycol[(t + D) * ld] = bv;
+    }
+  }
+  // phase 2: backward elimination of the upper band (UL factors)
+  double pend[D], bd[D];
+#pragma unroll
+  for (int jj = 0; jj < D; ++jj) pend[jj] = bd[jj] = 0.0;
+  for (int cc = nq - 1; cc >= D; --cc) {
+    const double bc = ycol[cc * ld] + pend[0];
+    ycol[cc * ld] = bc;
+#pragma unroll
+    for (int jj = 0; jj < D - 1; ++jj) pend[jj] = fma(-__ldg(multB + tix(cc, D - 1 - jj)), bc, pend[jj + 1]);
+    pend[D - 1] = -__ldg(multB + tix(cc, 0)) * bc;
+#pragma unroll
+    for (int r2 = 0; r2 < D; ++r2) bd[r2] = fma(-__ldg(multD + tix(cc, r2)), bc, bd[r2]);
   }
   // boundary rows (Eq. 6): parity combinations of f(1) +- f(-1)
-  double2 bb[D];
-  for (int r2 = 0; r2 < D; ++r2) bb[r2] = bd[r2];
-  if (KIND == KT && m == 0) bb[0].x += (p == 0) ? 0.5 : -0.5;   // T(-1/2) = 1, T(1/2) = 0
-  double2 win[D];
+  if (KIND == KT && m == 0 && c == 0) bd[0] += (p == 0) ? 0.5 : -0.5;   // T(-1/2) = 1, T(1/2) = 0
+  // phase 3: dense boundary block, forward substitution with the lower band
+  double win[D];
   bool ok = true;
+#pragma unroll
   for (int r2 = 0; r2 < D; ++r2) {
-    double2 x = {0.0, 0.0};
-    for (int c2 = 0; c2 < D; ++c2)
-      x = x + __ldg(Dinv + ((size_t)(p * D * D) + r2 * D + c2) * nmod + mi) * bb[c2];
+    double x = 0.0;
+#pragma unroll
+    for (int c2 = 0; c2 < D; ++c2) x = fma(__ldg(Dinv + ((size_t)(p * D * D) + r2 * D + c2) * nmod + mi), bd[c2], x);
     win[r2] = x;
-    st2(Xo + co(2 * r2 + p), x);
-    ok = ok && finite2(x);
+    ycol[r2 * ld] = x;
+    Xo[co(2 * r2 + p)] = x;
+    ok = ok && isfinite(x);
   }
-  // pass 2: forward substitution with the lower band
   for (int r2 = D; r2 < nq; ++r2) {
-    double2 y = ld2(Xo + co(2 * r2 + p));
-    for (int jj = 0; jj < D; ++jj) y = y - __ldg(Lb + tix(r2, jj)) * win[jj];
-    const double2 x = __ldg(invd + (size_t)(p * nq + r2) * nmod + mi) * y;
-    st2(Xo + co(2 * r2 + p), x);
+    double y = ycol[r2 * ld];
+#pragma unroll
+    for (int jj = 0; jj < D; ++jj) y = fma(-__ldg(Lb + tix(r2, jj)), win[jj], y);
+    const double x = __ldg(invd + (size_t)(p * nq + r2) * nmod + mi) * y;
+    ycol[r2 * ld] = x;
+    Xo[co(2 * r2 + p)] = x;
+#pragma unroll
     for (int jj = 0; jj < D - 1; ++jj) win[jj] = win[jj + 1];
     win[D - 1] = x;
-    ok = ok && finite2(x);
+    ok = ok && isfinite(x);
   }
-  // pass 3: dt aI_li L X_i = 2 aI_li (M X_i - r_i) into later accumulators
+  // phase 4: dt aI_li L X_i = 2 aI_li (M X_i - r_i) into later accumulators
   if (stage < 4) {
-    for (int t = 0; t < nq - D; ++t) {
-      double2 mx = {0.0, 0.0};
-      for (int jj = 0; jj <= LAM; ++jj) {
-        const int q = t + jj;
-        if (q < nq) mx = mx + tapM(t, jj) * ld2(Xo + co(2 * q + p));
+    for (int t0 = 0; t0 < nt; t0 += CH) {
+      double Rl[3][CH];
+#pragma unroll
+      for (int cc = 0; cc < CH; ++cc) {
+        const int t = t0 + cc;
+        const size_t ro = co(2 * (t < nt ? t : 0) + p);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) Rl[l][cc] = (t < nt && l + 2 > stage) ? R[(size_t)(l + 1) * S + ro] : 0.0;
       }
-      const size_t ro = co(2 * t + p);
-      const double2 lx2 = 2.0 * (mx - ld2(Ri + ro));
-      for (int l = stage + 1; l <= 4; ++l) {
-        double* Rl = R + (size_t)(l - 1) * S + ro;
-        st2(Rl, ld2(Rl) + c_AI[l][stage] * lx2);
+#pragma unroll
+      for (int cc = 0; cc < CH; ++cc) {
+        const int t = t0 + cc;
+        if (t >= nt) break;
+        double mx = 0.0;
+#pragma unroll
+        for (int jj = 0; jj <= LAM; ++jj) {
+          const int q = t + jj;
+          if (q < nq) mx = fma(tapM(t, jj), ycol[q * ld], mx);
+        }
+        const double lx2 = 2.0 * (mx - rcol[t * ld]);
+        const size_t ro = co(2 * t + p);
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+          if (l + 2 > stage) R[(size_t)(l + 1) * S + ro] = fma(c_AI[l + 2][stage], lx2, Rl[l][cc]);
       }
     }
   }
   return ok;
 }
 
+// Block = solve_threads(g) threads = (modes) x (real, imaginary) of one (slice, parity).
 __global__ void k_solve(Grid g, Tables tb, double* X, double* Xs, const double* F, double* R, size_t S,
                         const double* wT, double* nu, int* flags, int B, int stage, const int* nsteps,
                         const int* step) {
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long per = 2L * g.nm;
-  if (idx >= per * B) return;
-  const int b = (int)(idx / per);
-  if (!slice_active(nsteps, step, b)) return;
-  const int rem = (int)(idx - (long)b * per);
-  const int p = rem / g.nm, m = rem - p * g.nm;
+  extern __shared__ double scol[];
+  const int per_blk = blockDim.x / 2;
+  const int mtiles = (g.nm + per_blk - 1) / per_blk;
+  const int b = blockIdx.x / (2 * mtiles);
+  const int rem = blockIdx.x - b * 2 * mtiles;
+  const int p = rem / mtiles;
+  const int m = (rem - p * mtiles) * per_blk + (int)threadIdx.x / 2;
+  const int c = threadIdx.x & 1;
+  if (b >= B || !slice_active(nsteps, step, b)) return;   // uniform per block
+  const bool valid = m < g.nm;
   double* X0 = X + (size_t)b * S;
   double* Xo = (stage == 4) ? X0 : Xs + (size_t)b * S;
   const double* Fb = F + (size_t)b * S;
   double* Rb = R + (size_t)b * 4 * S;
-  if (stage == 1 && m == 0 && p == 0 && nu != nullptr) {
+  const int ld = blockDim.x;
+  double* ycol = scol + threadIdx.x;
+  double* rcol = scol + (size_t)g.nq * ld + threadIdx.x;
+  if (stage == 1 && m == 0 && p == 0 && c == 0 && nu != nullptr) {
     // Nu_V(t_n) (Eq. 9) of the step-start state: wall temperature difference of
     // the mean profile + Clenshaw-Curtis integral of <wT>_x; trapezoid weight.
     double cond = 0.0;
@@ -457,40 +582,130 @@ __global__ void k_solve(Grid g, Tables tb, double* X, double* Xs, const double* 
     const double nuv = cond + 0.5 * adv;
     nu[b] += ((*step == 0) ? 0.5 : 1.0) * g.dt * nuv;
   }
-  bool ok;
-  if (m == 0) {
-    ok = solve_system<KT>(g, tb, stage, p, 0, X0, Xo, Fb, Rb, S);
-    ok = solve_system<KU>(g, tb, stage, p, 0, X0, Xo, Fb, Rb, S) && ok;
-  } else {
-    ok = solve_system<KT>(g, tb, stage, p, m, X0, Xo, Fb, Rb, S);
-    ok = solve_system<KP>(g, tb, stage, p, m, X0, Xo, Fb, Rb, S) && ok;
+  bool ok = true;
+  const int mm = valid ? m : 0;
+  if (valid) ok = solve_system<KT>(g, tb, stage, p, mm, c, X0, Xo, Fb, Rb, S, ycol, rcol, ld);
+  __syncwarp();                         // partner lane's T_i is in Xo
+  if (valid) {
+    if (m == 0)
+      ok = solve_system<KU>(g, tb, stage, p, 0, c, X0, Xo, Fb, Rb, S, ycol, rcol, ld) && ok;
+    else
+      ok = solve_system<KP>(g, tb, stage, p, mm, c, X0, Xo, Fb, Rb, S, ycol, rcol, ld) && ok;
   }
   if (!ok) flags[b] = 1;
 }
+
+static int solve_threads(const Grid& g, int B) {
+  int bd = (B * 2 * g.nm >= 152 * 64 * 2) ? 64 : 32;
+  while (bd > 32 && (size_t)bd * 16 * g.nq > 200 * 1024) bd >>= 1;
+  return bd;
+}
+static size_t solve_smem(const Grid& g, int B) { return (size_t)solve_threads(g, B) * 16 * g.nq; }
 
 __global__ void k_advance(int* step) { *step += 1; }
 
 static inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long launches_so_far() { return g_launches.load(); }
+void add_launches(unsigned long long n) { g_launches.fetch_add(n); }
+static inline void count(int n = 1) { g_launches.fetch_add(n); }
+
+cudaError_t Prof::fold() {
+  for (size_t i = 0; i < used; ++i) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(ev[2 * i + 1]);
+    if (e != cudaSuccess) return e;
+    e = cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+    if (e != cudaSuccess) return e;
+    ms[kind[i]] += t;
+  }
+  used = 0;
+  return cudaSuccess;
+}
+
+void Prof::begin(int k, cudaStream_t s) {
+  if (used * 2 + 2 > ev.size()) {
+    if (ev.size() >= 8192) {
+      fold();
+    } else {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ev.push_back(e);
+      }
+      kind.resize(ev.size() / 2);
+    }
+  }
+  kind[used] = k;
+  cudaEventRecord(ev[2 * used], s);
+}
+
+void Prof::end(int k, cudaStream_t s, double fl, double by) {
+  cudaEventRecord(ev[2 * used + 1], s);
+  ++used;
+  launches[k] += 1;
+  flops[k] += fl;
+  bytes[k] += by;
+}
+
+// Algorithmic work of one launch over B slices (all active).
+static double zinv_flops(const Grid& g, int B) { return 24.0 * B * ((g.Mz + 1) / 2) * g.nm * g.Nz; }
+static double zinv_bytes(const Grid& g, int B) {
+  return 8.0 * B * state_doubles(g) + 8.0 * B * z_doubles(g);
+}
+static double rows_flops(const Grid& g, int B) {
+  return (double)B * g.Mz * (6.0 * 5.0 * g.Mx * std::log2((double)g.Mx) + 10.0 * g.Mx);
+}
+static double rows_bytes(const Grid& g, int B) { return 8.0 * B * (z_doubles(g) + q_doubles(g) + g.Mz); }
+static double zfwd_flops(const Grid& g, int B) { return 4.0 * B * g.Nz * g.nm * ((g.Mz + 1) / 2) * 2.0; }
+static double zfwd_bytes(const Grid& g, int B) { return 8.0 * B * (q_doubles(g) + state_doubles(g)); }
+// stage solve: per (m, parity) about 60 flops per coefficient row for T and psi;
+// reads F, X and up to four accumulators, writes X and the accumulators
+static double solve_flops(const Grid& g, int B) { return 120.0 * B * g.nm * 2.0 * g.nq * 2.0; }
+static double solve_bytes(const Grid& g, int B) { return 8.0 * B * state_doubles(g) * 10.0; }
+
 // The dynamic shared-memory allowance of k_rows only ever grows, so that a
 // later handle on a smaller grid does not shrink it below an earlier one's need.
 cudaError_t configure_kernels(const Grid& g) {
-  static int allowed = 48 * 1024;
+  static int allowed_rows = 48 * 1024, allowed_solve = 48 * 1024;
   const int need = (int)rows_smem_bytes(g);
-  if (need <= allowed) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
-  if (e == cudaSuccess) allowed = need;
-  return e;
+  if (need > allowed_rows) {
+    cudaError_t e = cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    if (e != cudaSuccess) return e;
+    allowed_rows = need;
+  }
+  const int need2 = (int)std::max(solve_smem(g, 1), solve_smem(g, 1 << 20));
+  if (need2 > allowed_solve) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, need2);
+    if (e != cudaSuccess) return e;
+    allowed_solve = need2;
+  }
+  static int allowed_zfwd = 48 * 1024;
+  const int need3 = (int)zfwd_smem(g);
+  if (need3 > allowed_zfwd) {
+    cudaError_t e = cudaFuncSetAttribute(k_zfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, need3);
+    if (e != cudaSuccess) return e;
+    allowed_zfwd = need3;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_explicit(const Grid& g, const Tables& t, const Work& w, const double* X, int B, bool all_active,
                             cudaStream_t s) {
   const int* ns = all_active ? nullptr : w.nsteps;
   const size_t S = state_doubles(g);
-  const int T1 = 128;
-  k_zinv<<<nblk((long)B * g.Mz * g.nm, T1), T1, 0, s>>>(g, t.zinv, X, S, w.Z, B, ns, w.step);
+  Prof* pf = (w.prof && w.prof->on && !all_active) ? w.prof : nullptr;
+  const long nz = (long)B * ((g.Mz + 1) / 2) * g.nm;
+  const int T1 = (nz >= 152L * 256) ? 128 : 32;
+  if (pf) pf->begin(RBC_KERNEL_ZINV, s);
+  k_zinv<<<nblk(nz, T1), T1, 0, s>>>(g, t.zinv, X, S, w.Z, B, ns, w.step);
+  if (pf) pf->end(RBC_KERNEL_ZINV, s, zinv_flops(g, B), zinv_bytes(g, B));
   const int T2 = (g.Mx >= 768) ? 256 : 128;
+  if (pf) pf->begin(RBC_KERNEL_ROWS, s);
   k_rows<<<(unsigned)(B * g.Mz), T2, rows_smem_bytes(g), s>>>(g, t.tw, w.Z, w.Q, w.wT, B, ns, w.step);
+  if (pf) pf->end(RBC_KERNEL_ROWS, s, rows_flops(g, B), rows_bytes(g, B));
+  count(2);
   return cudaGetLastError();
 }
 
@@ -500,16 +715,25 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   const double* Xin = (stage == 1) ? X : w.Xs;
   cudaError_t e = launch_explicit(g, t, w, Xin, B, false, s);
   if (e != cudaSuccess) return e;
-  const int T1 = 128;
-  k_zfwd<<<nblk((long)B * 2 * g.Nz * g.nm, T1), T1, 0, s>>>(g, t.zfwd, w.Q, w.F, S, B, w.nsteps, w.step);
-  const int T3 = 64;
-  k_solve<<<nblk((long)B * 2 * g.nm, T3), T3, 0, s>>>(g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags, B, stage,
-                                                      w.nsteps, w.step);
+  Prof* pf = (w.prof && w.prof->on) ? w.prof : nullptr;
+  const int tm = zfwd_tile(g);
+  const int mt = (g.nm + tm - 1) / tm;
+  if (pf) pf->begin(RBC_KERNEL_ZFWD, s);
+  k_zfwd<<<(unsigned)(B * 2 * mt), 128, zfwd_smem(g), s>>>(g, t.zfwd, w.Q, w.F, S, B, tm, w.nsteps, w.step);
+  if (pf) pf->end(RBC_KERNEL_ZFWD, s, zfwd_flops(g, B), zfwd_bytes(g, B));
+  const int T3 = solve_threads(g, B);
+  const int mtiles = (g.nm + T3 / 2 - 1) / (T3 / 2);
+  if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
+  k_solve<<<(unsigned)(B * 2 * mtiles), T3, solve_smem(g, B), s>>>(g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags,
+                                                                   B, stage, w.nsteps, w.step);
+  if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
+  count(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_advance(const Work& w, cudaStream_t s) {
   k_advance<<<1, 1, 0, s>>>(w.step);
+  count();
   return cudaGetLastError();
 }
 
@@ -533,6 +757,7 @@ cudaError_t launch_nu_final(const Grid& g, const Tables& t, const Work& w, const
   cudaError_t e = launch_explicit(g, t, w, X, B, true, s);
   if (e != cudaSuccess) return e;
   k_nu_final<<<nblk(B, 128), 128, 0, s>>>(g, t.cc, X, state_doubles(g), w.wT, nu, w.nsteps, B);
+  count();
   return cudaGetLastError();
 }
 
@@ -559,6 +784,7 @@ cudaError_t launch_nusselt(const Grid& g, const Tables& t, const Work& w, const 
   cudaError_t e = launch_explicit(g, t, w, X, 1, true, s);
   if (e != cudaSuccess) return e;
   k_nusselt<<<1, 32, 0, s>>>(g, t.cc, X, w.wT, out3);
+  count();
   return cudaGetLastError();
 }
 
@@ -594,6 +820,7 @@ cudaError_t launch_l2_diff(const Grid& g, const Tables& t, const double* A, cons
                            cudaStream_t s) {
   if (nst <= 0) return cudaSuccess;
   k_l2_diff<<<nst, 256, 0, s>>>(g, t.gram, A, Bm, out);
+  count();
   return cudaGetLastError();
 }
 
@@ -654,6 +881,7 @@ cudaError_t launch_set_state(const Grid& g, const Tables& t, const double* gT, c
   double* modes = scratch;
   k_grid_to_modes<<<nblk(3L * g.Nz * g.nm, 128), 128, 0, s>>>(g, t.twn, gT, modes);
   k_modes_to_state<<<nblk((long)g.Nz * g.nm, 128), 128, 0, s>>>(g, t.Wn, modes, X);
+  count(2);
   return cudaGetLastError();
 }
 
@@ -709,6 +937,7 @@ cudaError_t launch_get_state(const Grid& g, const Tables& t, const double* X, do
   double* modes = scratch;
   k_state_to_modes<<<nblk((long)g.Nz * g.nm, 128), 128, 0, s>>>(g, t.Vn, t.Vn1, X, modes);
   k_modes_to_grid<<<nblk(3L * g.Nz * g.Nx, 128), 128, 0, s>>>(g, t.twn, modes, gT);
+  count(2);
   return cudaGetLastError();
 }
 
@@ -726,6 +955,7 @@ __global__ void k_restrict(Grid gf, Grid gc, const double* Xf, double* Xc) {
 
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const double* Xf, double* Xc, cudaStream_t s) {
   k_restrict<<<nblk(2L * gc.Nz * gc.nm, 128), 128, 0, s>>>(gf, gc, Xf, Xc);
+  count();
   return cudaGetLastError();
 }
 
@@ -742,6 +972,7 @@ __global__ void k_prolong(Grid gf, Grid gc, const double* Xc, double* Xf) {
 
 cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, cudaStream_t s) {
   k_prolong<<<nblk(2L * gf.Nz * gf.nm, 128), 128, 0, s>>>(gf, gc, Xc, Xf);
+  count();
   return cudaGetLastError();
 }
 
@@ -760,6 +991,7 @@ __global__ void k_correct(Grid gf, Grid gc, const double* Ff, const double* Gnew
 cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, const double* Gnew, const double* Gold,
                            double* Uout, cudaStream_t s) {
   k_correct<<<nblk(2L * gf.Nz * gf.nm, 128), 128, 0, s>>>(gf, gc, Ff, Gnew, Gold, Uout);
+  count();
   return cudaGetLastError();
 }
 

@@ -19,8 +19,10 @@ CRIT_FIXED, CRIT_DEFECT, CRIT_NU = 0, 1, 2
 EXPORTS = [
     "rbc_last_error", "rbc_create", "rbc_destroy", "rbc_state_bytes", "rbc_workspace_bytes_per_state",
     "rbc_reserve", "rbc_set_state", "rbc_get_state", "rbc_step_batch", "rbc_check_diverged", "rbc_nusselt",
-    "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate",
+    "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate", "rbc_profile",
+    "rbc_profile_read", "rbc_launch_count",
 ]
+KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
 
 class RBCError(RuntimeError):
@@ -62,6 +64,9 @@ def load():
         "parareal_create": (I, [P, P, D, D, I, I, D, ctypes.POINTER(P)]),
         "parareal_destroy": (None, [P]),
         "parareal_iterate": (I, [P, P, P, I, PI, PD, PD, P]),
+        "rbc_profile": (I, [P, I]),
+        "rbc_profile_read": (I, [P, PD, ctypes.POINTER(ctypes.c_longlong), PD, PD]),
+        "rbc_launch_count": (ctypes.c_ulonglong, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -162,10 +167,23 @@ class Propagator:
         _check(load().rbc_nusselt(self.h, _ptr(state), _dptr(out), _stream(stream)))
         return tuple(out)
 
+    def profile(self, enable=True):
+        _check(load().rbc_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms, fl, by = np.zeros(4), np.zeros(4), np.zeros(4)
+        n = (ctypes.c_longlong * 4)()
+        _check(load().rbc_profile_read(self.h, _dptr(ms), n, _dptr(fl), _dptr(by)))
+        return {KERNEL_NAMES[k]: dict(ms=ms[k], launches=n[k], flops=fl[k], bytes=by[k]) for k in range(4)}
+
     def l2_temperature(self, state, stream=None):
         out = np.zeros(1)
         _check(load().rbc_l2_temperature(self.h, _ptr(state), _dptr(out), _stream(stream)))
         return float(out[0])
+
+
+def launch_count():
+    return int(load().rbc_launch_count())
 
 
 def coarse_dt(slice_length, dt_requested):
