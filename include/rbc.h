@@ -116,6 +116,26 @@ rbc_status rbc_check_diverged(rbc_t h, cudaStream_t stream);
  * written to host out[3].  Synchronous on `stream`.                         */
 rbc_status rbc_nusselt(rbc_t h, const void* d_state, double out[3], cudaStream_t stream);
 
+/* rbc_nusselt_static: the same three Nusselt numbers as rbc_nusselt, from a
+ * call that allocates no device memory.  The paper has no counterpart: this
+ * exists for callers that cannot allocate when they ask for a diagnostic, for
+ * example an application whose pool allocator already owns the free device
+ * memory (a raw cudaMalloc from the library would then fail), or a timed loop
+ * that cannot afford the device synchronisation cudaMalloc/cudaFree may cause.
+ * rbc_nusselt may grow the handle's workspace on first use; this call never
+ * does: its scratch (about 132 * Nx * Nz bytes) lives in one file-scope
+ * device array of 3 MiB that every GPU loading the library keeps until the
+ * process exits.  Grids needing more scratch than that (Nx * Nz above about
+ * 23000, e.g. 256 x 128) return RBC_EINVAL and do nothing.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  Every element a call reads is written by that call first, so no
+ * clearing is needed and the leftover contents of an earlier call do not
+ * matter.  Synchronous on `stream`; out[3] = (Nu_V, Nu_b, Nu_t) on the host. */
+rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double out[3], cudaStream_t stream);
+
 /* ||T||_{L2(Omega)} of one device state (exact in x and z), host out.       */
 rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream);
 

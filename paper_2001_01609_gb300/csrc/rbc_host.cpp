@@ -723,6 +723,16 @@ extern "C" rbc_status rbc_nusselt(rbc_t h, const void* d_state, double out[3], c
   return RBC_OK;
 }
 
+extern "C" rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double out[3], cudaStream_t stream) {
+  if (!h || !d_state || !out) return fail(RBC_EINVAL, "null argument");
+  const size_t need = static_scratch_doubles_needed(h->g);
+  if (need > kStaticScratchCapacity)
+    return fail(RBC_EINVAL, "grid %dx%d needs %zu doubles of scratch; the static array holds %zu (3 MiB)",
+                h->g.Nx, h->g.Nz, need, kStaticScratchCapacity);
+  CK(launch_nusselt_static(h->g, h->t, static_cast<const double*>(d_state), out, stream));
+  return RBC_OK;
+}
+
 extern "C" rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream) {
   if (!h || !d_state || !out) return fail(RBC_EINVAL, "null argument");
   rbc_status s = rbc_reserve(h, 1);

@@ -108,6 +108,10 @@ cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, con
                            const double* Gold, double* Uout, cudaStream_t s);
 cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, cudaStream_t s);
 size_t rows_smem_bytes(const Grid& g);
+size_t static_scratch_doubles_needed(const Grid& g);
+constexpr size_t kStaticScratchCapacity = (size_t)3 << 17;   // doubles in the static scratch array
+cudaError_t launch_nusselt_static(const Grid& g, const Tables& t, const double* X, double* host_out3,
+                                  cudaStream_t s);
 unsigned long long launches_so_far();
 void add_launches(unsigned long long n);   // kernels launched through a replayed graph
 constexpr int kStepKernels = 17;           // 4 stages x 4 kernels + step counter

@@ -995,4 +995,46 @@ cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, con
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Nusselt numbers without any allocation: the scratch of the explicit-term
+// evaluation (z-inverse fields, row outputs, the <wT>_x profile and the three
+// results) lives in one file-scope device array, shared by every call on a
+// device.  Its device address is looked up once per device, with that device
+// current, on the first call there.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchDoubles = (size_t)3 << 17;   // 3 MiB
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+constexpr int kMaxDevices = 64;
+static double* g_static_ptr[kMaxDevices] = {};
+
+size_t static_scratch_doubles_needed(const Grid& g) {
+  return z_doubles(g) + q_doubles(g) + (size_t)((g.Mz + 1) & ~1) + 8;
+}
+
+cudaError_t launch_nusselt_static(const Grid& g, const Tables& t, const double* X, double* host_out3,
+                                  cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (g_static_ptr[dev] == nullptr) {
+    double* ptr = nullptr;
+    e = cudaGetSymbolAddress((void**)&ptr, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = ptr;
+  }
+  double* base = g_static_ptr[dev];
+  Work w{};
+  w.Z = base;
+  w.Q = w.Z + z_doubles(g);
+  w.wT = w.Q + q_doubles(g);
+  w.small = w.wT + ((g.Mz + 1) & ~1);
+  w.prof = nullptr;
+  e = launch_nusselt(g, t, w, X, w.small, s);       // every element it reads is written first
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(host_out3, w.small, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
 }  // namespace rbc

@@ -20,7 +20,7 @@ EXPORTS = [
     "rbc_last_error", "rbc_create", "rbc_destroy", "rbc_state_bytes", "rbc_workspace_bytes_per_state",
     "rbc_reserve", "rbc_set_state", "rbc_get_state", "rbc_step_batch", "rbc_check_diverged", "rbc_nusselt",
     "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate", "rbc_profile",
-    "rbc_profile_read", "rbc_launch_count",
+    "rbc_profile_read", "rbc_launch_count", "rbc_nusselt_static",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -67,6 +67,7 @@ def load():
         "rbc_profile": (I, [P, I]),
         "rbc_profile_read": (I, [P, PD, ctypes.POINTER(ctypes.c_longlong), PD, PD]),
         "rbc_launch_count": (ctypes.c_ulonglong, []),
+        "rbc_nusselt_static": (I, [P, P, PD, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
