@@ -280,6 +280,31 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+NCU_CASES = {
+    # name: (Ra, Nx, Nz, dt, B) -- one RK443 step without graphs, for ncu captures
+    "fine_b32": (1e6, 256, 64, 1.25e-5, 32),
+    "coarse_b1": (1e6, 128, 32, 1.5625e-5, 1),
+}
+
+
+def run_ncu_case(name):
+    """One plain (graph-free) RK443 step of a batch: a small, self-ending case for ncu."""
+    import torch
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc
+    from paper_2001_01609_gb300.inputs import initial_temperature
+    Ra, Nx, Nz, dt, B = NCU_CASES[name]
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt)
+    st = F.new_states(B)
+    for b in range(B):
+        F.set_state(st[b], initial_temperature(Nx, Nz, seed=b, amplitude=0.3))
+    F.step_batch(st, 1)
+    torch.cuda.synchronize()
+    assert F.check_diverged() == rbc.RBC_OK
+    print(f"ncu case {name} ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,7 +313,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
     args = ap.parse_args()
+    if args.ncu_case:
+        run_ncu_case(args.ncu_case)
+        return
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)

@@ -120,6 +120,7 @@ __global__ void k_zinv(Grid g, const double* __restrict__ Bz, const double* __re
   double2 E[6], O[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) E[q] = O[q] = make_double2(0.0, 0.0);
+#pragma unroll 4
   for (int n = 0; n < g.Nz; n += 2) {                  // Nz is even
 #pragma unroll
     for (int par = 0; par < 2; ++par) {
@@ -159,7 +160,7 @@ __global__ void k_zinv(Grid g, const double* __restrict__ Bz, const double* __re
 // 4, ..., 4, [2], 3).  y_q = sum_r x_r exp(sign 2 pi i q r / N), unnormalised.
 // Ping-pongs between a and b; returns the buffer holding the result.
 // ---------------------------------------------------------------------------
-__device__ double2* fft_smem(double2* a, double2* b, int N, int sign, const double2* __restrict__ tw) {
+__device__ double2* fft_smem(double2* a, double2* b, int N, int sign, const double2* tw) {
   int p = 0;
   for (int M = N / 3; M > 1; M >>= 1) ++p;
   int nr = p / 2 + (p & 1) + 1;
@@ -177,7 +178,7 @@ __device__ double2* fft_smem(double2* a, double2* b, int N, int sign, const doub
       for (int r = 0; r < R; ++r) v[r] = x[jj + r * nb];
       if (Ns > 1) {
         for (int r = 1; r < R; ++r) {
-          double2 wv = __ldg(tw + (k * r * stride) % N);
+          double2 wv = tw[(k * r * stride) % N];
           if (sign > 0) wv.y = -wv.y;
           v[r] = cmul(v[r], wv);
         }
@@ -212,7 +213,7 @@ __device__ double2* fft_smem(double2* a, double2* b, int N, int sign, const doub
   return x;
 }
 
-size_t rows_smem_bytes(const Grid& g) { return (size_t)g.Mx * (2 * 16 + 9 * 8); }
+size_t rows_smem_bytes(const Grid& g) { return (size_t)g.Mx * (3 * 16 + 9 * 8); }
 
 // Deterministic block sum (fixed tree over blockDim.x threads, blockDim a power of two).
 __device__ double block_sum(double v, double* red) {
@@ -245,8 +246,10 @@ __global__ void __launch_bounds__(256) k_rows(Grid g, const double2* __restrict_
   const int Mx = g.Mx, nm = g.nm;
   double2* A = reinterpret_cast<double2*>(sm);
   double2* Bf = A + Mx;
-  double* fr = reinterpret_cast<double*>(Bf + Mx);
+  double2* tws = Bf + Mx;                              // twiddles, staged once per block
+  double* fr = reinterpret_cast<double*>(tws + Mx);
   __shared__ double red[256];
+  for (int x = threadIdx.x; x < Mx; x += blockDim.x) tws[x] = __ldg(tw + x);
   const size_t fs = (size_t)g.Mz * nm * 2;
   const double* zrow = Z + (size_t)b * 9 * fs + (size_t)j * nm * 2;
   for (int pr = 0; pr < 5; ++pr) {
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(256) k_rows(Grid g, const double2* __restrict_
       A[x] = c;
     }
     __syncthreads();
-    const double2* res = fft_smem(A, Bf, Mx, +1, tw);
+    const double2* res = fft_smem(A, Bf, Mx, +1, tws);
     for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
       fr[fa * Mx + x] = res[x].x;
       if (fb < 9) fr[fb * Mx + x] = res[x].y;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(256) k_rows(Grid g, const double2* __restrict_
   __syncthreads();
   const double sU = block_sum(nU, red);
   const double sW = block_sum(wt, red);
-  const double2* C = fft_smem(A, Bf, Mx, -1, tw);
+  const double2* C = fft_smem(A, Bf, Mx, -1, tws);
   const double inv = 1.0 / Mx;
   const size_t qs = (size_t)g.Mz * nm * 2;
   double* q0 = Q + (size_t)b * 2 * qs + (size_t)j * nm * 2;
@@ -350,6 +353,7 @@ __global__ void k_zfwd(Grid g, const double* __restrict__ W, const double* __res
     const double2* src = fold + (size_t)((n & 1) ? Mh : 0) * tm + mi;
     const double* wr = W + (size_t)n * g.Mz;
     double2 acc = {0.0, 0.0};
+#pragma unroll 4
     for (int jh = 0; jh < Mh; ++jh) {
       const double wv = __ldg(wr + jh);
       const double2 v = src[(size_t)jh * tm];
@@ -360,132 +364,135 @@ __global__ void k_zfwd(Grid g, const double* __restrict__ W, const double* __res
   }
 }
 
-static int zfwd_tile(const Grid& g) {
+static int zfwd_tile(const Grid& g, int B) {
   const int Mh = (g.Mz + 1) / 2;
   int tm = 32;
+  while (tm > 4 && (size_t)B * 2 * ((g.nm + tm - 1) / tm) < 2 * 152) tm >>= 1;
   while (tm > 4 && (size_t)2 * Mh * tm * 16 > 200 * 1024) tm >>= 1;
   return tm;
 }
-static size_t zfwd_smem(const Grid& g) { return (size_t)2 * ((g.Mz + 1) / 2) * zfwd_tile(g) * 16; }
+static size_t zfwd_smem(const Grid& g, int B) { return (size_t)2 * ((g.Mz + 1) / 2) * zfwd_tile(g, B) * 16; }
 
 // ---------------------------------------------------------------------------
-// Stage solve (k_solve).  Thread per (slice, Fourier mode m, Chebyshev parity
-// p, real/imaginary part c): the stage matrices are real, so the real and the
-// imaginary parts are independent systems, except for the implicit buoyancy
-// coupling -i k Pr Ra T, which feeds the imaginary part of T into the real
-// part of psi and the real part into the imaginary one; the two parts of one
-// mode sit on adjacent lanes and exchange T through memory after a warp
-// barrier.  T first, then psi (m >= 1) or the mean flow U (m = 0).  The stage
-// right-hand side is assembled in chunks of CH tau rows whose loads are issued
-// together; the elimination vectors live in this thread's shared-memory
-// columns, so the sequential recurrences never wait on global memory.
+// Stage solve (k_solve).  Block per (slice, Chebyshev parity p, tile of tms
+// Fourier modes); a column is one (mode m, real/imaginary part c) pair -- the
+// stage matrices are real, so the two parts are independent systems except for
+// the implicit buoyancy coupling -i k Pr Ra T (the imaginary part of T feeds
+// the real part of psi and vice versa).  Per system (T first, then psi for
+// m >= 1 or the mean flow U for m = 0):
+//   phase 1 (all threads, one tau row of one column each): right-hand side of
+//           the stage, updates of the later RK accumulators;
+//   phase 2 (one thread per column): backward elimination with the UL factors;
+//   phase 3 (same thread): boundary block, forward substitution;
+//   phase 4 (all threads): dt L X_i = 2 (M X_i - r_i) into later accumulators.
+// Inputs are staged in shared memory with coalesced loads, so the sequential
+// phases never wait on global memory.
 // ---------------------------------------------------------------------------
 enum { KT = 0, KP = 1, KU = 2 };
-constexpr int CH = 4;
 
-// One parity-split system of one field for one (slice, m, p, c).
-//   tau row t (full row 2t+p) of (M - dt/2 L) X_i = r_i, boundary rows on top;
-//   r_i = M X_0 + dt sum_{j<i} (aE_ij F_j + aI_ij L X_j) is kept in
-//   accumulators R_l (complete for l = i when stage i starts), and
-//   dt L X_i = 2 (M X_i - r_i) feeds the later accumulators.
-// ycol/rcol: this thread's shared-memory columns, element q at [q * ld].
+struct SolveSmem {
+  double* F;    // [nq][W] explicit-term coefficients of the system's field
+  double* X;    // [nq][W] step-start state (stage 1)
+  double* y;    // [nq][W] right-hand side, then solution
+  double* r;    // [nq][W] r_i of the tau rows
+  double* T;    // [nq][W] T_i, kept for the psi coupling
+  int W;        // columns = 2 * tms
+};
+
 template <int KIND>
-__device__ bool solve_system(const Grid& g, const Tables& tb, int stage, int p, int m, int c,
-                             const double* __restrict__ X0, double* __restrict__ Xo,
-                             const double* __restrict__ Fc, double* __restrict__ R, size_t S, double* ycol,
-                             double* rcol, int ld) {
-  constexpr int D = (KIND == KP) ? 2 : 1;
-  constexpr int LAM = 2 * D;
-  const int nq = g.nq, nt = nq - D;
+struct Sys {
+  static constexpr int D = (KIND == KP) ? 2 : 1;
+  static constexpr int LAM = 2 * D;
+  static __device__ __forceinline__ const double* multB(const Tables& tb) {
+    return KIND == KT ? tb.T_multB : KIND == KP ? tb.P_multB : tb.U_multB;
+  }
+  static __device__ __forceinline__ const double* multD(const Tables& tb) {
+    return KIND == KT ? tb.T_multD : KIND == KP ? tb.P_multD : tb.U_multD;
+  }
+  static __device__ __forceinline__ const double* Dinv(const Tables& tb) {
+    return KIND == KT ? tb.T_Dinv : KIND == KP ? tb.P_Dinv : tb.U_Dinv;
+  }
+  static __device__ __forceinline__ const double* Lb(const Tables& tb) {
+    return KIND == KT ? tb.T_Lb : KIND == KP ? tb.P_Lb : tb.U_Lb;
+  }
+  static __device__ __forceinline__ const double* invd(const Tables& tb) {
+    return KIND == KT ? tb.T_invd : KIND == KP ? tb.P_invd : tb.U_invd;
+  }
+  static __device__ __forceinline__ double tapF(const Grid& g, const Tables& tb, int p, int t, int j) {
+    return KIND == KP ? __ldg(tb.s4 + (p * g.nq + t) * 5 + j) : __ldg(tb.s2 + (p * g.nq + t) * 3 + j);
+  }
+  static __device__ __forceinline__ double tapM(const Grid& g, const Tables& tb, int p, int t, int j, int m) {
+    return KIND == KP ? __ldg(tb.mp + ((size_t)(p * g.nq + t) * 5 + j) * g.nm + m)
+                      : __ldg(tb.s2 + (p * g.nq + t) * 3 + j);
+  }
+};
+
+// phase 1 for one (tau row t, column col)
+template <int KIND>
+__device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int stage, int p, int m, int c, int t,
+                                          int col, const SolveSmem& sm, double* __restrict__ R, size_t S) {
+  using SY = Sys<KIND>;
+  const int nq = g.nq, W = sm.W;
+  const int f = (KIND == KT) ? 0 : 1;
+  double fv = 0.0;
+#pragma unroll
+  for (int j = 0; j <= SY::LAM; ++j)
+    if (t + j < nq) fv = fma(SY::tapF(g, tb, p, t, j), sm.F[(t + j) * W + col], fv);
+  if (KIND != KP) fv = -fv;
+  const double dt = g.dt;
+  const size_t ro = soff(g, f, 2 * t + p, m) + c;
+  double r;
+  if (stage == 1) {
+    double mx = 0.0;
+#pragma unroll
+    for (int j = 0; j <= SY::LAM; ++j)
+      if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), sm.X[(t + j) * W + col], mx);
+    r = fma(dt * c_AE[1][0], fv, mx);
+#pragma unroll
+    for (int l = 2; l <= 4; ++l) R[(size_t)(l - 1) * S + ro] = fma(dt * c_AE[l][0], fv, mx);
+  } else {
+    double Rl[3];
+    const double Ri = R[(size_t)(stage - 1) * S + ro];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) Rl[l] = (l + 2 > stage) ? R[(size_t)(l + 1) * S + ro] : 0.0;
+    r = fma(dt * c_AE[stage][stage - 1], fv, Ri);
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      if (l + 2 > stage) R[(size_t)(l + 1) * S + ro] = fma(dt * c_AE[l + 2][stage - 1], fv, Rl[l]);
+  }
+  sm.r[t * W + col] = r;
+  double bv = r;
+  if (KIND == KP) {
+    // + dt/2 (-i k Pr Ra) S4 T_i: real part + k.. Im(S4 T), imaginary part - k.. Re(S4 T)
+    double st = 0.0;
+#pragma unroll
+    for (int j = 0; j <= 4; ++j)
+      if (t + j < nq) st = fma(__ldg(tb.s4 + (p * nq + t) * 5 + j), sm.T[(t + j) * W + (col ^ 1)], st);
+    const double cpl = (c == 0 ? 1.0 : -1.0) * 0.5 * dt * g.Pr * g.Ra * (g.kfac * m);
+    bv = fma(cpl, st, bv);
+  }
+  sm.y[(t + SY::D) * W + col] = bv;
+}
+
+// phases 2 and 3 for one column
+template <int KIND>
+__device__ __forceinline__ bool solve_recurrence(const Grid& g, const Tables& tb, int p, int m, int c, int col,
+                                                 const SolveSmem& sm, double* __restrict__ Xo) {
+  using SY = Sys<KIND>;
+  constexpr int D = SY::D;
+  const int nq = g.nq, W = sm.W;
   const int f = (KIND == KT) ? 0 : 1;
   const int nmod = (KIND == KU) ? 1 : g.nm;
   const int mi = (KIND == KU) ? 0 : m;
-  const double* multB = (KIND == KT) ? tb.T_multB : (KIND == KP) ? tb.P_multB : tb.U_multB;
-  const double* multD = (KIND == KT) ? tb.T_multD : (KIND == KP) ? tb.P_multD : tb.U_multD;
-  const double* Dinv = (KIND == KT) ? tb.T_Dinv : (KIND == KP) ? tb.P_Dinv : tb.U_Dinv;
-  const double* Lb = (KIND == KT) ? tb.T_Lb : (KIND == KP) ? tb.P_Lb : tb.U_Lb;
-  const double* invd = (KIND == KT) ? tb.T_invd : (KIND == KP) ? tb.P_invd : tb.U_invd;
+  const double* multB = SY::multB(tb);
+  const double* multD = SY::multD(tb);
   auto tix = [&](int cc, int jj) { return ((size_t)(p * nq + cc) * D + jj) * nmod + mi; };
-  auto co = [&](int n) { return soff(g, f, n, m) + c; };
-  auto tapF = [&](int t, int jj) -> double {
-    return (KIND == KP) ? __ldg(tb.s4 + (p * nq + t) * 5 + jj) : __ldg(tb.s2 + (p * nq + t) * 3 + jj);
-  };
-  auto tapM = [&](int t, int jj) -> double {
-    return (KIND == KP) ? __ldg(tb.mp + ((size_t)(p * nq + t) * 5 + jj) * g.nm + m)
-                        : __ldg(tb.s2 + (p * nq + t) * 3 + jj);
-  };
-  const double fsign = (KIND == KP) ? 1.0 : -1.0;
-  const double dt = g.dt;
-  // + dt/2 (-i k Pr Ra) S4 T_i: real part gets +k.. Im(S4 T), imaginary part -k.. Re(S4 T)
-  const double cpl = (c == 0 ? 1.0 : -1.0) * 0.5 * dt * g.Pr * g.Ra * (g.kfac * m);
-  const double aEi = dt * c_AE[stage][stage - 1];
-
-  // phase 1: right-hand side of every tau row, accumulator updates for later stages
-  for (int t0 = 0; t0 < nt; t0 += CH) {
-    double Fw[CH + LAM], Xw[CH + LAM], Tw[CH + 4], Ri[CH], Rl[3][CH];
-#pragma unroll
-    for (int j = 0; j < CH + LAM; ++j) {
-      const int q = t0 + j;
-      Fw[j] = (q < nq) ? __ldg(Fc + co(2 * q + p)) : 0.0;
-      Xw[j] = (stage == 1 && q < nq) ? __ldg(X0 + co(2 * q + p)) : 0.0;
-    }
-    if (KIND == KP) {
-#pragma unroll
-      for (int j = 0; j < CH + 4; ++j) {
-        const int q = t0 + j;
-        Tw[j] = (q < nq) ? Xo[soff(g, 0, 2 * q + p, m) + (1 - c)] : 0.0;
-      }
-    }
-#pragma unroll
-    for (int cc = 0; cc < CH; ++cc) {
-      const int t = t0 + cc;
-      const size_t ro = co(2 * (t < nt ? t : 0) + p);
-      Ri[cc] = (stage > 1 && t < nt) ? R[(size_t)(stage - 1) * S + ro] : 0.0;
-#pragma unroll
-      for (int l = 0; l < 3; ++l)
-        Rl[l][cc] = (stage > 1 && t < nt && l + 2 > stage) ? R[(size_t)(l + 1) * S + ro] : 0.0;
-    }
-#pragma unroll
-    for (int cc = 0; cc < CH; ++cc) {
-      const int t = t0 + cc;
-      if (t >= nt) break;
-      double fv = 0.0;
-#pragma unroll
-      for (int jj = 0; jj <= LAM; ++jj) fv = fma(tapF(t, jj), Fw[cc + jj], fv);
-      fv *= fsign;
-      const size_t ro = co(2 * t + p);
-      double r;
-      if (stage == 1) {
-        double mx = 0.0;
-#pragma unroll
-        for (int jj = 0; jj <= LAM; ++jj) mx = fma(tapM(t, jj), Xw[cc + jj], mx);
-        r = fma(dt * c_AE[1][0], fv, mx);
-#pragma unroll
-        for (int l = 2; l <= 4; ++l) R[(size_t)(l - 1) * S + ro] = fma(dt * c_AE[l][0], fv, mx);
-      } else {
-        r = fma(aEi, fv, Ri[cc]);
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-          if (l + 2 > stage) R[(size_t)(l + 1) * S + ro] = fma(dt * c_AE[l + 2][stage - 1], fv, Rl[l][cc]);
-      }
-      rcol[t * ld] = r;
-      double bv = r;
-      if (KIND == KP) {
-        double st = 0.0;
-#pragma unroll
-        for (int jj = 0; jj <= 4; ++jj) st = fma(__ldg(tb.s4 + (p * nq + t) * 5 + jj), Tw[cc + jj], st);
-        bv = fma(cpl, st, bv);
-      }
-      ycol[(t + D) * ld] = bv;
-    }
-  }
-  // phase 2: backward elimination of the upper band (UL factors)
   double pend[D], bd[D];
 #pragma unroll
   for (int jj = 0; jj < D; ++jj) pend[jj] = bd[jj] = 0.0;
   for (int cc = nq - 1; cc >= D; --cc) {
-    const double bc = ycol[cc * ld] + pend[0];
-    ycol[cc * ld] = bc;
+    const double bc = sm.y[cc * W + col] + pend[0];
+    sm.y[cc * W + col] = bc;
 #pragma unroll
     for (int jj = 0; jj < D - 1; ++jj) pend[jj] = fma(-__ldg(multB + tix(cc, D - 1 - jj)), bc, pend[jj + 1]);
     pend[D - 1] = -__ldg(multB + tix(cc, 0)) * bc;
@@ -494,7 +501,9 @@ __device__ bool solve_system(const Grid& g, const Tables& tb, int stage, int p, 
   }
   // boundary rows (Eq. 6): parity combinations of f(1) +- f(-1)
   if (KIND == KT && m == 0 && c == 0) bd[0] += (p == 0) ? 0.5 : -0.5;   // T(-1/2) = 1, T(1/2) = 0
-  // phase 3: dense boundary block, forward substitution with the lower band
+  const double* Dinv = SY::Dinv(tb);
+  const double* Lb = SY::Lb(tb);
+  const double* invd = SY::invd(tb);
   double win[D];
   bool ok = true;
 #pragma unroll
@@ -503,104 +512,150 @@ __device__ bool solve_system(const Grid& g, const Tables& tb, int stage, int p, 
 #pragma unroll
     for (int c2 = 0; c2 < D; ++c2) x = fma(__ldg(Dinv + ((size_t)(p * D * D) + r2 * D + c2) * nmod + mi), bd[c2], x);
     win[r2] = x;
-    ycol[r2 * ld] = x;
-    Xo[co(2 * r2 + p)] = x;
+    sm.y[r2 * W + col] = x;
+    Xo[soff(g, f, 2 * r2 + p, m) + c] = x;
+    if (KIND == KT) sm.T[r2 * W + col] = x;
     ok = ok && isfinite(x);
   }
   for (int r2 = D; r2 < nq; ++r2) {
-    double y = ycol[r2 * ld];
+    double y = sm.y[r2 * W + col];
 #pragma unroll
     for (int jj = 0; jj < D; ++jj) y = fma(-__ldg(Lb + tix(r2, jj)), win[jj], y);
     const double x = __ldg(invd + (size_t)(p * nq + r2) * nmod + mi) * y;
-    ycol[r2 * ld] = x;
-    Xo[co(2 * r2 + p)] = x;
+    sm.y[r2 * W + col] = x;
+    Xo[soff(g, f, 2 * r2 + p, m) + c] = x;
+    if (KIND == KT) sm.T[r2 * W + col] = x;
 #pragma unroll
     for (int jj = 0; jj < D - 1; ++jj) win[jj] = win[jj + 1];
     win[D - 1] = x;
     ok = ok && isfinite(x);
   }
-  // phase 4: dt aI_li L X_i = 2 aI_li (M X_i - r_i) into later accumulators
-  if (stage < 4) {
-    for (int t0 = 0; t0 < nt; t0 += CH) {
-      double Rl[3][CH];
-#pragma unroll
-      for (int cc = 0; cc < CH; ++cc) {
-        const int t = t0 + cc;
-        const size_t ro = co(2 * (t < nt ? t : 0) + p);
-#pragma unroll
-        for (int l = 0; l < 3; ++l) Rl[l][cc] = (t < nt && l + 2 > stage) ? R[(size_t)(l + 1) * S + ro] : 0.0;
-      }
-#pragma unroll
-      for (int cc = 0; cc < CH; ++cc) {
-        const int t = t0 + cc;
-        if (t >= nt) break;
-        double mx = 0.0;
-#pragma unroll
-        for (int jj = 0; jj <= LAM; ++jj) {
-          const int q = t + jj;
-          if (q < nq) mx = fma(tapM(t, jj), ycol[q * ld], mx);
-        }
-        const double lx2 = 2.0 * (mx - rcol[t * ld]);
-        const size_t ro = co(2 * t + p);
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-          if (l + 2 > stage) R[(size_t)(l + 1) * S + ro] = fma(c_AI[l + 2][stage], lx2, Rl[l][cc]);
-      }
-    }
-  }
   return ok;
 }
 
-// Block = solve_threads(g) threads = (modes) x (real, imaginary) of one (slice, parity).
-__global__ void k_solve(Grid g, Tables tb, double* X, double* Xs, const double* F, double* R, size_t S,
-                        const double* wT, double* nu, int* flags, int B, int stage, const int* nsteps,
-                        const int* step) {
-  extern __shared__ double scol[];
-  const int per_blk = blockDim.x / 2;
-  const int mtiles = (g.nm + per_blk - 1) / per_blk;
-  const int b = blockIdx.x / (2 * mtiles);
-  const int rem = blockIdx.x - b * 2 * mtiles;
-  const int p = rem / mtiles;
-  const int m = (rem - p * mtiles) * per_blk + (int)threadIdx.x / 2;
-  const int c = threadIdx.x & 1;
+// phase 4 for one (tau row t, column col)
+template <int KIND>
+__device__ __forceinline__ void solve_lx(const Grid& g, const Tables& tb, int stage, int p, int m, int c, int t,
+                                         int col, const SolveSmem& sm, double* __restrict__ R, size_t S) {
+  using SY = Sys<KIND>;
+  const int nq = g.nq, W = sm.W;
+  const int f = (KIND == KT) ? 0 : 1;
+  double mx = 0.0;
+#pragma unroll
+  for (int j = 0; j <= SY::LAM; ++j)
+    if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), sm.y[(t + j) * W + col], mx);
+  const double lx2 = 2.0 * (mx - sm.r[t * W + col]);
+  const size_t ro = soff(g, f, 2 * t + p, m) + c;
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+    if (l + 2 > stage) {
+      double* Rl = R + (size_t)(l + 1) * S + ro;
+      *Rl = fma(c_AI[l + 2][stage], lx2, *Rl);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, double* Xs, const double* F, double* R,
+                                               size_t S, const double* wT, double* nu, int* flags, int B, int stage,
+                                               int tms, const int* nsteps, const int* step) {
+  extern __shared__ double sbuf[];
+  const int mt = (g.nm + tms - 1) / tms;
+  const int b = blockIdx.x / (2 * mt);
+  const int rem = blockIdx.x - b * 2 * mt;
+  const int p = rem / mt;
+  const int m0 = (rem - p * mt) * tms;
   if (b >= B || !slice_active(nsteps, step, b)) return;   // uniform per block
-  const bool valid = m < g.nm;
+  const int nq = g.nq;
+  const int W = 2 * tms;
+  const int ncol = 2 * min(tms, g.nm - m0);
+  SolveSmem sm;
+  sm.W = W;
+  sm.F = sbuf;
+  sm.X = sm.F + (size_t)nq * W;
+  sm.y = sm.X + (size_t)nq * W;
+  sm.r = sm.y + (size_t)nq * W;
+  sm.T = sm.r + (size_t)nq * W;
   double* X0 = X + (size_t)b * S;
   double* Xo = (stage == 4) ? X0 : Xs + (size_t)b * S;
   const double* Fb = F + (size_t)b * S;
   double* Rb = R + (size_t)b * 4 * S;
-  const int ld = blockDim.x;
-  double* ycol = scol + threadIdx.x;
-  double* rcol = scol + (size_t)g.nq * ld + threadIdx.x;
-  if (stage == 1 && m == 0 && p == 0 && c == 0 && nu != nullptr) {
+  if (stage == 1 && m0 == 0 && p == 0 && threadIdx.x == 0 && nu != nullptr) {
     // Nu_V(t_n) (Eq. 9) of the step-start state: wall temperature difference of
     // the mean profile + Clenshaw-Curtis integral of <wT>_x; trapezoid weight.
     double cond = 0.0;
     for (int n = 1; n < g.Nz; n += 2) cond -= 2.0 * X0[soff(g, 0, n, 0)];
     double adv = 0.0;
     for (int jz = 0; jz < g.Mz; ++jz) adv = fma(__ldg(tb.cc + jz), wT[(size_t)b * g.Mz + jz], adv);
-    const double nuv = cond + 0.5 * adv;
-    nu[b] += ((*step == 0) ? 0.5 : 1.0) * g.dt * nuv;
+    nu[b] += ((*step == 0) ? 0.5 : 1.0) * g.dt * (cond + 0.5 * adv);
   }
   bool ok = true;
-  const int mm = valid ? m : 0;
-  if (valid) ok = solve_system<KT>(g, tb, stage, p, mm, c, X0, Xo, Fb, Rb, S, ycol, rcol, ld);
-  __syncwarp();                         // partner lane's T_i is in Xo
-  if (valid) {
-    if (m == 0)
-      ok = solve_system<KU>(g, tb, stage, p, 0, c, X0, Xo, Fb, Rb, S, ycol, rcol, ld) && ok;
-    else
-      ok = solve_system<KP>(g, tb, stage, p, mm, c, X0, Xo, Fb, Rb, S, ycol, rcol, ld) && ok;
+  for (int sys = 0; sys < 2; ++sys) {
+    const int f = sys;                               // field 0 = T, 1 = psi / U
+    // stage the field's coefficients of this parity and tile
+    for (int it = threadIdx.x; it < nq * W; it += blockDim.x) {
+      const int q = it / W, col = it - q * W;
+      double fv = 0.0, xv = 0.0;
+      if (col < ncol) {
+        const size_t o = soff(g, f, 2 * q + p, m0 + col / 2) + (col & 1);
+        fv = Fb[o];
+        if (stage == 1) xv = X0[o];
+      }
+      sm.F[it] = fv;
+      sm.X[it] = xv;
+    }
+    __syncthreads();
+    // phase 1
+    const int ntmax = nq - 1;
+    for (int it = threadIdx.x; it < ntmax * W; it += blockDim.x) {
+      const int t = it / W, col = it - t * W;
+      if (col >= ncol) continue;
+      const int m = m0 + col / 2, c = col & 1;
+      if (sys == 0)
+        solve_rhs<KT>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+      else if (m == 0)
+        solve_rhs<KU>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+      else if (t < nq - 2)
+        solve_rhs<KP>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+    }
+    __syncthreads();
+    // phases 2, 3
+    if ((int)threadIdx.x < ncol) {
+      const int col = threadIdx.x, m = m0 + col / 2, c = col & 1;
+      bool o2;
+      if (sys == 0)
+        o2 = solve_recurrence<KT>(g, tb, p, m, c, col, sm, Xo);
+      else if (m == 0)
+        o2 = solve_recurrence<KU>(g, tb, p, m, c, col, sm, Xo);
+      else
+        o2 = solve_recurrence<KP>(g, tb, p, m, c, col, sm, Xo);
+      ok = ok && o2;
+    }
+    __syncthreads();
+    // phase 4
+    if (stage < 4) {
+      for (int it = threadIdx.x; it < ntmax * W; it += blockDim.x) {
+        const int t = it / W, col = it - t * W;
+        if (col >= ncol) continue;
+        const int m = m0 + col / 2, c = col & 1;
+        if (sys == 0)
+          solve_lx<KT>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+        else if (m == 0)
+          solve_lx<KU>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+        else if (t < nq - 2)
+          solve_lx<KP>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+      }
+    }
+    __syncthreads();
   }
   if (!ok) flags[b] = 1;
 }
 
-static int solve_threads(const Grid& g, int B) {
-  int bd = (B * 2 * g.nm >= 152 * 64 * 2) ? 64 : 32;
-  while (bd > 32 && (size_t)bd * 16 * g.nq > 200 * 1024) bd >>= 1;
-  return bd;
+static int solve_tile(const Grid& g, int B) {
+  int tms = (B * 2 * ((g.nm + 15) / 16) >= 152) ? 16 : 8;
+  if (tms > g.nm) tms = g.nm < 8 ? g.nm : 8;
+  while (tms > 2 && (size_t)5 * g.nq * 2 * tms * 8 > 200 * 1024) tms >>= 1;
+  return tms;
 }
-static size_t solve_smem(const Grid& g, int B) { return (size_t)solve_threads(g, B) * 16 * g.nq; }
+static size_t solve_smem(const Grid& g, int B) { return (size_t)5 * g.nq * 2 * solve_tile(g, B) * 8; }
 
 __global__ void k_advance(int* step) { *step += 1; }
 
@@ -682,7 +737,7 @@ cudaError_t configure_kernels(const Grid& g) {
     allowed_solve = need2;
   }
   static int allowed_zfwd = 48 * 1024;
-  const int need3 = (int)zfwd_smem(g);
+  const int need3 = (int)std::max(zfwd_smem(g, 1), zfwd_smem(g, 1 << 20));
   if (need3 > allowed_zfwd) {
     cudaError_t e = cudaFuncSetAttribute(k_zfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, need3);
     if (e != cudaSuccess) return e;
@@ -716,16 +771,16 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   cudaError_t e = launch_explicit(g, t, w, Xin, B, false, s);
   if (e != cudaSuccess) return e;
   Prof* pf = (w.prof && w.prof->on) ? w.prof : nullptr;
-  const int tm = zfwd_tile(g);
+  const int tm = zfwd_tile(g, B);
   const int mt = (g.nm + tm - 1) / tm;
   if (pf) pf->begin(RBC_KERNEL_ZFWD, s);
-  k_zfwd<<<(unsigned)(B * 2 * mt), 128, zfwd_smem(g), s>>>(g, t.zfwd, w.Q, w.F, S, B, tm, w.nsteps, w.step);
+  k_zfwd<<<(unsigned)(B * 2 * mt), 128, zfwd_smem(g, B), s>>>(g, t.zfwd, w.Q, w.F, S, B, tm, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_ZFWD, s, zfwd_flops(g, B), zfwd_bytes(g, B));
-  const int T3 = solve_threads(g, B);
-  const int mtiles = (g.nm + T3 / 2 - 1) / (T3 / 2);
+  const int tms = solve_tile(g, B);
+  const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
-  k_solve<<<(unsigned)(B * 2 * mtiles), T3, solve_smem(g, B), s>>>(g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags,
-                                                                   B, stage, w.nsteps, w.step);
+  k_solve<<<(unsigned)(B * 2 * mtiles), 256, solve_smem(g, B), s>>>(g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags,
+                                                                    B, stage, tms, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);
   return cudaGetLastError();
