@@ -447,6 +447,14 @@ static rbc_status upload_tables(rbc_t h) {
   add(Pb); add(Pd); add(PDi); add(PL); add(Pi);
   add(Ub); add(Ud); add(UDi); add(UL_); add(Ui);
   add(gram); add(twn); add(Vn); add(Vn1); add(Wn);
+  // FP32 copies of the transform tables, packed two floats per double slot
+  auto add_f32 = [&](const std::vector<double>& v) {
+    std::vector<double> packed((v.size() + 1) / 2, 0.0);
+    float* f = reinterpret_cast<float*>(packed.data());
+    for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
+    add(packed);
+  };
+  add_f32(zinv); add_f32(zfwd); add_f32(tw);
   CK(cudaMalloc(&h->d_tables, buf.size() * sizeof(double)));
   CK(cudaMemcpy(h->d_tables, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
   const double* b = h->d_tables;
@@ -467,6 +475,9 @@ static rbc_status upload_tables(rbc_t h) {
   T.Vn = b + offs[i++];
   T.Vn1 = b + offs[i++];
   T.Wn = b + offs[i++];
+  T.zinv32 = reinterpret_cast<const float*>(b + offs[i++]);
+  T.zfwd32 = reinterpret_cast<const float*>(b + offs[i++]);
+  T.tw32 = reinterpret_cast<const float2*>(b + offs[i++]);
   return RBC_OK;
 }
 
@@ -480,7 +491,8 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
     return fail(RBC_EINVAL, "need dt > 0, Pr > 0, Lx > 0, Ra >= 0");
   rbc_opts o{RBC_FP64, RBC_FIXED_T};
   if (opts) o = *opts;
-  if (o.precision != RBC_FP64) return fail(RBC_EINVAL, "precision mode %d not available", o.precision);
+  if (o.precision != RBC_FP64 && o.precision != RBC_MIXED)
+    return fail(RBC_EINVAL, "precision mode %d not available", o.precision);
   if (o.bc != RBC_FIXED_T) return fail(RBC_EINVAL, "boundary condition %d not available", o.bc);
   // padded x length 3 Nx / 2 must be 3 * 2^p for the FFT
   int Mx = 3 * Nx / 2, r = Mx / 3;
@@ -501,6 +513,7 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   g.Lx = Lx;
   g.dt = dt;
   g.kfac = 2.0 * M_PI / Lx;
+  g.mixed = (o.precision == RBC_MIXED) ? 1 : 0;
   rbc_status s = upload_tables(h);
   if (s == RBC_OK) {
     cudaError_t e = configure_kernels(g);
@@ -545,7 +558,7 @@ extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
   if (B <= h->cap) return RBC_OK;
   const Grid& g = h->g;
   const size_t S = state_doubles(g);
-  const size_t tot = (size_t)B * work_doubles_per_state(g) + 64;
+  const size_t tot = (size_t)B * work_doubles_per_state(g) + 80;
   void* p = nullptr;
   if (cudaMalloc(&p, tot * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();

@@ -17,6 +17,7 @@ struct Grid {
   int nq;         // coefficients per Chebyshev parity (Nz/2)
   double Ra, Pr, Lx, dt;
   double kfac;    // 2 pi / Lx, k_m = kfac * m
+  int mixed;      // 1: transforms and products in FP32 (RBC_MIXED)
 };
 
 // Device-resident operator tables (built on the host in FP64 once per grid/dt).
@@ -43,6 +44,10 @@ struct Tables {
   const double* Vn;     // [Nz][Nz]  T_n(s_j) at the native points
   const double* Vn1;    // [Nz][Nz]  T_n'(s_j)
   const double* Wn;     // [Nz][Nz]  native values -> T coefficients (exact interpolation)
+  // FP32 copies of the transform tables (RBC_MIXED)
+  const float* zinv32;  // [4][Mz][Nz]
+  const float* zfwd32;  // [Nz][Mz]
+  const float2* tw32;   // [Mx]
 };
 
 // Optional per-kernel CUDA-event timing (host side).  Event pairs come from a
@@ -53,10 +58,10 @@ struct Prof {
   std::vector<cudaEvent_t> ev;   // 2 per record
   std::vector<int> kind;         // kind of each recorded pair
   size_t used = 0;
-  double ms[4] = {0, 0, 0, 0};
-  long long launches[4] = {0, 0, 0, 0};
-  double flops[4] = {0, 0, 0, 0};
-  double bytes[4] = {0, 0, 0, 0};
+  double ms[RBC_NKERNELS] = {};
+  long long launches[RBC_NKERNELS] = {};
+  double flops[RBC_NKERNELS] = {};
+  double bytes[RBC_NKERNELS] = {};
   cudaError_t fold();
   void begin(int k, cudaStream_t s);
   void end(int k, cudaStream_t s, double fl, double by);
@@ -67,8 +72,8 @@ struct Work {
   double* Xs;      // stage state, B states
   double* F;       // explicit-term coefficients, B states
   double* R;       // RK accumulators, [B][4] states (tau rows in the coefficient slots)
-  double* Z;       // z-inverse output, [B][9][Mz][nm] complex
-  double* Q;       // row-kernel output, [B][2][Mz][nm] complex
+  double* Z;       // z-inverse output, [B][9][Mz][nm] complex (FP64, or FP32 in the first half)
+  double* Q;       // row-kernel output, [B][2][Mz][nm] complex (FP64 or FP32)
   double* wT;      // [B][Mz] x-mean of w T
   int* nsteps;     // [B]
   int* step;       // [1] step counter of the running batch
@@ -93,6 +98,7 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
 cudaError_t launch_explicit(const Grid& g, const Tables& t, const Work& w, const double* X, int B,
                             bool all_active, cudaStream_t s);
 cudaError_t launch_advance(const Work& w, cudaStream_t s);
+
 cudaError_t launch_nu_final(const Grid& g, const Tables& t, const Work& w, const double* X, int B,
                             double* nu, cudaStream_t s);
 cudaError_t launch_nusselt(const Grid& g, const Tables& t, const Work& w, const double* X, double* out3,

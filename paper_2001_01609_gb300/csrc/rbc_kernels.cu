@@ -57,155 +57,252 @@ __device__ __forceinline__ size_t soff(const Grid& g, int f, int n, int m) {
 __device__ __forceinline__ bool slice_active(const int* nsteps, const int* step, int b) {
   return nsteps == nullptr || *step < nsteps[b];
 }
+__device__ __forceinline__ bool slice_active_at(const int* nsteps, int stepidx, int b) {
+  return nsteps == nullptr || stepidx < nsteps[b];
+}
+
 
 // ---------------------------------------------------------------------------
-// z inverse transform (k_zinv).  Thread per (slice, padded row j < ceil(Mz/2),
-// mode m).  Even/odd split: the padded points are symmetric, s_{Mz-1-j} = -s_j,
-// and T_n^(q)(-s) = (-1)^(n+q) T_n^(q)(s), so the sums E, O over even and odd n
-// at s_j give f^(q)(s_j) = E + O and f^(q)(-s_j) = (-1)^q (E - O): half the
+// Real-type generic complex helpers for the transform kernels, which run in
+// FP64 (RBC_FP64) or in FP32 (RBC_MIXED); the state, the explicit terms F and
+// the stage solve stay FP64 in both modes.
+// ---------------------------------------------------------------------------
+template <typename T> struct Cx;
+template <> struct Cx<double> { using t = double2; };
+template <> struct Cx<float> { using t = float2; };
+template <typename T> using C2 = typename Cx<T>::t;
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 times_i(float2 a) { return make_float2(-a.y, a.x); }
+
+template <typename T> __device__ __forceinline__ C2<T> mk2(T x, T y);
+template <> __device__ __forceinline__ double2 mk2<double>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 mk2<float>(float x, float y) { return make_float2(x, y); }
+template <typename T> __device__ __forceinline__ C2<T> ldc(const T* p) { return *reinterpret_cast<const C2<T>*>(p); }
+template <typename T> __device__ __forceinline__ void stc(T* p, C2<T> v) { *reinterpret_cast<C2<T>*>(p) = v; }
+template <typename T> __device__ __forceinline__ C2<T> ldgc(const C2<T>* p) { return __ldg(p); }
+template <typename T> __device__ __forceinline__ C2<T> cvt2(double2 a) { return mk2<T>((T)a.x, (T)a.y); }
+
+// ---------------------------------------------------------------------------
+// z inverse transform (k_zinv).  Block per (slice, padded row pair j / Mz-1-j,
+// tile of 32 modes) with kp warps; warp w accumulates the coefficients n of its
+// share of [0, Nz), and the kp partial sums are added in a fixed order.
+// Even/odd split: the padded points are symmetric, s_{Mz-1-j} = -s_j, and
+// T_n^(q)(-s) = (-1)^(n+q) T_n^(q)(s), so the sums E, O over even and odd n at
+// s_j give f^(q)(s_j) = E + O and f^(q)(-s_j) = (-1)^q (E - O): half the
 // multiply-adds of evaluating both rows.  psi-slot operators V, VD, VD^2, VD^3
 // (d/ds) and T-slot V, VD; the epilogue forms, with d/dz = 2 d/ds, d/dx = ik:
 //   u = d_z psi (m = 0: U),  w = -ik psi,  d_x omega, d_z omega (omega = -lap psi,
 //   m = 0: omega = -U'),  d_x u,  d_z u,  T,  d_x T,  d_z T.
-// Output Z[b][field][j][m] (complex), fields in that order.
+// Output Z[b][field][j][m] (complex, real type T), fields in that order.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void zinv_store(const Grid& g, double* Zb, int j, int m, double k, const double2* P,
-                                           double2 t0, double2 t1) {
-  double2 u, w, dxo, dzo, dxu, dzu, dxT;
+template <typename T>
+__device__ __forceinline__ void zinv_store(const Grid& g, T* Zb, int j, int m, T k, const C2<T>* P, C2<T> t0,
+                                           C2<T> t1) {
+  using V = C2<T>;
+  const T zero = 0;
+  V u, w, dxo, dzo, dxu, dzu, dxT;
   if (m == 0) {
-    u = make_double2(P[0].x, 0.0);
-    w = make_double2(0.0, 0.0);
-    dxo = make_double2(0.0, 0.0);
-    dzo = make_double2(-4.0 * P[2].x, 0.0);
-    dxu = make_double2(0.0, 0.0);
-    dzu = make_double2(2.0 * P[1].x, 0.0);
-    dxT = make_double2(0.0, 0.0);
+    u = mk2<T>(P[0].x, zero);
+    w = mk2<T>(zero, zero);
+    dxo = mk2<T>(zero, zero);
+    dzo = mk2<T>((T)-4 * P[2].x, zero);
+    dxu = mk2<T>(zero, zero);
+    dzu = mk2<T>((T)2 * P[1].x, zero);
+    dxT = mk2<T>(zero, zero);
   } else {
-    u = 2.0 * P[1];
+    u = (T)2 * P[1];
     w = -k * times_i(P[0]);                            // -ik psi
-    const double2 om = (k * k) * P[0] - 4.0 * P[2];    // omega = -(4 psi'' - k^2 psi)
+    const V om = (k * k) * P[0] - (T)4 * P[2];         // omega = -(4 psi'' - k^2 psi)
     dxo = k * times_i(om);
-    dzo = (2.0 * k * k) * P[1] - 8.0 * P[3];           // -(8 psi''' - 2 k^2 psi')
+    dzo = ((T)2 * k * k) * P[1] - (T)8 * P[3];         // -(8 psi''' - 2 k^2 psi')
     dxu = k * times_i(u);
-    dzu = 4.0 * P[2];
+    dzu = (T)4 * P[2];
     dxT = k * times_i(t0);
   }
   const size_t fs = (size_t)g.Mz * g.nm * 2;
-  double* zb = Zb + ((size_t)j * g.nm + m) * 2;
-  st2(zb + 0 * fs, u);
-  st2(zb + 1 * fs, w);
-  st2(zb + 2 * fs, dxo);
-  st2(zb + 3 * fs, dzo);
-  st2(zb + 4 * fs, dxu);
-  st2(zb + 5 * fs, dzu);
-  st2(zb + 6 * fs, t0);
-  st2(zb + 7 * fs, dxT);
-  st2(zb + 8 * fs, 2.0 * t1);
+  T* zb = Zb + ((size_t)j * g.nm + m) * 2;
+  stc<T>(zb + 0 * fs, u);
+  stc<T>(zb + 1 * fs, w);
+  stc<T>(zb + 2 * fs, dxo);
+  stc<T>(zb + 3 * fs, dzo);
+  stc<T>(zb + 4 * fs, dxu);
+  stc<T>(zb + 5 * fs, dzu);
+  stc<T>(zb + 6 * fs, t0);
+  stc<T>(zb + 7 * fs, dxT);
+  stc<T>(zb + 8 * fs, (T)2 * t1);
 }
 
-__global__ void k_zinv(Grid g, const double* __restrict__ Bz, const double* __restrict__ X, size_t S,
-                       double* __restrict__ Z, int B, const int* nsteps, const int* step) {
+template <typename T>
+__device__ void zinv_item(const Grid& g, const T* __restrict__ Bz, const double* __restrict__ X, size_t S,
+                          T* __restrict__ Z, int B, const int* nsteps, int stepidx, int blk, int kp) {
+  using V = C2<T>;
+  extern __shared__ __align__(16) unsigned char zsm[];
+  V* part = reinterpret_cast<V*>(zsm);                 // [kp][12][32] when kp > 1
   const int Mh = (g.Mz + 1) / 2;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long per = (long)Mh * g.nm;
-  if (idx >= per * B) return;
-  const int b = (int)(idx / per);
-  if (!slice_active(nsteps, step, b)) return;
-  const int rem = (int)(idx - (long)b * per);
-  const int j = rem / g.nm, m = rem - j * g.nm;
+  const int mt = (g.nm + 31) / 32;
+  const int b = blk / (Mh * mt);
+  const int rem = blk - b * Mh * mt;
+  const int j = rem / mt, m0 = (rem - j * mt) * 32;
+  if (b >= B || !slice_active_at(nsteps, stepidx, b)) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m = m0 + lane;
+  const bool valid = m < g.nm;
+  const bool wact = w < kp;                            // warps beyond kp, if any, idle
   const double* Xb = X + (size_t)b * S;
-  const double* bq[4];
+  const T* bq[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) bq[q] = Bz + (size_t)(q * g.Mz + j) * g.Nz;
-  double2 E[6], O[6];
+  // share of the coefficient pairs (n, n+1) of this warp
+  const int npair = g.Nz / 2;
+  const int per = (npair + kp - 1) / kp;
+  const int p0 = w * per, p1 = min(npair, p0 + per);
+  V E[6], O[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) E[q] = O[q] = make_double2(0.0, 0.0);
+  for (int q = 0; q < 6; ++q) E[q] = O[q] = mk2<T>(0, 0);
+  if (valid && wact) {
 #pragma unroll 4
-  for (int n = 0; n < g.Nz; n += 2) {                  // Nz is even
+    for (int pp = p0; pp < p1; ++pp) {
+      const int n = 2 * pp;
 #pragma unroll
-    for (int par = 0; par < 2; ++par) {
-      const double2 xp = ld2(Xb + soff(g, 1, n + par, m));
-      const double2 xt = ld2(Xb + soff(g, 0, n + par, m));
-      double2* A = par ? O : E;
-      double v[4];
+      for (int par = 0; par < 2; ++par) {
+        const V xp = cvt2<T>(ld2(Xb + soff(g, 1, n + par, m)));
+        const V xt = cvt2<T>(ld2(Xb + soff(g, 0, n + par, m)));
+        V* A = par ? O : E;
+        T v[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = __ldg(bq[q] + n + par);
+        for (int q = 0; q < 4; ++q) v[q] = __ldg(bq[q] + n + par);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        A[q].x = fma(v[q], xp.x, A[q].x);
-        A[q].y = fma(v[q], xp.y, A[q].y);
+        for (int q = 0; q < 4; ++q) {
+          A[q].x = fma(v[q], xp.x, A[q].x);
+          A[q].y = fma(v[q], xp.y, A[q].y);
+        }
+        A[4].x = fma(v[0], xt.x, A[4].x);
+        A[4].y = fma(v[0], xt.y, A[4].y);
+        A[5].x = fma(v[1], xt.x, A[5].x);
+        A[5].y = fma(v[1], xt.y, A[5].y);
       }
-      A[4].x = fma(v[0], xt.x, A[4].x);
-      A[4].y = fma(v[0], xt.y, A[4].y);
-      A[5].x = fma(v[1], xt.x, A[5].x);
-      A[5].y = fma(v[1], xt.y, A[5].y);
     }
   }
-  const double k = g.kfac * m;
-  double* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
-  double2 P[4];
+  if (kp > 1) {
+    if (wact) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        part[(w * 12 + q) * 32 + lane] = E[q];
+        part[(w * 12 + 6 + q) * 32 + lane] = O[q];
+      }
+    }
+    __syncthreads();
+    if (w != 0) return;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      V e = part[q * 32 + lane], o = part[(6 + q) * 32 + lane];
+      for (int ww = 1; ww < kp; ++ww) {                // fixed order
+        e = e + part[(ww * 12 + q) * 32 + lane];
+        o = o + part[(ww * 12 + 6 + q) * 32 + lane];
+      }
+      E[q] = e;
+      O[q] = o;
+    }
+  } else if (w != 0) {
+    return;
+  }
+  if (!valid) return;
+  const T k = (T)(g.kfac * m);
+  T* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
+  V P[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) P[q] = E[q] + O[q];
-  zinv_store(g, Zb, j, m, k, P, E[4] + O[4], E[5] + O[5]);
+  zinv_store<T>(g, Zb, j, m, k, P, E[4] + O[4], E[5] + O[5]);
   const int jr = g.Mz - 1 - j;
   if (jr != j) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) P[q] = ((q & 1) ? -1.0 : 1.0) * (E[q] - O[q]);
-    zinv_store(g, Zb, jr, m, k, P, E[4] - O[4], -1.0 * (E[5] - O[5]));
+    for (int q = 0; q < 4; ++q) P[q] = ((q & 1) ? (T)-1 : (T)1) * (E[q] - O[q]);
+    zinv_store<T>(g, Zb, jr, m, k, P, E[4] - O[4], (T)-1 * (E[5] - O[5]));
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_zinv(Grid g, const T* __restrict__ Bz, const double* __restrict__ X, size_t S,
+                                              T* __restrict__ Z, int B, const int* nsteps, const int* step) {
+  zinv_item<T>(g, Bz, X, S, Z, B, nsteps, nsteps ? *step : 0, blockIdx.x, blockDim.x / 32);
+}
+
+// Warps sharing the coefficient sum of one k_zinv row pair.  It fixes the order
+// of the floating-point additions, so it depends on the grid only (every batch
+// size gives the same bits): small grids, whose single-state launches are
+// latency-bound, split the sum over up to 8 warps; large grids keep one warp.
+static int zinv_warps(const Grid& g) {
+  if ((long)g.Nx * g.Nz > 8192) return 1;
+  int kp = 1;
+  while (kp < 8 && (g.Nz / 2) / (2 * kp) >= 2) kp *= 2;
+  return kp;
 }
 
 // ---------------------------------------------------------------------------
 // Shared-memory mixed-radix Stockham FFT of length N = 3 * 2^p (radices
-// 4, ..., 4, [2], 3).  y_q = sum_r x_r exp(sign 2 pi i q r / N), unnormalised.
-// Ping-pongs between a and b; returns the buffer holding the result.
+// 4, ..., 4, [2], 3) applied to na arrays of length N at once (array a at
+// [a * N]).  y_q = sum_r x_r exp(sign 2 pi i q r / N), unnormalised.
+// Ping-pongs between a and b; returns the buffer holding the results.
 // ---------------------------------------------------------------------------
-__device__ double2* fft_smem(double2* a, double2* b, int N, int sign, const double2* tw) {
+template <typename T>
+__device__ C2<T>* fft_smem(C2<T>* a, C2<T>* b, int N, int na, int sign, const C2<T>* tw) {
+  using V = C2<T>;
   int p = 0;
   for (int M = N / 3; M > 1; M >>= 1) ++p;
-  int nr = p / 2 + (p & 1) + 1;
+  const int nr = p / 2 + (p & 1) + 1;
   int Ns = 1;
-  double2* x = a;
-  double2* y = b;
-  const double s3 = 0.86602540378443864676 * sign;   // sign * sqrt(3)/2
+  V* x = a;
+  V* y = b;
+  const T s3 = (T)0.86602540378443864676 * (T)sign;   // sign * sqrt(3)/2
+  const T sg = (T)sign;
   for (int pass = 0; pass < nr; ++pass) {
     const int R = (pass < p / 2) ? 4 : ((p & 1) && pass == p / 2) ? 2 : 3;
     const int nb = N / R;
     const int stride = N / (Ns * R);
-    for (int jj = threadIdx.x; jj < nb; jj += blockDim.x) {
+    for (int it = threadIdx.x; it < na * nb; it += blockDim.x) {
+      const int arr = it / nb, jj = it - arr * nb;
+      const V* xa = x + arr * N;
+      V* ya = y + arr * N;
       const int k = jj % Ns;
-      double2 v[4];
-      for (int r = 0; r < R; ++r) v[r] = x[jj + r * nb];
+      V v[4];
+      for (int r = 0; r < R; ++r) v[r] = xa[jj + r * nb];
       if (Ns > 1) {
         for (int r = 1; r < R; ++r) {
-          double2 wv = tw[(k * r * stride) % N];
+          V wv = tw[(k * r * stride) % N];
           if (sign > 0) wv.y = -wv.y;
           v[r] = cmul(v[r], wv);
         }
       }
       const int base = (jj / Ns) * Ns * R + k;
       if (R == 2) {
-        y[base] = v[0] + v[1];
-        y[base + Ns] = v[0] - v[1];
+        ya[base] = v[0] + v[1];
+        ya[base + Ns] = v[0] - v[1];
       } else if (R == 4) {
-        const double2 a0 = v[0] + v[2], a1 = v[0] - v[2];
-        const double2 b0 = v[1] + v[3], b1 = v[1] - v[3];
-        const double2 ib1 = (double)sign * times_i(b1);
-        y[base] = a0 + b0;
-        y[base + Ns] = a1 + ib1;
-        y[base + 2 * Ns] = a0 - b0;
-        y[base + 3 * Ns] = a1 - ib1;
+        const V a0 = v[0] + v[2], a1 = v[0] - v[2];
+        const V b0 = v[1] + v[3], b1 = v[1] - v[3];
+        const V ib1 = sg * times_i(b1);
+        ya[base] = a0 + b0;
+        ya[base + Ns] = a1 + ib1;
+        ya[base + 2 * Ns] = a0 - b0;
+        ya[base + 3 * Ns] = a1 - ib1;
       } else {
-        const double2 t1 = v[1] + v[2], t2 = v[1] - v[2];
-        const double2 m1 = v[0] - 0.5 * t1;
-        const double2 m2 = s3 * times_i(t2);
-        y[base] = v[0] + t1;
-        y[base + Ns] = m1 + m2;
-        y[base + 2 * Ns] = m1 - m2;
+        const V t1 = v[1] + v[2], t2 = v[1] - v[2];
+        const V m1 = v[0] - (T)0.5 * t1;
+        const V m2 = s3 * times_i(t2);
+        ya[base] = v[0] + t1;
+        ya[base + Ns] = m1 + m2;
+        ya[base + 2 * Ns] = m1 - m2;
       }
     }
     __syncthreads();
-    double2* tmp = x;
+    V* tmp = x;
     x = y;
     y = tmp;
     Ns *= R;
@@ -213,7 +310,16 @@ __device__ double2* fft_smem(double2* a, double2* b, int N, int sign, const doub
   return x;
 }
 
-size_t rows_smem_bytes(const Grid& g) { return (size_t)g.Mx * (3 * 16 + 9 * 8); }
+// Shared memory of k_rows: two ping-pong sets of 5 complex rows and the
+// twiddles (11 Mx complex values), or, when that does not fit, two single rows,
+// the twiddles and 9 real fields, with the five inverse FFTs in turn.
+static size_t rows_bytes_batched(const Grid& g, size_t es) { return (size_t)g.Mx * 11 * 2 * es; }
+static size_t rows_bytes_serial(const Grid& g, size_t es) { return (size_t)g.Mx * (3 * 2 + 9) * es; }
+static bool rows_batched(const Grid& g, size_t es) { return rows_bytes_batched(g, es) <= 200 * 1024; }
+static size_t rows_smem_for(const Grid& g, size_t es) {
+  return rows_batched(g, es) ? rows_bytes_batched(g, es) : rows_bytes_serial(g, es);
+}
+size_t rows_smem_bytes(const Grid& g) { return rows_smem_for(g, 8); }
 
 // Deterministic block sum (fixed tree over blockDim.x threads, blockDim a power of two).
 __device__ double block_sum(double v, double* red) {
@@ -228,6 +334,28 @@ __device__ double block_sum(double v, double* red) {
   return r;
 }
 
+// Pair pr of real fields (2 pr, 2 pr + 1) of row j as one complex spectrum of
+// length Mx: C = A + iB with the Hermitian extensions, zero beyond the kept modes.
+template <typename T>
+__device__ __forceinline__ C2<T> rows_packed(const Grid& g, const T* zrow, size_t fs, int pr, int x) {
+  using V = C2<T>;
+  const int fa = 2 * pr, fb = 2 * pr + 1, Mx = g.Mx, nm = g.nm;
+  const T* za = zrow + fa * fs;
+  const T* zb = zrow + fb * fs;
+  V c = mk2<T>(0, 0);
+  if (x < nm) {
+    const V a = ldc<T>(za + 2 * x);
+    const V bb = (fb < 9) ? ldc<T>(zb + 2 * x) : mk2<T>(0, 0);
+    c = a + times_i(bb);
+  } else if (x > Mx - nm) {
+    const int m = Mx - x;
+    const V a = ldc<T>(za + 2 * m);
+    const V bb = (fb < 9) ? ldc<T>(zb + 2 * m) : mk2<T>(0, 0);
+    c = conj2(a) + times_i(conj2(bb));
+  }
+  return c;
+}
+
 // ---------------------------------------------------------------------------
 // Row kernel (k_rows).  Block per (slice, padded row j).  Pairs of real fields
 // share one complex inverse FFT (C = A + iB with the Hermitian extensions);
@@ -236,76 +364,99 @@ __device__ double block_sum(double v, double* red) {
 //   <N_u>_x = <u u_x + w u_z>_x,  <w T>_x;
 // one packed forward FFT (N_T + i N_omega), truncation to m < nm.
 // Q[b][0][j][m] = N_T, Q[b][1][j][m] = N_omega (m >= 1), (<N_u>, 0) at m = 0.
+// The x-means are summed in FP64 in both precision modes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_rows(Grid g, const double2* __restrict__ tw, const double* __restrict__ Z,
-                                              double* __restrict__ Q, double* __restrict__ wT, int B,
-                                              const int* nsteps, const int* step) {
-  extern __shared__ double sm[];
-  const int b = blockIdx.x / g.Mz, j = blockIdx.x - b * g.Mz;
-  if (!slice_active(nsteps, step, b)) return;
+template <typename T>
+__device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* __restrict__ Z, T* __restrict__ Q,
+                          double* __restrict__ wT, int B, int batched, const int* nsteps, int stepidx, int blk) {
+  using V = C2<T>;
+  extern __shared__ __align__(16) unsigned char rsm[];
+  const int b = blk / g.Mz, j = blk - b * g.Mz;
+  if (b >= B || !slice_active_at(nsteps, stepidx, b)) return;
   const int Mx = g.Mx, nm = g.nm;
-  double2* A = reinterpret_cast<double2*>(sm);
-  double2* Bf = A + Mx;
-  double2* tws = Bf + Mx;                              // twiddles, staged once per block
-  double* fr = reinterpret_cast<double*>(tws + Mx);
   __shared__ double red[256];
-  for (int x = threadIdx.x; x < Mx; x += blockDim.x) tws[x] = __ldg(tw + x);
   const size_t fs = (size_t)g.Mz * nm * 2;
-  const double* zrow = Z + (size_t)b * 9 * fs + (size_t)j * nm * 2;
-  for (int pr = 0; pr < 5; ++pr) {
-    const int fa = 2 * pr, fb = 2 * pr + 1;
-    const double* za = zrow + fa * fs;
-    const double* zb = zrow + fb * fs;
-    for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
-      double2 c = make_double2(0.0, 0.0);
-      if (x < nm) {
-        const double2 a = ld2(za + 2 * x);
-        const double2 bb = (fb < 9) ? ld2(zb + 2 * x) : make_double2(0.0, 0.0);
-        c = a + times_i(bb);
-      } else if (x > Mx - nm) {
-        const int m = Mx - x;
-        const double2 a = ld2(za + 2 * m);
-        const double2 bb = (fb < 9) ? ld2(zb + 2 * m) : make_double2(0.0, 0.0);
-        c = conj2(a) + times_i(conj2(bb));
+  const T* zrow = Z + (size_t)b * 9 * fs + (size_t)j * nm * 2;
+  const V* fld;      // field value at x: real/imag parts of the five packed rows
+  V* A;
+  V* Bf;
+  V* tws;
+  T* fr = nullptr;
+  if (batched) {
+    A = reinterpret_cast<V*>(rsm);
+    Bf = A + 5 * Mx;
+    tws = Bf + 5 * Mx;
+    for (int x = threadIdx.x; x < Mx; x += blockDim.x) tws[x] = ldgc<T>(tw + x);
+    for (int it = threadIdx.x; it < 5 * Mx; it += blockDim.x) {
+      const int pr = it / Mx, x = it - pr * Mx;
+      A[it] = rows_packed<T>(g, zrow, fs, pr, x);
+    }
+    __syncthreads();
+    fld = fft_smem<T>(A, Bf, Mx, 5, +1, tws);
+  } else {
+    A = reinterpret_cast<V*>(rsm);
+    Bf = A + Mx;
+    tws = Bf + Mx;
+    fr = reinterpret_cast<T*>(tws + Mx);
+    for (int x = threadIdx.x; x < Mx; x += blockDim.x) tws[x] = ldgc<T>(tw + x);
+    for (int pr = 0; pr < 5; ++pr) {
+      for (int x = threadIdx.x; x < Mx; x += blockDim.x) A[x] = rows_packed<T>(g, zrow, fs, pr, x);
+      __syncthreads();
+      const V* res = fft_smem<T>(A, Bf, Mx, 1, +1, tws);
+      for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
+        fr[(2 * pr) * Mx + x] = res[x].x;
+        if (pr < 4) fr[(2 * pr + 1) * Mx + x] = res[x].y;
       }
-      A[x] = c;
+      __syncthreads();
     }
-    __syncthreads();
-    const double2* res = fft_smem(A, Bf, Mx, +1, tws);
-    for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
-      fr[fa * Mx + x] = res[x].x;
-      if (fb < 9) fr[fb * Mx + x] = res[x].y;
-    }
-    __syncthreads();
+    fld = nullptr;
   }
+  auto field = [&](int fi, int x) -> T {
+    if (fld) {
+      const V v = fld[(fi >> 1) * Mx + x];
+      return (fi & 1) ? v.y : v.x;
+    }
+    return fr[fi * Mx + x];
+  };
+  // products into the first row of the buffer not holding the fields
+  V* P = (fld == A) ? Bf : A;
   double nU = 0.0, wt = 0.0;
   for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
-    const double u = fr[0 * Mx + x], w = fr[1 * Mx + x];
-    const double nO = u * fr[2 * Mx + x] + w * fr[3 * Mx + x];
-    nU += u * fr[4 * Mx + x] + w * fr[5 * Mx + x];
-    const double nT = u * fr[7 * Mx + x] + w * fr[8 * Mx + x];
-    wt += w * fr[6 * Mx + x];
-    A[x] = make_double2(nT, nO);
+    const T u = field(0, x), w = field(1, x);
+    const T nO = u * field(2, x) + w * field(3, x);
+    nU += (double)(u * field(4, x) + w * field(5, x));
+    const T nT = u * field(7, x) + w * field(8, x);
+    wt += (double)(w * field(6, x));
+    P[x] = mk2<T>(nT, nO);
   }
   __syncthreads();
   const double sU = block_sum(nU, red);
   const double sW = block_sum(wt, red);
-  const double2* C = fft_smem(A, Bf, Mx, -1, tws);
-  const double inv = 1.0 / Mx;
+  V* P2 = (P == A) ? Bf : A;                           // scratch row for the ping-pong
+  const V* C = fft_smem<T>(P, P2, Mx, 1, -1, tws);
+  const T inv = (T)1 / (T)Mx;
+  const T half = (T)0.5 * inv;
   const size_t qs = (size_t)g.Mz * nm * 2;
-  double* q0 = Q + (size_t)b * 2 * qs + (size_t)j * nm * 2;
-  double* q1 = q0 + qs;
+  T* q0 = Q + (size_t)b * 2 * qs + (size_t)j * nm * 2;
+  T* q1 = q0 + qs;
   for (int m = threadIdx.x; m < nm; m += blockDim.x) {
-    const double2 cm = C[m];
-    const double2 cn = conj2(C[m == 0 ? 0 : Mx - m]);
-    const double2 s = cm + cn, d = cm - cn;
-    st2(q0 + 2 * m, make_double2(0.5 * inv * s.x, 0.5 * inv * s.y));
+    const V cm = C[m];
+    const V cn = conj2(C[m == 0 ? 0 : Mx - m]);
+    const V s = cm + cn, d = cm - cn;
+    stc<T>(q0 + 2 * m, mk2<T>(half * s.x, half * s.y));
     if (m == 0)
-      st2(q1, make_double2(sU * inv, 0.0));
+      stc<T>(q1, mk2<T>((T)(sU / Mx), (T)0));
     else
-      st2(q1 + 2 * m, make_double2(0.5 * inv * d.y, -0.5 * inv * d.x));
+      stc<T>(q1 + 2 * m, mk2<T>(half * d.y, -half * d.x));
   }
-  if (threadIdx.x == 0) wT[(size_t)b * g.Mz + j] = sW * inv;
+  if (threadIdx.x == 0) wT[(size_t)b * g.Mz + j] = sW / Mx;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows(Grid g, const C2<T>* __restrict__ tw, const T* __restrict__ Z,
+                                              T* __restrict__ Q, double* __restrict__ wT, int B, int batched,
+                                              const int* nsteps, const int* step) {
+  rows_item<T>(g, tw, Z, Q, wT, B, batched, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -313,28 +464,35 @@ __global__ void __launch_bounds__(256) k_rows(Grid g, const double2* __restrict_
 // W[n][Mz-1-j] = (-1)^n W[n][j] (symmetric points), so with the folds
 // Ev_j = Q_j + Q_{Mz-1-j}, Od_j = Q_j - Q_{Mz-1-j} (the middle row, for odd Mz,
 // once in Ev) F_n = sum_{j < ceil(Mz/2)} W[n][j] (n even ? Ev : Od)_j.  Block per
-// (slice, field, tile of tm modes): folds staged in shared memory once, reused
-// by every n.
+// (slice, field, tile of tm modes, chunk of the n range): the folds are staged
+// in shared memory once per block and reused by every n of the chunk.  F is
+// written in FP64 for the stage solve.
 // ---------------------------------------------------------------------------
-__global__ void k_zfwd(Grid g, const double* __restrict__ W, const double* __restrict__ Q, double* __restrict__ F,
-                       size_t S, int B, int tm, const int* nsteps, const int* step) {
-  extern __shared__ double2 fold[];                    // [2][Mh][tm]
+template <typename T>
+__device__ void zfwd_item(const Grid& g, const T* __restrict__ W, const T* __restrict__ Q, double* __restrict__ F,
+                          size_t S, int B, int tm, int nch, const int* nsteps, int stepidx, int blk) {
+  using V = C2<T>;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  V* fold = reinterpret_cast<V*>(fsm);                 // [2][Mh][tm]
   const int Mh = (g.Mz + 1) / 2;
   const int mt = (g.nm + tm - 1) / tm;
-  const int b = blockIdx.x / (2 * mt);
-  const int rem = blockIdx.x - b * 2 * mt;
+  const int per_b = 2 * mt * nch;
+  const int b = blk / per_b;
+  int rem = blk - b * per_b;
+  const int ch = rem % nch;
+  rem /= nch;
   const int f = rem / mt, m0 = (rem - f * mt) * tm;
-  if (b >= B || !slice_active(nsteps, step, b)) return;
+  if (b >= B || !slice_active_at(nsteps, stepidx, b)) return;
   const size_t qs = (size_t)g.Mz * g.nm * 2;
-  const double* q = Q + (size_t)(b * 2 + f) * qs;
+  const T* q = Q + (size_t)(b * 2 + f) * qs;
   for (int it = threadIdx.x; it < Mh * tm; it += blockDim.x) {
     const int jh = it / tm, mi = it - jh * tm, m = m0 + mi;
-    double2 ev = {0.0, 0.0}, od = {0.0, 0.0};
+    V ev = mk2<T>(0, 0), od = mk2<T>(0, 0);
     if (m < g.nm) {
-      const double2 a = ld2(q + ((size_t)jh * g.nm + m) * 2);
+      const V a = ldc<T>(q + ((size_t)jh * g.nm + m) * 2);
       const int jr = g.Mz - 1 - jh;
       if (jr != jh) {
-        const double2 c = ld2(q + ((size_t)jr * g.nm + m) * 2);
+        const V c = ldc<T>(q + ((size_t)jr * g.nm + m) * 2);
         ev = a + c;
         od = a - c;
       } else {
@@ -349,29 +507,45 @@ __global__ void k_zfwd(Grid g, const double* __restrict__ W, const double* __res
   const int mi = threadIdx.x % tm, n0 = threadIdx.x / tm;
   const int m = m0 + mi;
   if (m >= g.nm) return;
-  for (int n = n0; n < g.Nz; n += ng) {
-    const double2* src = fold + (size_t)((n & 1) ? Mh : 0) * tm + mi;
-    const double* wr = W + (size_t)n * g.Mz;
-    double2 acc = {0.0, 0.0};
+  const int nper = (g.Nz + nch - 1) / nch;
+  const int nlo = ch * nper, nhi = min(g.Nz, nlo + nper);
+  for (int n = nlo + n0; n < nhi; n += ng) {
+    const V* src = fold + (size_t)((n & 1) ? Mh : 0) * tm + mi;
+    const T* wr = W + (size_t)n * g.Mz;
+    V acc = mk2<T>(0, 0);
 #pragma unroll 4
     for (int jh = 0; jh < Mh; ++jh) {
-      const double wv = __ldg(wr + jh);
-      const double2 v = src[(size_t)jh * tm];
+      const T wv = __ldg(wr + jh);
+      const V v = src[(size_t)jh * tm];
       acc.x = fma(wv, v.x, acc.x);
       acc.y = fma(wv, v.y, acc.y);
     }
-    st2(F + (size_t)b * S + soff(g, f, n, m), acc);
+    st2(F + (size_t)b * S + soff(g, f, n, m), make_double2((double)acc.x, (double)acc.y));
   }
 }
 
-static int zfwd_tile(const Grid& g, int B) {
+template <typename T>
+__global__ void k_zfwd(Grid g, const T* __restrict__ W, const T* __restrict__ Q, double* __restrict__ F, size_t S,
+                       int B, int tm, int nch, const int* nsteps, const int* step) {
+  zfwd_item<T>(g, W, Q, F, S, B, tm, nch, nsteps, nsteps ? *step : 0, blockIdx.x);
+}
+
+static int zfwd_tile(const Grid& g, int B, size_t es) {
   const int Mh = (g.Mz + 1) / 2;
   int tm = 32;
   while (tm > 4 && (size_t)B * 2 * ((g.nm + tm - 1) / tm) < 2 * 152) tm >>= 1;
-  while (tm > 4 && (size_t)2 * Mh * tm * 16 > 200 * 1024) tm >>= 1;
+  while (tm > 4 && (size_t)2 * Mh * tm * 2 * es > 200 * 1024) tm >>= 1;
   return tm;
 }
-static size_t zfwd_smem(const Grid& g, int B) { return (size_t)2 * ((g.Mz + 1) / 2) * zfwd_tile(g, B) * 16; }
+static int zfwd_chunks(const Grid& g, int B, int tm) {
+  const long blocks = (long)B * 2 * ((g.nm + tm - 1) / tm);
+  int nch = 1;
+  while (nch < 8 && blocks * nch < 4L * 152 && g.Nz / (2 * nch) >= 128 / tm) nch *= 2;
+  return nch;
+}
+static size_t zfwd_smem(const Grid& g, int B, size_t es) {
+  return (size_t)2 * ((g.Mz + 1) / 2) * zfwd_tile(g, B, es) * 2 * es;
+}
 
 // ---------------------------------------------------------------------------
 // Stage solve (k_solve).  Block per (slice, Chebyshev parity p, tile of tms
@@ -452,9 +626,9 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
     for (int l = 2; l <= 4; ++l) R[(size_t)(l - 1) * S + ro] = fma(dt * c_AE[l][0], fv, mx);
   } else {
     double Rl[3];
-    const double Ri = R[(size_t)(stage - 1) * S + ro];
+    const double Ri = *(R + (size_t)(stage - 1) * S + ro);
 #pragma unroll
-    for (int l = 0; l < 3; ++l) Rl[l] = (l + 2 > stage) ? R[(size_t)(l + 1) * S + ro] : 0.0;
+    for (int l = 0; l < 3; ++l) Rl[l] = (l + 2 > stage) ? *(R + (size_t)(l + 1) * S + ro) : 0.0;
     r = fma(dt * c_AE[stage][stage - 1], fv, Ri);
 #pragma unroll
     for (int l = 0; l < 3; ++l)
@@ -550,20 +724,20 @@ __device__ __forceinline__ void solve_lx(const Grid& g, const Tables& tb, int st
   for (int l = 0; l < 3; ++l)
     if (l + 2 > stage) {
       double* Rl = R + (size_t)(l + 1) * S + ro;
-      *Rl = fma(c_AI[l + 2][stage], lx2, *Rl);
+      *Rl = fma(c_AI[l + 2][stage], lx2, *(Rl));
     }
 }
 
-__global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, double* Xs, const double* F, double* R,
-                                               size_t S, const double* wT, double* nu, int* flags, int B, int stage,
-                                               int tms, const int* nsteps, const int* step) {
+__device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* Xs, const double* F, double* R,
+                           size_t S, const double* wT, double* nu, int* flags, int B, int stage, int tms,
+                           bool sparse, const int* nsteps, int stepidx, int blk) {
   extern __shared__ double sbuf[];
   const int mt = (g.nm + tms - 1) / tms;
-  const int b = blockIdx.x / (2 * mt);
-  const int rem = blockIdx.x - b * 2 * mt;
+  const int b = blk / (2 * mt);
+  const int rem = blk - b * 2 * mt;
   const int p = rem / mt;
   const int m0 = (rem - p * mt) * tms;
-  if (b >= B || !slice_active(nsteps, step, b)) return;   // uniform per block
+  if (b >= B || !slice_active_at(nsteps, stepidx, b)) return;   // uniform per block
   const int nq = g.nq;
   const int W = 2 * tms;
   const int ncol = 2 * min(tms, g.nm - m0);
@@ -582,10 +756,10 @@ __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, dou
     // Nu_V(t_n) (Eq. 9) of the step-start state: wall temperature difference of
     // the mean profile + Clenshaw-Curtis integral of <wT>_x; trapezoid weight.
     double cond = 0.0;
-    for (int n = 1; n < g.Nz; n += 2) cond -= 2.0 * X0[soff(g, 0, n, 0)];
+    for (int n = 1; n < g.Nz; n += 2) cond -= 2.0 * *(X0 + soff(g, 0, n, 0));
     double adv = 0.0;
-    for (int jz = 0; jz < g.Mz; ++jz) adv = fma(__ldg(tb.cc + jz), wT[(size_t)b * g.Mz + jz], adv);
-    nu[b] += ((*step == 0) ? 0.5 : 1.0) * g.dt * (cond + 0.5 * adv);
+    for (int jz = 0; jz < g.Mz; ++jz) adv = fma(__ldg(tb.cc + jz), *(wT + (size_t)b * g.Mz + jz), adv);
+    nu[b] += ((stepidx == 0) ? 0.5 : 1.0) * g.dt * (cond + 0.5 * adv);
   }
   bool ok = true;
   for (int sys = 0; sys < 2; ++sys) {
@@ -596,8 +770,8 @@ __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, dou
       double fv = 0.0, xv = 0.0;
       if (col < ncol) {
         const size_t o = soff(g, f, 2 * q + p, m0 + col / 2) + (col & 1);
-        fv = Fb[o];
-        if (stage == 1) xv = X0[o];
+        fv = *(Fb + o);
+        if (stage == 1) xv = *(X0 + o);
       }
       sm.F[it] = fv;
       sm.X[it] = xv;
@@ -617,9 +791,12 @@ __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, dou
         solve_rhs<KP>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
     }
     __syncthreads();
-    // phases 2, 3
-    if ((int)threadIdx.x < ncol) {
-      const int col = threadIdx.x, m = m0 + col / 2, c = col & 1;
+    // phases 2, 3: one column per thread, spread over all warps so that each
+    // warp has few active lanes (a full-warp FP64 instruction costs ~64 cycles)
+    const int nw = blockDim.x >> 5;
+    const int rcol = sparse ? (int)(threadIdx.x & 31) * nw + (int)(threadIdx.x >> 5) : (int)threadIdx.x;
+    if (rcol < ncol) {
+      const int col = rcol, m = m0 + col / 2, c = col & 1;
       bool o2;
       if (sys == 0)
         o2 = solve_recurrence<KT>(g, tb, p, m, c, col, sm, Xo);
@@ -647,6 +824,13 @@ __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, dou
     __syncthreads();
   }
   if (!ok) flags[b] = 1;
+}
+
+__global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, double* Xs, const double* F, double* R,
+                                               size_t S, const double* wT, double* nu, int* flags, int B, int stage,
+                                               int tms, int sparse, const int* nsteps, const int* step) {
+  solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, B, stage, tms, sparse != 0, nsteps, nsteps ? *step : 0,
+                    blockIdx.x);
 }
 
 static int solve_tile(const Grid& g, int B) {
@@ -706,15 +890,19 @@ void Prof::end(int k, cudaStream_t s, double fl, double by) {
 
 // Algorithmic work of one launch over B slices (all active).
 static double zinv_flops(const Grid& g, int B) { return 24.0 * B * ((g.Mz + 1) / 2) * g.nm * g.Nz; }
-static double zinv_bytes(const Grid& g, int B) {
-  return 8.0 * B * state_doubles(g) + 8.0 * B * z_doubles(g);
+static double zinv_bytes(const Grid& g, int B, size_t es = 8) {
+  return 8.0 * B * state_doubles(g) + (double)es * B * z_doubles(g);
 }
 static double rows_flops(const Grid& g, int B) {
   return (double)B * g.Mz * (6.0 * 5.0 * g.Mx * std::log2((double)g.Mx) + 10.0 * g.Mx);
 }
-static double rows_bytes(const Grid& g, int B) { return 8.0 * B * (z_doubles(g) + q_doubles(g) + g.Mz); }
+static double rows_bytes(const Grid& g, int B, size_t es = 8) {
+  return (double)es * B * (z_doubles(g) + q_doubles(g)) + 8.0 * B * g.Mz;
+}
 static double zfwd_flops(const Grid& g, int B) { return 4.0 * B * g.Nz * g.nm * ((g.Mz + 1) / 2) * 2.0; }
-static double zfwd_bytes(const Grid& g, int B) { return 8.0 * B * (q_doubles(g) + state_doubles(g)); }
+static double zfwd_bytes(const Grid& g, int B, size_t es = 8) {
+  return (double)es * B * q_doubles(g) + 8.0 * B * state_doubles(g);
+}
 // stage solve: per (m, parity) about 60 flops per coefficient row for T and psi;
 // reads F, X and up to four accumulators, writes X and the accumulators
 static double solve_flops(const Grid& g, int B) { return 120.0 * B * g.nm * 2.0 * g.nq * 2.0; }
@@ -722,46 +910,70 @@ static double solve_bytes(const Grid& g, int B) { return 8.0 * B * state_doubles
 
 // The dynamic shared-memory allowance of k_rows only ever grows, so that a
 // later handle on a smaller grid does not shrink it below an earlier one's need.
+// The dynamic shared-memory allowances only ever grow, so that a later handle
+// on a smaller grid does not shrink them below an earlier one's need.
+template <typename F>
+static cudaError_t allow_smem(F* fn, int need, int& allowed) {
+  if (need <= allowed) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+  if (e == cudaSuccess) allowed = need;
+  return e;
+}
+
 cudaError_t configure_kernels(const Grid& g) {
-  static int allowed_rows = 48 * 1024, allowed_solve = 48 * 1024;
-  const int need = (int)rows_smem_bytes(g);
-  if (need > allowed_rows) {
-    cudaError_t e = cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
-    if (e != cudaSuccess) return e;
-    allowed_rows = need;
-  }
-  const int need2 = (int)std::max(solve_smem(g, 1), solve_smem(g, 1 << 20));
-  if (need2 > allowed_solve) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, need2);
-    if (e != cudaSuccess) return e;
-    allowed_solve = need2;
-  }
-  static int allowed_zfwd = 48 * 1024;
-  const int need3 = (int)std::max(zfwd_smem(g, 1), zfwd_smem(g, 1 << 20));
-  if (need3 > allowed_zfwd) {
-    cudaError_t e = cudaFuncSetAttribute(k_zfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, need3);
-    if (e != cudaSuccess) return e;
-    allowed_zfwd = need3;
-  }
-  return cudaSuccess;
+  static int a_rows_d = 48 * 1024, a_rows_f = 48 * 1024, a_solve = 48 * 1024;
+  static int a_zfwd_d = 48 * 1024, a_zfwd_f = 48 * 1024;
+  cudaError_t e = allow_smem(k_rows<double>, (int)rows_smem_for(g, 8), a_rows_d);
+  if (e == cudaSuccess) e = allow_smem(k_rows<float>, (int)rows_smem_for(g, 4), a_rows_f);
+  if (e == cudaSuccess)
+    e = allow_smem(k_solve, (int)std::max(solve_smem(g, 1), solve_smem(g, 1 << 20)), a_solve);
+  if (e == cudaSuccess)
+    e = allow_smem(k_zfwd<double>, (int)std::max(zfwd_smem(g, 1, 8), zfwd_smem(g, 1 << 20, 8)), a_zfwd_d);
+  if (e == cudaSuccess)
+    e = allow_smem(k_zfwd<float>, (int)std::max(zfwd_smem(g, 1, 4), zfwd_smem(g, 1 << 20, 4)), a_zfwd_f);
+  return e;
+}
+
+template <typename T>
+static void launch_transforms_in(const Grid& g, const T* Bz, const C2<T>* tw, const Work& w, const double* X, int B,
+                                 const int* ns, Prof* pf, cudaStream_t s) {
+  const size_t S = state_doubles(g);
+  const int kp = zinv_warps(g);
+  const unsigned zb = (unsigned)(B * ((g.Mz + 1) / 2) * ((g.nm + 31) / 32));
+  T* Z = reinterpret_cast<T*>(w.Z);
+  T* Q = reinterpret_cast<T*>(w.Q);
+  if (pf) pf->begin(RBC_KERNEL_ZINV, s);
+  k_zinv<T><<<zb, 32 * kp, kp > 1 ? (size_t)kp * 12 * 32 * 2 * sizeof(T) : 0, s>>>(g, Bz, X, S, Z, B, ns, w.step);
+  if (pf) pf->end(RBC_KERNEL_ZINV, s, zinv_flops(g, B), zinv_bytes(g, B, sizeof(T)));
+  const size_t es = sizeof(T);
+  if (pf) pf->begin(RBC_KERNEL_ROWS, s);
+  k_rows<T><<<(unsigned)(B * g.Mz), 256, rows_smem_for(g, es), s>>>(g, tw, Z, Q, w.wT, B, rows_batched(g, es) ? 1 : 0,
+                                                                     ns, w.step);
+  if (pf) pf->end(RBC_KERNEL_ROWS, s, rows_flops(g, B), rows_bytes(g, B, sizeof(T)));
 }
 
 cudaError_t launch_explicit(const Grid& g, const Tables& t, const Work& w, const double* X, int B, bool all_active,
                             cudaStream_t s) {
   const int* ns = all_active ? nullptr : w.nsteps;
-  const size_t S = state_doubles(g);
   Prof* pf = (w.prof && w.prof->on && !all_active) ? w.prof : nullptr;
-  const long nz = (long)B * ((g.Mz + 1) / 2) * g.nm;
-  const int T1 = (nz >= 152L * 256) ? 128 : 32;
-  if (pf) pf->begin(RBC_KERNEL_ZINV, s);
-  k_zinv<<<nblk(nz, T1), T1, 0, s>>>(g, t.zinv, X, S, w.Z, B, ns, w.step);
-  if (pf) pf->end(RBC_KERNEL_ZINV, s, zinv_flops(g, B), zinv_bytes(g, B));
-  const int T2 = (g.Mx >= 768) ? 256 : 128;
-  if (pf) pf->begin(RBC_KERNEL_ROWS, s);
-  k_rows<<<(unsigned)(B * g.Mz), T2, rows_smem_bytes(g), s>>>(g, t.tw, w.Z, w.Q, w.wT, B, ns, w.step);
-  if (pf) pf->end(RBC_KERNEL_ROWS, s, rows_flops(g, B), rows_bytes(g, B));
+  if (g.mixed)
+    launch_transforms_in<float>(g, t.zinv32, t.tw32, w, X, B, ns, pf, s);
+  else
+    launch_transforms_in<double>(g, t.zinv, t.tw, w, X, B, ns, pf, s);
   count(2);
   return cudaGetLastError();
+}
+
+template <typename T>
+static void launch_zfwd(const Grid& g, const T* W, const Work& w, int B, Prof* pf, cudaStream_t s) {
+  const size_t S = state_doubles(g), es = sizeof(T);
+  const int tm = zfwd_tile(g, B, es);
+  const int mt = (g.nm + tm - 1) / tm;
+  const int nch = zfwd_chunks(g, B, tm);
+  if (pf) pf->begin(RBC_KERNEL_ZFWD, s);
+  k_zfwd<T><<<(unsigned)(B * 2 * mt * nch), 128, zfwd_smem(g, B, es), s>>>(g, W, reinterpret_cast<const T*>(w.Q), w.F,
+                                                                            S, B, tm, nch, w.nsteps, w.step);
+  if (pf) pf->end(RBC_KERNEL_ZFWD, s, zfwd_flops(g, B), zfwd_bytes(g, B, es));
 }
 
 cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* X, int B, int stage, double* nu,
@@ -771,16 +983,16 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   cudaError_t e = launch_explicit(g, t, w, Xin, B, false, s);
   if (e != cudaSuccess) return e;
   Prof* pf = (w.prof && w.prof->on) ? w.prof : nullptr;
-  const int tm = zfwd_tile(g, B);
-  const int mt = (g.nm + tm - 1) / tm;
-  if (pf) pf->begin(RBC_KERNEL_ZFWD, s);
-  k_zfwd<<<(unsigned)(B * 2 * mt), 128, zfwd_smem(g, B), s>>>(g, t.zfwd, w.Q, w.F, S, B, tm, w.nsteps, w.step);
-  if (pf) pf->end(RBC_KERNEL_ZFWD, s, zfwd_flops(g, B), zfwd_bytes(g, B));
+  if (g.mixed)
+    launch_zfwd<float>(g, t.zfwd32, w, B, pf, s);
+  else
+    launch_zfwd<double>(g, t.zfwd, w, B, pf, s);
   const int tms = solve_tile(g, B);
   const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
+  const int sparse = (B * 2 * mtiles < 152) ? 1 : 0;
   k_solve<<<(unsigned)(B * 2 * mtiles), 256, solve_smem(g, B), s>>>(g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags,
-                                                                    B, stage, tms, w.nsteps, w.step);
+                                                                    B, stage, tms, sparse, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);
   return cudaGetLastError();

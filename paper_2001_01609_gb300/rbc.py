@@ -172,10 +172,11 @@ class Propagator:
         _check(load().rbc_profile(self.h, 1 if enable else 0))
 
     def profile_read(self):
-        ms, fl, by = np.zeros(4), np.zeros(4), np.zeros(4)
-        n = (ctypes.c_longlong * 4)()
+        K = len(KERNEL_NAMES)
+        ms, fl, by = np.zeros(K), np.zeros(K), np.zeros(K)
+        n = (ctypes.c_longlong * K)()
         _check(load().rbc_profile_read(self.h, _dptr(ms), n, _dptr(fl), _dptr(by)))
-        return {KERNEL_NAMES[k]: dict(ms=ms[k], launches=n[k], flops=fl[k], bytes=by[k]) for k in range(4)}
+        return {KERNEL_NAMES[k]: dict(ms=ms[k], launches=n[k], flops=fl[k], bytes=by[k]) for k in range(K)}
 
     def l2_temperature(self, state, stream=None):
         out = np.zeros(1)

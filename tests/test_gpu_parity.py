@@ -235,3 +235,34 @@ def test_parareal_stopping_criteria(rbc):
     assert st3 == rbc.RBC_ENOTCONVERGED and k3 == 2
     with pytest.raises(rbc.RBCError):
         rbc.Parareal(F, G, 0.0, T * 1.0001, N)          # not a whole number of steps
+
+
+@pytest.mark.parametrize("Nx,Nz,Ra", [(64, 32, 1e5), (32, 18, 2e5), (256, 64, 1e6)])
+def test_mixed_precision_few_steps_within_stated_tolerance(rbc, Nx, Nz, Ra):
+    """RBC_MIXED: FP32 transforms and products, FP64 solves and RK combination.
+
+    Stated tolerance: 1e-5 relative to the largest coefficient after 4 steps
+    (FP32 rounding of the explicit terms, ~1e-7, enters the state through
+    dt * F and is not amplified over a few steps).
+    """
+    dt = 1e-4 if Ra < 1e6 else 1e-5
+    o = RBC(Ra, 1.0, 2.0, Nx, Nz, dt)
+    X0 = developed_state(o, seed=Nx + 7)
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt, precision=rbc.RBC_MIXED)
+    st = F.new_states(1)
+    put(st, 0, X0)
+    nu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F.step_batch(st, 4, nu)
+    assert F.check_diverged() == rbc.RBC_OK
+    ref, integ = o.run(X0, 4)
+    err = max_rel_diff(get(st, 0), ref)
+    print(f"mixed {Nx}x{Nz} Ra={Ra:g}: state rel err {err:.3e}, Nu integral rel err "
+          f"{abs(nu.item() - integ) / abs(integ):.3e}")
+    assert err < 1e-5
+    assert abs(nu.item() - integ) < 1e-5 * abs(integ)
+    # the FP64 path on the same input is much closer
+    F64 = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt)
+    st64 = F64.new_states(1)
+    put(st64, 0, X0)
+    F64.step_batch(st64, 4)
+    assert max_rel_diff(get(st64, 0), ref) < 1e-11 < err
