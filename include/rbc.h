@@ -170,8 +170,9 @@ rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_i
 enum { RBC_KERNEL_ZINV = 0, RBC_KERNEL_ROWS = 1, RBC_KERNEL_ZFWD = 2, RBC_KERNEL_SOLVE = 3, RBC_NKERNELS = 4 };
 
 /* rbc_profile(h, 1) starts recording a CUDA event pair on the launching stream
- * around every stage kernel that h launches and clears the totals; (h, 0)
- * stops recording.  rbc_profile_read synchronises the device and returns, per
+ * around every stage kernel that h launches and clears the totals; (h, 2)
+ * does the same for the next rbc_step_batch call only (a sample: calls that
+ * are recorded run without their CUDA graph); (h, 0) stops recording.  rbc_profile_read synchronises the device and returns, per
  * kernel kind, the summed event time (ms), the launch count, and the
  * algorithmic FP operations and DRAM bytes of those launches (each operand
  * read once, each result written once, all B slices active).  Any of the

@@ -351,6 +351,19 @@ static rbc_status upload_tables(rbc_t h) {
   std::vector<double> Pb((size_t)2 * nq * 2 * nm), Pd(Pb.size()), PDi((size_t)2 * 4 * nm), PL(Pb.size()),
       Pi((size_t)2 * nq * nm);
   std::vector<double> Ub((size_t)2 * nq), Ud(Ub.size()), UDi(2), UL_(Ub.size()), Ui(Ub.size());
+  // explicit inverses of the parity systems of small grids, [p][r][q][m]
+  const bool dense = nq <= kDenseSolveMaxNq;
+  const size_t ninv = dense ? (size_t)2 * nq * nq : 0;
+  std::vector<double> Tinv(ninv * nm), Pinv(ninv * nm), Uinv(ninv);
+  auto inverse_into = [&](const UL& f, std::vector<double>& dst, int p, int nmod, int mi) {
+    std::vector<double> y, x;
+    for (int q = 0; q < nq; ++q) {
+      y.assign(nq, 0.0);
+      y[q] = 1.0;
+      ul_solve(f, y, x);
+      for (int r = 0; r < nq; ++r) dst[(((size_t)p * nq + r) * nq + q) * nmod + mi] = x[r];
+    }
+  };
   double worst = 0.0;
   std::string why;
   for (int p = 0; p < 2; ++p) {
@@ -372,6 +385,7 @@ static rbc_status upload_tables(rbc_t h) {
       layout(TL, f.Lb, p, nq, 1, nm, m);
       for (int r = 0; r < nq; ++r) Ti[(size_t)(p * nq + r) * nm + m] = f.invd[r];
       TDi[(size_t)p * nm + m] = f.Dinv[0];
+      if (dense) inverse_into(f, Tinv, p, nm, m);
       if (m == 0) {
         // mean flow: S2 - h 4 Pr D2
         Mat U((size_t)nq * nq, 0.0);
@@ -389,6 +403,7 @@ static rbc_status upload_tables(rbc_t h) {
         layout(UL_, fu.Lb, p, nq, 1, 1, 0);
         for (int r = 0; r < nq; ++r) Ui[(size_t)p * nq + r] = fu.invd[r];
         UDi[p] = fu.Dinv[0];
+        if (dense) inverse_into(fu, Uinv, p, 1, 0);
       } else {
         // streamfunction: BC rows (ones, n^2), tau rows of M - h L in C^(4)
         Mat P((size_t)nq * nq, 0.0);
@@ -413,6 +428,7 @@ static rbc_status upload_tables(rbc_t h) {
         layout(PL, fp.Lb, p, nq, 2, nm, m);
         for (int r = 0; r < nq; ++r) Pi[(size_t)(p * nq + r) * nm + m] = fp.invd[r];
         for (int e = 0; e < 4; ++e) PDi[((size_t)p * 4 + e) * nm + m] = fp.Dinv[e];
+        if (dense) inverse_into(fp, Pinv, p, nm, m);
       }
     }
   }
@@ -455,6 +471,7 @@ static rbc_status upload_tables(rbc_t h) {
     add(packed);
   };
   add_f32(zinv); add_f32(zfwd); add_f32(tw);
+  add(Tinv); add(Pinv); add(Uinv);
   CK(cudaMalloc(&h->d_tables, buf.size() * sizeof(double)));
   CK(cudaMemcpy(h->d_tables, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
   const double* b = h->d_tables;
@@ -478,6 +495,12 @@ static rbc_status upload_tables(rbc_t h) {
   T.zinv32 = reinterpret_cast<const float*>(b + offs[i++]);
   T.zfwd32 = reinterpret_cast<const float*>(b + offs[i++]);
   T.tw32 = reinterpret_cast<const float2*>(b + offs[i++]);
+  T.T_inv = dense ? b + offs[i] : nullptr;
+  ++i;
+  T.P_inv = dense ? b + offs[i] : nullptr;
+  ++i;
+  T.U_inv = dense ? b + offs[i] : nullptr;
+  ++i;
   return RBC_OK;
 }
 
@@ -588,6 +611,7 @@ extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
 extern "C" rbc_status rbc_profile(rbc_t h, int enable) {
   if (!h) return fail(RBC_EINVAL, "null handle");
   Prof& p = h->prof;
+  if (enable < 0 || enable > 2) return fail(RBC_EINVAL, "profile mode %d", enable);
   if (enable) {
     CK(p.fold());
     for (int k = 0; k < RBC_NKERNELS; ++k) {
@@ -596,6 +620,7 @@ extern "C" rbc_status rbc_profile(rbc_t h, int enable) {
     }
   }
   p.on = enable != 0;
+  p.once = enable == 2;
   return RBC_OK;
 }
 
@@ -712,6 +737,7 @@ extern "C" rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* 
     }
   }
   if (maxs > 0) CK(launch_nu_final(h->g, h->t, w, X, B, nu, stream));
+  if (h->prof.once) h->prof.on = h->prof.once = false;   // sampled profiling: this call only
   return RBC_OK;
 }
 

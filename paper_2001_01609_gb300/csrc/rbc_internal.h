@@ -9,6 +9,9 @@
 
 namespace rbc {
 
+// Largest coefficient count per Chebyshev parity solved with explicit inverses.
+constexpr int kDenseSolveMaxNq = 16;
+
 // Grid and physical parameters, passed to kernels by value.
 struct Grid {
   int Nx, Nz;     // native resolution (Fourier points, Chebyshev points)
@@ -44,6 +47,11 @@ struct Tables {
   const double* Vn;     // [Nz][Nz]  T_n(s_j) at the native points
   const double* Vn1;    // [Nz][Nz]  T_n'(s_j)
   const double* Wn;     // [Nz][Nz]  native values -> T coefficients (exact interpolation)
+  // Explicit inverses of the parity systems, [2][nq][nq][nmod], built for grids
+  // with nq <= kDenseSolveMaxNq only (otherwise nullptr): small systems are
+  // solved by a parallel matrix-vector product instead of the sequential UL
+  // recurrences, whose FP64 dependency chain dominates their latency.
+  const double *T_inv, *P_inv, *U_inv;
   // FP32 copies of the transform tables (RBC_MIXED)
   const float* zinv32;  // [4][Mz][Nz]
   const float* zfwd32;  // [Nz][Mz]
@@ -55,6 +63,7 @@ struct Tables {
 // folded into the totals so that the pool can be reused.
 struct Prof {
   bool on = false;
+  bool once = false;             // record the next rbc_step_batch call only
   std::vector<cudaEvent_t> ev;   // 2 per record
   std::vector<int> kind;         // kind of each recorded pair
   size_t used = 0;

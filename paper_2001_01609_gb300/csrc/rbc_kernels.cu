@@ -661,17 +661,35 @@ __device__ __forceinline__ bool solve_recurrence(const Grid& g, const Tables& tb
   const double* multB = SY::multB(tb);
   const double* multD = SY::multD(tb);
   auto tix = [&](int cc, int jj) { return ((size_t)(p * nq + cc) * D + jj) * nmod + mi; };
+  // The factor entries of RC consecutive steps are loaded together before the
+  // steps run, so the sequential chain does not wait on one load per step.
+  constexpr int RC = 8;
   double pend[D], bd[D];
 #pragma unroll
   for (int jj = 0; jj < D; ++jj) pend[jj] = bd[jj] = 0.0;
-  for (int cc = nq - 1; cc >= D; --cc) {
-    const double bc = sm.y[cc * W + col] + pend[0];
-    sm.y[cc * W + col] = bc;
+  for (int c0 = nq - 1; c0 >= D; c0 -= RC) {
+    double mb[RC][D], md[RC][D];
 #pragma unroll
-    for (int jj = 0; jj < D - 1; ++jj) pend[jj] = fma(-__ldg(multB + tix(cc, D - 1 - jj)), bc, pend[jj + 1]);
-    pend[D - 1] = -__ldg(multB + tix(cc, 0)) * bc;
+    for (int k = 0; k < RC; ++k) {
+      const int cc = c0 - k;
 #pragma unroll
-    for (int r2 = 0; r2 < D; ++r2) bd[r2] = fma(-__ldg(multD + tix(cc, r2)), bc, bd[r2]);
+      for (int jj = 0; jj < D; ++jj) {
+        mb[k][jj] = (cc >= D) ? __ldg(multB + tix(cc, jj)) : 0.0;
+        md[k][jj] = (cc >= D) ? __ldg(multD + tix(cc, jj)) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+      const int cc = c0 - k;
+      if (cc < D) break;
+      const double bc = sm.y[cc * W + col] + pend[0];
+      sm.y[cc * W + col] = bc;
+#pragma unroll
+      for (int jj = 0; jj < D - 1; ++jj) pend[jj] = fma(-mb[k][D - 1 - jj], bc, pend[jj + 1]);
+      pend[D - 1] = -mb[k][0] * bc;
+#pragma unroll
+      for (int r2 = 0; r2 < D; ++r2) bd[r2] = fma(-md[k][r2], bc, bd[r2]);
+    }
   }
   // boundary rows (Eq. 6): parity combinations of f(1) +- f(-1)
   if (KIND == KT && m == 0 && c == 0) bd[0] += (p == 0) ? 0.5 : -0.5;   // T(-1/2) = 1, T(1/2) = 0
@@ -691,33 +709,72 @@ __device__ __forceinline__ bool solve_recurrence(const Grid& g, const Tables& tb
     if (KIND == KT) sm.T[r2 * W + col] = x;
     ok = ok && isfinite(x);
   }
-  for (int r2 = D; r2 < nq; ++r2) {
-    double y = sm.y[r2 * W + col];
+  for (int r0 = D; r0 < nq; r0 += RC) {
+    double lb[RC][D], iv[RC];
 #pragma unroll
-    for (int jj = 0; jj < D; ++jj) y = fma(-__ldg(Lb + tix(r2, jj)), win[jj], y);
-    const double x = __ldg(invd + (size_t)(p * nq + r2) * nmod + mi) * y;
-    sm.y[r2 * W + col] = x;
-    Xo[soff(g, f, 2 * r2 + p, m) + c] = x;
-    if (KIND == KT) sm.T[r2 * W + col] = x;
+    for (int k = 0; k < RC; ++k) {
+      const int r2 = r0 + k;
 #pragma unroll
-    for (int jj = 0; jj < D - 1; ++jj) win[jj] = win[jj + 1];
-    win[D - 1] = x;
-    ok = ok && isfinite(x);
+      for (int jj = 0; jj < D; ++jj) lb[k][jj] = (r2 < nq) ? __ldg(Lb + tix(r2, jj)) : 0.0;
+      iv[k] = (r2 < nq) ? __ldg(invd + (size_t)(p * nq + r2) * nmod + mi) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+      const int r2 = r0 + k;
+      if (r2 >= nq) break;
+      double y = sm.y[r2 * W + col];
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) y = fma(-lb[k][jj], win[jj], y);
+      const double x = iv[k] * y;
+      sm.y[r2 * W + col] = x;
+      Xo[soff(g, f, 2 * r2 + p, m) + c] = x;
+      if (KIND == KT) sm.T[r2 * W + col] = x;
+#pragma unroll
+      for (int jj = 0; jj < D - 1; ++jj) win[jj] = win[jj + 1];
+      win[D - 1] = x;
+      ok = ok && isfinite(x);
+    }
   }
   return ok;
+}
+
+// phases 2-3 for small grids: x_r = sum_q Ainv[r][q] b_q for one (row r, column
+// col); b holds the boundary values in rows 0 .. D-1 and the tau right-hand
+// sides below them.
+template <int KIND>
+__device__ __forceinline__ bool solve_dense(const Grid& g, const Tables& tb, int p, int m, int c, int r, int col,
+                                            const SolveSmem& sm, double* __restrict__ Xo) {
+  const int nq = g.nq, W = sm.W;
+  const int f = (KIND == KT) ? 0 : 1;
+  const int nmod = (KIND == KU) ? 1 : g.nm;
+  const int mi = (KIND == KU) ? 0 : m;
+  const double* inv = (KIND == KT) ? tb.T_inv : (KIND == KP) ? tb.P_inv : tb.U_inv;
+  const double* row = inv + ((size_t)p * nq + r) * nq * nmod + mi;
+  double acc0 = 0.0, acc1 = 0.0;                       // two partial sums: shorter chain
+  for (int q = 0; q + 1 < nq; q += 2) {
+    acc0 = fma(__ldg(row + (size_t)q * nmod), sm.y[q * W + col], acc0);
+    acc1 = fma(__ldg(row + (size_t)(q + 1) * nmod), sm.y[(q + 1) * W + col], acc1);
+  }
+  if (nq & 1) acc0 = fma(__ldg(row + (size_t)(nq - 1) * nmod), sm.y[(nq - 1) * W + col], acc0);
+  const double x = acc0 + acc1;
+  sm.X[r * W + col] = x;
+  Xo[soff(g, f, 2 * r + p, m) + c] = x;
+  if (KIND == KT) sm.T[r * W + col] = x;
+  return isfinite(x);
 }
 
 // phase 4 for one (tau row t, column col)
 template <int KIND>
 __device__ __forceinline__ void solve_lx(const Grid& g, const Tables& tb, int stage, int p, int m, int c, int t,
-                                         int col, const SolveSmem& sm, double* __restrict__ R, size_t S) {
+                                         int col, const SolveSmem& sm, const double* xs, double* __restrict__ R,
+                                         size_t S) {
   using SY = Sys<KIND>;
   const int nq = g.nq, W = sm.W;
   const int f = (KIND == KT) ? 0 : 1;
   double mx = 0.0;
 #pragma unroll
   for (int j = 0; j <= SY::LAM; ++j)
-    if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), sm.y[(t + j) * W + col], mx);
+    if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), xs[(t + j) * W + col], mx);
   const double lx2 = 2.0 * (mx - sm.r[t * W + col]);
   const size_t ro = soff(g, f, 2 * t + p, m) + c;
 #pragma unroll
@@ -730,7 +787,7 @@ __device__ __forceinline__ void solve_lx(const Grid& g, const Tables& tb, int st
 
 __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* Xs, const double* F, double* R,
                            size_t S, const double* wT, double* nu, int* flags, int B, int stage, int tms,
-                           bool sparse, const int* nsteps, int stepidx, int blk) {
+                           const int* nsteps, int stepidx, int blk) {
   extern __shared__ double sbuf[];
   const int mt = (g.nm + tms - 1) / tms;
   const int b = blk / (2 * mt);
@@ -791,12 +848,37 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
         solve_rhs<KP>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
     }
     __syncthreads();
-    // phases 2, 3: one column per thread, spread over all warps so that each
-    // warp has few active lanes (a full-warp FP64 instruction costs ~64 cycles)
-    const int nw = blockDim.x >> 5;
-    const int rcol = sparse ? (int)(threadIdx.x & 31) * nw + (int)(threadIdx.x >> 5) : (int)threadIdx.x;
-    if (rcol < ncol) {
-      const int col = rcol, m = m0 + col / 2, c = col & 1;
+    const bool dense = g.nq <= kDenseSolveMaxNq;
+    if (dense) {
+      // boundary rows of b (Eq. 6): T(-1/2) = 1, T(1/2) = 0 in the parity
+      // combinations f(1) +- f(-1); zero for T at m >= 1, psi and U
+      for (int it = threadIdx.x; it < 2 * W; it += blockDim.x) {
+        const int r = it / W, col = it - r * W;
+        if (col >= ncol) continue;
+        const int m = m0 + col / 2, c = col & 1;
+        const int D = (sys == 1 && m != 0) ? 2 : 1;
+        if (r >= D) continue;
+        sm.y[r * W + col] = (sys == 0 && m == 0 && c == 0) ? ((p == 0) ? 0.5 : -0.5) : 0.0;
+      }
+      __syncthreads();
+      for (int it = threadIdx.x; it < nq * W; it += blockDim.x) {
+        const int r = it / W, col = it - r * W;
+        if (col >= ncol) continue;
+        const int m = m0 + col / 2, c = col & 1;
+        bool o2;
+        if (sys == 0)
+          o2 = solve_dense<KT>(g, tb, p, m, c, r, col, sm, Xo);
+        else if (m == 0)
+          o2 = solve_dense<KU>(g, tb, p, m, c, r, col, sm, Xo);
+        else
+          o2 = solve_dense<KP>(g, tb, p, m, c, r, col, sm, Xo);
+        ok = ok && o2;
+      }
+    } else if ((int)threadIdx.x < ncol) {
+      // phases 2, 3: one column per thread, columns packed into the fewest warps
+      // (an FP64 warp instruction occupies its sub-partition's FP64 pipe for the
+      // same time however many lanes are active, so packing is cheapest)
+      const int col = threadIdx.x, m = m0 + col / 2, c = col & 1;
       bool o2;
       if (sys == 0)
         o2 = solve_recurrence<KT>(g, tb, p, m, c, col, sm, Xo);
@@ -807,6 +889,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
       ok = ok && o2;
     }
     __syncthreads();
+    const double* xs = dense ? sm.X : sm.y;
     // phase 4
     if (stage < 4) {
       for (int it = threadIdx.x; it < ntmax * W; it += blockDim.x) {
@@ -814,11 +897,11 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
         if (col >= ncol) continue;
         const int m = m0 + col / 2, c = col & 1;
         if (sys == 0)
-          solve_lx<KT>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+          solve_lx<KT>(g, tb, stage, p, m, c, t, col, sm, xs, Rb, S);
         else if (m == 0)
-          solve_lx<KU>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+          solve_lx<KU>(g, tb, stage, p, m, c, t, col, sm, xs, Rb, S);
         else if (t < nq - 2)
-          solve_lx<KP>(g, tb, stage, p, m, c, t, col, sm, Rb, S);
+          solve_lx<KP>(g, tb, stage, p, m, c, t, col, sm, xs, Rb, S);
       }
     }
     __syncthreads();
@@ -828,9 +911,8 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
 
 __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, double* Xs, const double* F, double* R,
                                                size_t S, const double* wT, double* nu, int* flags, int B, int stage,
-                                               int tms, int sparse, const int* nsteps, const int* step) {
-  solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, B, stage, tms, sparse != 0, nsteps, nsteps ? *step : 0,
-                    blockIdx.x);
+                                               int tms, const int* nsteps, const int* step) {
+  solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, B, stage, tms, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
 static int solve_tile(const Grid& g, int B) {
@@ -990,9 +1072,8 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   const int tms = solve_tile(g, B);
   const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
-  const int sparse = (B * 2 * mtiles < 152) ? 1 : 0;
   k_solve<<<(unsigned)(B * 2 * mtiles), 256, solve_smem(g, B), s>>>(g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags,
-                                                                    B, stage, tms, sparse, w.nsteps, w.step);
+                                                                    B, stage, tms, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);
   return cudaGetLastError();

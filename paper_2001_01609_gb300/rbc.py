@@ -168,8 +168,9 @@ class Propagator:
         _check(load().rbc_nusselt(self.h, _ptr(state), _dptr(out), _stream(stream)))
         return tuple(out)
 
-    def profile(self, enable=True):
-        _check(load().rbc_profile(self.h, 1 if enable else 0))
+    def profile(self, enable=True, sample=False):
+        """Per-kernel CUDA-event timing: all calls, or the next rbc_step_batch call only."""
+        _check(load().rbc_profile(self.h, (2 if sample else 1) if enable else 0))
 
     def profile_read(self):
         K = len(KERNEL_NAMES)
