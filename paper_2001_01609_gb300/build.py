@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librbc.so")
-SOURCES = ["rbc_host.cpp", "rbc_kernels.cu"]
+SOURCES = ["rbc_host.cpp", "rbc_kernels.cu", "rbc_tcgen05.cu"]
 HEADERS = ["rbc_internal.h", os.path.join("..", "..", "include", "rbc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-Xptxas", "-v"]

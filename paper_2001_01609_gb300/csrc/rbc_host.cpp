@@ -472,6 +472,22 @@ static rbc_status upload_tables(rbc_t h) {
   };
   add_f32(zinv); add_f32(zfwd); add_f32(tw);
   add(Tinv); add(Pinv); add(Uinv);
+  // tensor-core z-inverse operator images (mixed precision only)
+  const bool tc = g.mixed && tc_zinv_supported(g);
+  auto add_floats = [&](const std::vector<float>& v) {
+    std::vector<double> packed((v.size() + 1) / 2, 0.0);
+    memcpy(packed.data(), v.data(), v.size() * sizeof(float));
+    add(packed);
+  };
+  {
+    std::vector<float> ph(tc ? tc_zinv_image_floats(g, 4) : 0), pl(ph.size());
+    std::vector<float> th(tc ? tc_zinv_image_floats(g, 2) : 0), tl(th.size());
+    if (tc) {
+      tc_zinv_build_images(g, zinv.data(), 4, ph.data(), pl.data());
+      tc_zinv_build_images(g, zinv.data(), 2, th.data(), tl.data());
+    }
+    add_floats(ph); add_floats(pl); add_floats(th); add_floats(tl);
+  }
   CK(cudaMalloc(&h->d_tables, buf.size() * sizeof(double)));
   CK(cudaMemcpy(h->d_tables, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
   const double* b = h->d_tables;
@@ -500,6 +516,14 @@ static rbc_status upload_tables(rbc_t h) {
   T.P_inv = dense ? b + offs[i] : nullptr;
   ++i;
   T.U_inv = dense ? b + offs[i] : nullptr;
+  ++i;
+  T.tcA_psi_hi = tc ? reinterpret_cast<const float*>(b + offs[i]) : nullptr;
+  ++i;
+  T.tcA_psi_lo = tc ? reinterpret_cast<const float*>(b + offs[i]) : nullptr;
+  ++i;
+  T.tcA_T_hi = tc ? reinterpret_cast<const float*>(b + offs[i]) : nullptr;
+  ++i;
+  T.tcA_T_lo = tc ? reinterpret_cast<const float*>(b + offs[i]) : nullptr;
   ++i;
   return RBC_OK;
 }

@@ -56,6 +56,9 @@ struct Tables {
   const float* zinv32;  // [4][Mz][Nz]
   const float* zfwd32;  // [Nz][Mz]
   const float2* tw32;   // [Mx]
+  // tensor-core z-inverse operands (RBC_MIXED): TF32 hi/lo images of the
+  // interleaved operator rows, pre-swizzled per 128-row tile and 32-wide K-chunk
+  const float *tcA_psi_hi, *tcA_psi_lo, *tcA_T_hi, *tcA_T_lo;
 };
 
 // Optional per-kernel CUDA-event timing (host side).  Event pairs come from a
@@ -131,5 +134,13 @@ unsigned long long launches_so_far();
 void add_launches(unsigned long long n);   // kernels launched through a replayed graph
 constexpr int kStepKernels = 17;           // 4 stages x 4 kernels + step counter
 cudaError_t configure_kernels(const Grid& g);
+// tensor-core z inverse transform (rbc_tcgen05.cu)
+RBC_HD int tc_zinv_mtiles(const Grid& g, int nops);
+RBC_HD int tc_zinv_kchunks(const Grid& g);
+size_t tc_zinv_image_floats(const Grid& g, int nops);
+void tc_zinv_build_images(const Grid& g, const double* zinv, int nops, float* hi, float* lo);
+bool tc_zinv_supported(const Grid& g);
+cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const double* X, int B, const int* ns,
+                           cudaStream_t s);
 
 }  // namespace rbc

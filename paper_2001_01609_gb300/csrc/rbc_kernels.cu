@@ -1017,15 +1017,18 @@ cudaError_t configure_kernels(const Grid& g) {
 }
 
 template <typename T>
-static void launch_transforms_in(const Grid& g, const T* Bz, const C2<T>* tw, const Work& w, const double* X, int B,
-                                 const int* ns, Prof* pf, cudaStream_t s) {
+static void launch_transforms_in(const Grid& g, const Tables& t, const T* Bz, const C2<T>* tw, const Work& w,
+                                 const double* X, int B, const int* ns, Prof* pf, cudaStream_t s) {
   const size_t S = state_doubles(g);
   const int kp = zinv_warps(g);
   const unsigned zb = (unsigned)(B * ((g.Mz + 1) / 2) * ((g.nm + 31) / 32));
   T* Z = reinterpret_cast<T*>(w.Z);
   T* Q = reinterpret_cast<T*>(w.Q);
   if (pf) pf->begin(RBC_KERNEL_ZINV, s);
-  k_zinv<T><<<zb, 32 * kp, kp > 1 ? (size_t)kp * 12 * 32 * 2 * sizeof(T) : 0, s>>>(g, Bz, X, S, Z, B, ns, w.step);
+  if (sizeof(T) == 4 && t.tcA_psi_hi != nullptr)
+    launch_zinv_tc(g, t, w, X, B, ns, s);              // tensor cores, TF32 with split compensation
+  else
+    k_zinv<T><<<zb, 32 * kp, kp > 1 ? (size_t)kp * 12 * 32 * 2 * sizeof(T) : 0, s>>>(g, Bz, X, S, Z, B, ns, w.step);
   if (pf) pf->end(RBC_KERNEL_ZINV, s, zinv_flops(g, B), zinv_bytes(g, B, sizeof(T)));
   const size_t es = sizeof(T);
   if (pf) pf->begin(RBC_KERNEL_ROWS, s);
@@ -1039,9 +1042,9 @@ cudaError_t launch_explicit(const Grid& g, const Tables& t, const Work& w, const
   const int* ns = all_active ? nullptr : w.nsteps;
   Prof* pf = (w.prof && w.prof->on && !all_active) ? w.prof : nullptr;
   if (g.mixed)
-    launch_transforms_in<float>(g, t.zinv32, t.tw32, w, X, B, ns, pf, s);
+    launch_transforms_in<float>(g, t, t.zinv32, t.tw32, w, X, B, ns, pf, s);
   else
-    launch_transforms_in<double>(g, t.zinv, t.tw, w, X, B, ns, pf, s);
+    launch_transforms_in<double>(g, t, t.zinv, t.tw, w, X, B, ns, pf, s);
   count(2);
   return cudaGetLastError();
 }

@@ -1,0 +1,348 @@
+// Tensor-core (tcgen05) z inverse transform for the mixed-precision path.
+//
+// The z inverse transform of one slice and one field is a dense contraction:
+// C[(j, op)][col] = sum_n A[(j, op)][n] X[n][col], with A the values of
+// d^q T_n / ds^q at the padded Lobatto points (rows interleaved as j * nops + op,
+// nops = 4 for psi: V, VD, VD^2, VD^3; nops = 2 for T: V, VD) and X the state's
+// Chebyshev coefficients (columns = Fourier mode x real/imaginary part).  It runs
+// on the 5th-generation tensor cores with TF32 operands and split compensation:
+// a = a_hi + a_lo, x = x_hi + x_lo (each a TF32 value), and
+// A X ~ A_hi X_hi + A_hi X_lo + A_lo X_hi, accumulated in FP32 in tensor memory,
+// which keeps about FP32 accuracy (the mixed mode computes the transforms and
+// products in FP32).
+//
+// CTA per (slice, field, tile of 64 columns).  The X tile (all K) is converted
+// from FP64 into hi/lo TF32 operands in shared memory once; for each 128-row
+// tile of A the K-chunks of A (pre-swizzled images built on the host) are
+// staged in shared memory, one thread issues the MMAs, and the four warps read
+// the 128 x 64 FP32 accumulator from tensor memory and form the fields of the
+// z-inverse output with the ik factors (the epilogue of k_zinv).
+// Operands are K-major with the 128-byte swizzle; every mbarrier wait is bounded
+// and reports through the slice's error flag.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "rbc_internal.h"
+
+namespace rbc {
+
+namespace {
+
+constexpr int kTileN = 64;       // columns per CTA (32 Fourier modes x re/im)
+constexpr int kTileM = 128;      // rows per MMA tile
+constexpr int kChunkK = 32;      // TF32 elements per 128-byte swizzle row
+constexpr long kWaitLimit = 1L << 24;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) (k < 32) in a K-major, 128B-swizzled tile
+__device__ __forceinline__ uint32_t swz(int r, int k) {
+  return (uint32_t)(r * 128 + ((((k * 4) >> 4) ^ (r & 7)) << 4) + ((k * 4) & 15));
+}
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  const uint64_t lbo = 16, sbo = 1024;
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
+// instruction descriptor: kind::tf32, FP32 accumulator, K-major A and B, M x N
+__device__ __forceinline__ uint32_t instr_desc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar)));
+}
+
+// bounded wait for the completion of phase `parity` of an mbarrier
+__device__ __forceinline__ bool wait_parity(uint64_t* mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < kWaitLimit; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(saddr(mbar)), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ size_t soff2(const Grid& g, int f, int n, int m) {
+  return ((size_t)(f * g.Nz + n) * g.nm + m) * 2;
+}
+
+__device__ __forceinline__ void store_c(float* Zb, const Grid& g, int field, int j, int m, float re, float im) {
+  const size_t fs = (size_t)g.Mz * g.nm * 2;
+  *reinterpret_cast<float2*>(Zb + field * fs + ((size_t)j * g.nm + m) * 2) = make_float2(re, im);
+}
+
+}  // namespace
+
+// Number of 128-row tiles and K-chunks of the operator images (host and device agree).
+__host__ __device__ int tc_zinv_mtiles(const Grid& g, int nops) { return (nops * g.Mz + kTileM - 1) / kTileM; }
+__host__ __device__ int tc_zinv_kchunks(const Grid& g) { return (g.Nz + kChunkK - 1) / kChunkK; }
+size_t tc_zinv_image_floats(const Grid& g, int nops) {
+  return (size_t)tc_zinv_mtiles(g, nops) * tc_zinv_kchunks(g) * kTileM * kChunkK;
+}
+
+// Pre-swizzled hi/lo operator images for field f (nops operators per row j),
+// [mtile][kchunk][128 x 32 swizzled].  d[q][j][n] = d^q T_n / ds^q at s_j.
+void tc_zinv_build_images(const Grid& g, const double* zinv, int nops, float* hi, float* lo) {
+  const int mt = tc_zinv_mtiles(g, nops), kc = tc_zinv_kchunks(g);
+  for (int t = 0; t < mt; ++t)
+    for (int c = 0; c < kc; ++c) {
+      float* bh = hi + ((size_t)t * kc + c) * kTileM * kChunkK;
+      float* bl = lo + ((size_t)t * kc + c) * kTileM * kChunkK;
+      for (int r = 0; r < kTileM; ++r)
+        for (int k = 0; k < kChunkK; ++k) {
+          const int row = t * kTileM + r, j = row / nops, q = row % nops, n = c * kChunkK + k;
+          double v = 0.0;
+          if (j < g.Mz && n < g.Nz) v = zinv[((size_t)q * g.Mz + j) * g.Nz + n];
+          // TF32 split: hi = v rounded to 10 mantissa bits, lo = the rest
+          float f = (float)v;
+          uint32_t u;
+          memcpy(&u, &f, 4);
+          u = (u + 0x1000u) & 0xFFFFE000u;
+          float h;
+          memcpy(&h, &u, 4);
+          float l = (float)(v - (double)h);
+          memcpy(&u, &l, 4);
+          u = (u + 0x1000u) & 0xFFFFE000u;
+          memcpy(&l, &u, 4);
+          const int off = r * 128 + ((((k * 4) >> 4) ^ (r & 7)) << 4) + ((k * 4) & 15);
+          bh[off / 4] = h;
+          bl[off / 4] = l;
+        }
+    }
+}
+
+size_t tc_zinv_smem_bytes(const Grid& g) {
+  const int kc = tc_zinv_kchunks(g);
+  // X tile hi/lo (all K), two buffers of the A chunk hi/lo, alignment slack
+  return (size_t)kc * kTileN * 128 * 2 + 2 * 2 * (size_t)kTileM * 128 + 1024;
+}
+
+// Output fields: psi (nops = 4): u, w, d_x omega, d_z omega, d_x u, d_z u (0..5);
+// T (nops = 2): T, d_x T, d_z T (6..8).
+__global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict__ Ahi_psi,
+                                                 const float* __restrict__ Alo_psi, const float* __restrict__ Ahi_T,
+                                                 const float* __restrict__ Alo_T, const double* __restrict__ X,
+                                                 size_t S, float* __restrict__ Z, int B, const int* nsteps,
+                                                 const int* step, int* flags) {
+  extern __shared__ __align__(1024) unsigned char tc_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t mbar[3];   // 0, 1: A-chunk buffers free; 2: accumulator ready
+  __shared__ uint32_t tmem_base;
+  const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
+  const int b = blockIdx.x / (2 * ntile);
+  const int rem = blockIdx.x - b * 2 * ntile;
+  const int fsel = rem / ntile;               // 0: psi (nops 4), 1: T (nops 2)
+  const int c0 = (rem - fsel * ntile) * kTileN;
+  if (b >= B || !(nsteps == nullptr || *step < nsteps[b])) return;   // uniform per block
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nops = fsel == 0 ? 4 : 2;
+  const int f = fsel == 0 ? 1 : 0;            // state field: psi slot 1, T slot 0
+  const float* Ahi = fsel == 0 ? Ahi_psi : Ahi_T;
+  const float* Alo = fsel == 0 ? Alo_psi : Alo_T;
+  const int kc = tc_zinv_kchunks(g), mtiles = tc_zinv_mtiles(g, nops);
+  unsigned char* sXhi = base;
+  unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
+  unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [buf][hi, lo][128 x 128 B]
+  // X tile -> hi/lo TF32 operands, K-major (row = column of the tile, k = n)
+  const double* Xb = X + (size_t)b * S;
+  for (int it = tid; it < kc * kChunkK * kTileN; it += blockDim.x) {
+    const int n = it / kTileN, col = it - n * kTileN;
+    const int gc = c0 + col;
+    float x = 0.f;
+    if (n < g.Nz && gc < 2 * g.nm) x = (float)Xb[soff2(g, f, n, gc >> 1) + (gc & 1)];
+    const uint32_t h = to_tf32(x);
+    const uint32_t l = to_tf32(x - __uint_as_float(h));
+    const uint32_t o = (uint32_t)(n / kChunkK) * kTileN * 128 + swz(col, n % kChunkK);
+    *reinterpret_cast<uint32_t*>(sXhi + o) = h;
+    *reinterpret_cast<uint32_t*>(sXlo + o) = l;
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[i])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
+  uint32_t use[2] = {0, 0};                   // completions of each A buffer already waited for
+  uint32_t issued[2] = {0, 0};                // commits issued on each A buffer
+  uint32_t acc_phase = 0;
+  bool ok = true;
+  float* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
+  const int rows_per_j = nops, jper = kTileM / nops;
+  for (int t = 0; t < mtiles && ok; ++t) {
+    for (int c = 0; c < kc && ok; ++c) {
+      const int gidx = t * kc + c, buf = gidx & 1;
+      if (gidx >= 2) {                        // buffer free once its previous MMAs completed
+        ok = wait_parity(&mbar[buf], use[buf] & 1);
+        use[buf]++;
+        if (!ok) break;
+      }
+      unsigned char* ah = sA + (size_t)buf * 2 * kTileM * 128;
+      unsigned char* al = ah + (size_t)kTileM * 128;
+      const float4* gh = reinterpret_cast<const float4*>(Ahi + (size_t)gidx * kTileM * kChunkK);
+      const float4* gl = reinterpret_cast<const float4*>(Alo + (size_t)gidx * kTileM * kChunkK);
+      for (int i = tid; i < kTileM * kChunkK / 4; i += blockDim.x) {
+        reinterpret_cast<float4*>(ah)[i] = __ldg(gh + i);
+        reinterpret_cast<float4*>(al)[i] = __ldg(gl + i);
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
+        const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
+        for (int ks = 0; ks < kChunkK / 8; ++ks) {
+          const uint32_t o = ks * 32;
+          const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
+          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
+          mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
+        }
+        commit(&mbar[buf]);
+        if (c == kc - 1) commit(&mbar[2]);
+      }
+      issued[buf]++;
+    }
+    if (!ok) break;
+    // accumulator of tile t ready
+    ok = wait_parity(&mbar[2], acc_phase & 1);
+    acc_phase++;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) break;
+    const int r = warp * 32 + lane;           // tile row = TMEM lane
+    const int jl = r / rows_per_j, op = r % rows_per_j;
+    const int j = t * jper + jl;
+    for (int cc = 0; cc < kTileN; cc += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
+      float P[4][16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int src = (lane & ~(rows_per_j - 1)) | (q & (rows_per_j - 1));
+          P[q][i] = __shfl_sync(0xffffffffu, v[i], src);
+        }
+      if (j >= g.Mz) continue;
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        const int gc = c0 + cc + i;
+        if (gc >= 2 * g.nm) break;
+        const int m = gc >> 1;
+        const float k = (float)(g.kfac * m);
+        if (nops == 4) {
+          // P[q] = (re, im) of d^q psi/ds^q (m = 0: of U)
+          const float p0r = P[0][i], p0i = P[0][i + 1], p1r = P[1][i], p1i = P[1][i + 1];
+          const float p2r = P[2][i], p2i = P[2][i + 1], p3r = P[3][i], p3i = P[3][i + 1];
+          if (m == 0) {
+            if (op == 0) {
+              store_c(Zb, g, 0, j, 0, p0r, 0.f);            // u = U
+              store_c(Zb, g, 1, j, 0, 0.f, 0.f);            // w
+            } else if (op == 1) {
+              store_c(Zb, g, 2, j, 0, 0.f, 0.f);            // d_x omega
+              store_c(Zb, g, 3, j, 0, -4.f * p2r, 0.f);     // d_z omega = -U_zz
+            } else if (op == 2) {
+              store_c(Zb, g, 4, j, 0, 0.f, 0.f);            // d_x u
+              store_c(Zb, g, 5, j, 0, 2.f * p1r, 0.f);      // d_z u = U_z
+            }
+          } else if (op == 0) {
+            store_c(Zb, g, 0, j, m, 2.f * p1r, 2.f * p1i);  // u = d_z psi
+            store_c(Zb, g, 1, j, m, k * p0i, -k * p0r);     // w = -ik psi
+          } else if (op == 1) {
+            const float omr = k * k * p0r - 4.f * p2r, omi = k * k * p0i - 4.f * p2i;
+            store_c(Zb, g, 2, j, m, -k * omi, k * omr);     // d_x omega = ik omega
+            store_c(Zb, g, 3, j, m, 2.f * k * k * p1r - 8.f * p3r, 2.f * k * k * p1i - 8.f * p3i);
+          } else if (op == 2) {
+            store_c(Zb, g, 4, j, m, -k * 2.f * p1i, k * 2.f * p1r);   // d_x u = ik u
+            store_c(Zb, g, 5, j, m, 4.f * p2r, 4.f * p2i);            // d_z u
+          }
+        } else {
+          const float tr = P[0][i], ti = P[0][i + 1], dr = P[1][i], di = P[1][i + 1];
+          if (op == 0) {
+            store_c(Zb, g, 6, j, m, tr, ti);                          // T
+            store_c(Zb, g, 7, j, m, m == 0 ? 0.f : -k * ti, m == 0 ? 0.f : k * tr);   // d_x T
+          } else {
+            store_c(Zb, g, 8, j, m, 2.f * dr, 2.f * di);              // d_z T
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();                          // accumulator read before the next tile overwrites it
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (!ok && tid == 0) flags[b] = 2;          // a bounded wait gave up
+  // drain: let outstanding MMAs finish (bounded) before freeing tensor memory
+  if (tid == 0) {
+    for (int bb = 0; bb < 2; ++bb)
+      while (use[bb] < issued[bb]) {
+        if (!wait_parity(&mbar[bb], use[bb] & 1)) break;
+        use[bb]++;
+      }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
+cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const double* X, int B, const int* ns,
+                           cudaStream_t s) {
+  static int allowed = 48 * 1024;
+  const size_t smem = tc_zinv_smem_bytes(g);
+  if ((int)smem > allowed) {
+    cudaError_t e = cudaFuncSetAttribute(k_zinv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    allowed = (int)smem;
+  }
+  const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
+  k_zinv_tc<<<(unsigned)(B * 2 * ntile), 128, smem, s>>>(g, t.tcA_psi_hi, t.tcA_psi_lo, t.tcA_T_hi, t.tcA_T_lo, X,
+                                                         state_doubles(g), reinterpret_cast<float*>(w.Z), B, ns,
+                                                         w.step, w.flags);
+  return cudaGetLastError();
+}
+
+bool tc_zinv_supported(const Grid& g) { return tc_zinv_smem_bytes(g) <= 200 * 1024; }
+
+}  // namespace rbc
