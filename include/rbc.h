@@ -108,6 +108,14 @@ rbc_status rbc_get_state(rbc_t h, const void* d_state, double* h_T, double* h_u,
 rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps,
                           double* d_nu_integral, cudaStream_t stream);
 
+/* rbc_step_batch_ra: rbc_step_batch with a Rayleigh number per state,
+ * h_ra[b] (host double[B], each >= 0).  The implicit operators and their
+ * factors do not depend on Ra (it enters the stage systems only through the
+ * buoyancy coupling, Eq. 3), so one handle serves states of any Ra; the
+ * handle's own Ra is ignored by this call.                                 */
+rbc_status rbc_step_batch_ra(rbc_t h, void* d_states, int B, const int* h_nsteps, const double* h_ra,
+                             double* d_nu_integral, cudaStream_t stream);
+
 /* Synchronises `stream`; RBC_EDIVERGED if any state of the batch went
  * non-finite since the last rbc_step_batch, else RBC_OK.                   */
 rbc_status rbc_check_diverged(rbc_t h, cudaStream_t stream);
@@ -138,6 +146,22 @@ rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double out[3], cudaS
 
 /* ||T||_{L2(Omega)} of one device state (exact in x and z), host out.       */
 rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream);
+
+/* Building blocks of Eq. 20 for callers that drive Parareal themselves (the
+ * serving engine interleaves many runs).  All act on B contiguous states on
+ * `stream`, asynchronously; the coarse grid must be no finer than the fine.
+ *  rbc_restrict:  coarse[b] = fine[b] truncated to the coarse modes (Sec. 3.6).
+ *  rbc_prolong:   fine[b] = coarse[b] zero-padded to the fine modes.
+ *  rbc_parareal_correct: U[b] = F[b] + (prolong(Gnew[b]) - prolong(Gold[b])),
+ *                 elementwise in that order (fine F, U; coarse Gnew, Gold).
+ *  rbc_l2_diff:   d_out[b] = ||A[b] - B[b]||^2 of the temperature field (L2 over
+ *                 the domain, exact), or ||A[b]||^2 when d_B is NULL; device
+ *                 double[B].                                                */
+rbc_status rbc_restrict(rbc_t fine, rbc_t coarse, const void* d_fine, void* d_coarse, int B, cudaStream_t stream);
+rbc_status rbc_prolong(rbc_t fine, rbc_t coarse, const void* d_coarse, void* d_fine, int B, cudaStream_t stream);
+rbc_status rbc_parareal_correct(rbc_t fine, rbc_t coarse, const void* d_F, const void* d_Gnew, const void* d_Gold,
+                                void* d_U, int B, cudaStream_t stream);
+rbc_status rbc_l2_diff(rbc_t h, const void* d_A, const void* d_B, int B, double* d_out, cudaStream_t stream);
 
 /* Parareal (Sec. 3.1, Eq. 20).  fine and coarse share Ra, Pr, Lx; the coarse
  * grid is no finer than the fine one.  [t0, t1] is cut into nslices equal

@@ -240,6 +240,15 @@ struct rbc_s {
   Work w{};
   double* d_scratch = nullptr;   // set/get state and diagnostics, independent of B
   int last_B = 0;
+  // Pinned staging of each call's host arrays (Ra, step counts): a ring of
+  // slots, each reused only after the copy that last read it has run, so the
+  // host can queue several calls ahead of the device.
+  static constexpr int kPinSlots = 8;
+  char* pin = nullptr;
+  size_t pin_slot = 0;
+  cudaEvent_t pin_ev[kPinSlots] = {};
+  bool pin_busy[kPinSlots] = {};
+  int pin_next = 0;
   Prof prof;
   // one captured RK443 step (4 stages + step counter), replayed per step
   cudaStream_t cap_stream = nullptr;
@@ -583,6 +592,11 @@ extern "C" void rbc_destroy(rbc_t h) {
   for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
   if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int i = 0; i < rbc_s::kPinSlots; ++i) {
+    if (h->pin_busy[i]) cudaEventSynchronize(h->pin_ev[i]);
+    if (h->pin_ev[i]) cudaEventDestroy(h->pin_ev[i]);
+  }
+  cudaFreeHost(h->pin);
   cudaFree(h->d_tables);
   cudaFree(h->d_work);
   cudaFree(h->d_scratch);
@@ -593,7 +607,7 @@ extern "C" size_t rbc_state_bytes(rbc_t h) { return h ? state_doubles(h->g) * si
 
 static size_t work_doubles_per_state(const Grid& g) {
   const size_t S = state_doubles(g);
-  return 6 * S + z_doubles(g) + q_doubles(g) + g.Mz + 4;   // Xs, F, R[4], Z, Q, wT, ints + nu
+  return 6 * S + z_doubles(g) + q_doubles(g) + g.Mz + 5;   // Xs, F, R[4], Z, Q, wT, ints + nu + Ra
 }
 
 extern "C" size_t rbc_workspace_bytes_per_state(rbc_t h) {
@@ -623,6 +637,7 @@ extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
   w.Q = d; d += (size_t)B * q_doubles(g);
   w.wT = d; d += (size_t)B * g.Mz;
   w.nu = d; d += B;
+  w.ra = d; d += B;
   w.small = d; d += 16;
   int* ip = reinterpret_cast<int*>(d);
   w.nsteps = ip; ip += B;
@@ -729,21 +744,51 @@ static rbc_status ensure_step_graph(rbc_t h, double* X, int B, double* nu) {
   return RBC_OK;
 }
 
-extern "C" rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps, double* d_nu_integral,
-                                     cudaStream_t stream) {
+static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps, const double* h_ra,
+                             double* d_nu_integral, cudaStream_t stream) {
   if (!h || B < 0 || (B > 0 && (!d_states || !h_nsteps))) return fail(RBC_EINVAL, "null argument or B < 0");
   if (B == 0) return RBC_OK;
   int maxs = 0;
   for (int b = 0; b < B; ++b) {
     if (h_nsteps[b] < 0) return fail(RBC_EINVAL, "negative step count");
     maxs = std::max(maxs, h_nsteps[b]);
+    if (h_ra && !(h_ra[b] >= 0 && std::isfinite(h_ra[b]))) return fail(RBC_EINVAL, "Rayleigh number must be >= 0");
   }
   rbc_status s = rbc_reserve(h, B);
   if (s != RBC_OK) return s;
   const Work& w = h->w;
   double* X = static_cast<double*>(d_states);
   double* nu = d_nu_integral ? d_nu_integral : w.nu;
-  CK(cudaMemcpyAsync(w.nsteps, h_nsteps, (size_t)B * sizeof(int), cudaMemcpyHostToDevice, stream));
+  const size_t need = ((size_t)B * (sizeof(double) + sizeof(int)) + 255) & ~(size_t)255;
+  if (need > h->pin_slot) {
+    for (int i = 0; i < rbc_s::kPinSlots; ++i) {
+      if (h->pin_busy[i]) CK(cudaEventSynchronize(h->pin_ev[i]));
+      h->pin_busy[i] = false;
+    }
+    cudaFreeHost(h->pin);
+    h->pin = nullptr;
+    h->pin_slot = 0;
+    if (cudaMallocHost(&h->pin, need * rbc_s::kPinSlots) != cudaSuccess) {
+      cudaGetLastError();
+      h->pin = nullptr;
+      return fail(RBC_ENOMEM, "pinned staging for %d states", B);
+    }
+    h->pin_slot = need;
+  }
+  const int slot = h->pin_next;
+  h->pin_next = (slot + 1) % rbc_s::kPinSlots;
+  if (!h->pin_ev[slot]) CK(cudaEventCreateWithFlags(&h->pin_ev[slot], cudaEventDisableTiming));
+  if (h->pin_busy[slot]) CK(cudaEventSynchronize(h->pin_ev[slot]));
+  double* pin_ra = reinterpret_cast<double*>(h->pin + slot * h->pin_slot);
+  int* pin_ns = reinterpret_cast<int*>(pin_ra + B);
+  for (int b = 0; b < B; ++b) {
+    pin_ra[b] = h_ra ? h_ra[b] : h->g.Ra;
+    pin_ns[b] = h_nsteps[b];
+  }
+  CK(cudaMemcpyAsync(w.ra, pin_ra, (size_t)B * sizeof(double), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(w.nsteps, pin_ns, (size_t)B * sizeof(int), cudaMemcpyHostToDevice, stream));
+  CK(cudaEventRecord(h->pin_ev[slot], stream));
+  h->pin_busy[slot] = true;
   CK(cudaMemsetAsync(w.step, 0, sizeof(int), stream));
   CK(cudaMemsetAsync(w.flags, 0, (size_t)B * sizeof(int), stream));
   CK(cudaMemsetAsync(nu, 0, (size_t)B * sizeof(double), stream));
@@ -762,6 +807,55 @@ extern "C" rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* 
   }
   if (maxs > 0) CK(launch_nu_final(h->g, h->t, w, X, B, nu, stream));
   if (h->prof.once) h->prof.on = h->prof.once = false;   // sampled profiling: this call only
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps, double* d_nu_integral,
+                                     cudaStream_t stream) {
+  return step_batch(h, d_states, B, h_nsteps, nullptr, d_nu_integral, stream);
+}
+
+extern "C" rbc_status rbc_step_batch_ra(rbc_t h, void* d_states, int B, const int* h_nsteps, const double* h_ra,
+                                        double* d_nu_integral, cudaStream_t stream) {
+  if (!h_ra) return fail(RBC_EINVAL, "h_ra is NULL");
+  return step_batch(h, d_states, B, h_nsteps, h_ra, d_nu_integral, stream);
+}
+
+static bool compatible(rbc_t fine, rbc_t coarse) {
+  return fine && coarse && coarse->g.Nx <= fine->g.Nx && coarse->g.Nz <= fine->g.Nz;
+}
+
+extern "C" rbc_status rbc_restrict(rbc_t fine, rbc_t coarse, const void* d_fine, void* d_coarse, int B,
+                                   cudaStream_t stream) {
+  if (!compatible(fine, coarse) || B < 0 || (B > 0 && (!d_fine || !d_coarse)))
+    return fail(RBC_EINVAL, "bad handles, buffers or B");
+  CK(launch_restrict(fine->g, coarse->g, static_cast<const double*>(d_fine), static_cast<double*>(d_coarse), B,
+                     stream));
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_prolong(rbc_t fine, rbc_t coarse, const void* d_coarse, void* d_fine, int B,
+                                  cudaStream_t stream) {
+  if (!compatible(fine, coarse) || B < 0 || (B > 0 && (!d_fine || !d_coarse)))
+    return fail(RBC_EINVAL, "bad handles, buffers or B");
+  CK(launch_prolong(fine->g, coarse->g, static_cast<const double*>(d_coarse), static_cast<double*>(d_fine), B,
+                    stream));
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_parareal_correct(rbc_t fine, rbc_t coarse, const void* d_F, const void* d_Gnew,
+                                           const void* d_Gold, void* d_U, int B, cudaStream_t stream) {
+  if (!compatible(fine, coarse) || B < 0 || (B > 0 && (!d_F || !d_Gnew || !d_Gold || !d_U)))
+    return fail(RBC_EINVAL, "bad handles, buffers or B");
+  CK(launch_correct(fine->g, coarse->g, static_cast<const double*>(d_F), static_cast<const double*>(d_Gnew),
+                    static_cast<const double*>(d_Gold), static_cast<double*>(d_U), B, stream));
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_l2_diff(rbc_t h, const void* d_A, const void* d_B, int B, double* d_out,
+                                  cudaStream_t stream) {
+  if (!h || B < 0 || (B > 0 && (!d_A || !d_out))) return fail(RBC_EINVAL, "null argument or B < 0");
+  CK(launch_l2_diff(h->g, h->t, static_cast<const double*>(d_A), static_cast<const double*>(d_B), B, d_out, stream));
   return RBC_OK;
 }
 
@@ -888,11 +982,11 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
   CK(cudaMemcpyAsync(U, d_U0, Sf * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   // k = 0: serial coarse sweep U_{n+1}^0 = G(U_n^0)
   for (int n = 0; n < N; ++n) {
-    CK(launch_restrict(gf, gc, U + n * Sf, p->d_C, stream));
+    CK(launch_restrict(gf, gc, U + n * Sf, p->d_C, 1, stream));
     rbc_status s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, stream);
     if (s != RBC_OK) return s;
     CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Sc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-    CK(launch_prolong(gf, gc, p->d_C, U + (n + 1) * Sf, stream));
+    CK(launch_prolong(gf, gc, p->d_C, U + (n + 1) * Sf, 1, stream));
   }
   std::vector<int> nfv(N, p->nf);
   std::vector<double> I(N), nrm(2 * (N + 1));
@@ -914,14 +1008,14 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
     for (int n = 0; n < N; ++n) {
       if (n <= k - 1) {
         // U_n unchanged since the last iteration: G(U_n) = Gold_n exactly
-        CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_Gold + n * Sc, p->d_Gold + n * Sc, U + (n + 1) * Sf,
+        CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_Gold + n * Sc, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1,
                           stream));
         continue;
       }
-      CK(launch_restrict(gf, gc, U + n * Sf, p->d_C, stream));
+      CK(launch_restrict(gf, gc, U + n * Sf, p->d_C, 1, stream));
       s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, stream);
       if (s != RBC_OK) return s;
-      CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_C, p->d_Gold + n * Sc, U + (n + 1) * Sf, stream));
+      CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_C, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1, stream));
       CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Sc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     }
     s = rbc_check_diverged(G, stream);

@@ -92,6 +92,7 @@ struct Work {
   int* flags;      // [B] non-finite flags
   double* nu;      // [B] internal Nu integral when the caller passes none
   double* small;   // [16] scalars
+  double* ra;      // [B] Rayleigh number of each state
   Prof* prof;      // timing, or nullptr
 };
 
@@ -121,10 +122,10 @@ cudaError_t launch_set_state(const Grid& g, const Tables& t, const double* gT, c
                              const double* gw, double* scratch, double* X, cudaStream_t s);
 cudaError_t launch_get_state(const Grid& g, const Tables& t, const double* X, double* scratch, double* gT,
                              double* gu, double* gw, cudaStream_t s);
-cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const double* Xf, double* Xc, cudaStream_t s);
+cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const double* Xf, double* Xc, int B, cudaStream_t s);
 cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, const double* Gnew,
-                           const double* Gold, double* Uout, cudaStream_t s);
-cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, cudaStream_t s);
+                           const double* Gold, double* Uout, int B, cudaStream_t s);
+cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, int B, cudaStream_t s);
 size_t rows_smem_bytes(const Grid& g);
 size_t static_scratch_doubles_needed(const Grid& g);
 constexpr size_t kStaticScratchCapacity = (size_t)3 << 17;   // doubles in the static scratch array

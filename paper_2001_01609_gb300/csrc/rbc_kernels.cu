@@ -571,6 +571,7 @@ struct SolveSmem {
   double* r;    // [nq][W] r_i of the tau rows
   double* T;    // [nq][W] T_i, kept for the psi coupling
   int W;        // columns = 2 * tms
+  double Ra;    // Rayleigh number of this slice
 };
 
 template <int KIND>
@@ -642,7 +643,7 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
 #pragma unroll
     for (int j = 0; j <= 4; ++j)
       if (t + j < nq) st = fma(__ldg(tb.s4 + (p * nq + t) * 5 + j), sm.T[(t + j) * W + (col ^ 1)], st);
-    const double cpl = (c == 0 ? 1.0 : -1.0) * 0.5 * dt * g.Pr * g.Ra * (g.kfac * m);
+    const double cpl = (c == 0 ? 1.0 : -1.0) * 0.5 * dt * g.Pr * sm.Ra * (g.kfac * m);
     bv = fma(cpl, st, bv);
   }
   sm.y[(t + SY::D) * W + col] = bv;
@@ -787,7 +788,7 @@ __device__ __forceinline__ void solve_lx(const Grid& g, const Tables& tb, int st
 
 __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* Xs, const double* F, double* R,
                            size_t S, const double* wT, double* nu, int* flags, int B, int stage, int tms,
-                           const int* nsteps, int stepidx, int blk) {
+                           const double* ra, const int* nsteps, int stepidx, int blk) {
   extern __shared__ double sbuf[];
   const int mt = (g.nm + tms - 1) / tms;
   const int b = blk / (2 * mt);
@@ -800,6 +801,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
   const int ncol = 2 * min(tms, g.nm - m0);
   SolveSmem sm;
   sm.W = W;
+  sm.Ra = ra ? ra[b] : g.Ra;
   sm.F = sbuf;
   sm.X = sm.F + (size_t)nq * W;
   sm.y = sm.X + (size_t)nq * W;
@@ -911,8 +913,8 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
 
 __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, double* Xs, const double* F, double* R,
                                                size_t S, const double* wT, double* nu, int* flags, int B, int stage,
-                                               int tms, const int* nsteps, const int* step) {
-  solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, B, stage, tms, nsteps, nsteps ? *step : 0, blockIdx.x);
+                                               int tms, const double* ra, const int* nsteps, const int* step) {
+  solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, B, stage, tms, ra, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
 static int solve_tile(const Grid& g, int B) {
@@ -1076,7 +1078,7 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
   k_solve<<<(unsigned)(B * 2 * mtiles), 256, solve_smem(g, B), s>>>(g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags,
-                                                                    B, stage, tms, w.nsteps, w.step);
+                                                                    B, stage, tms, w.ra, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);
   return cudaGetLastError();
@@ -1295,53 +1297,68 @@ cudaError_t launch_get_state(const Grid& g, const Tables& t, const double* X, do
 // ---------------------------------------------------------------------------
 // Parareal transfer and correction (Eq. 20).
 // ---------------------------------------------------------------------------
-__global__ void k_restrict(Grid gf, Grid gc, const double* Xf, double* Xc) {
+__global__ void k_restrict(Grid gf, Grid gc, const double* Xf, double* Xc, int B) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2L * gc.Nz * gc.nm) return;
-  const int m = idx % gc.nm;
-  const int n = (idx / gc.nm) % gc.Nz;
-  const int f = idx / ((long)gc.nm * gc.Nz);
-  st2(Xc + soff(gc, f, n, m), ld2(Xf + soff(gf, f, n, m)));
+  const long per = 2L * gc.Nz * gc.nm;
+  if (idx >= per * B) return;
+  const int b = (int)(idx / per);
+  const long r = idx - (long)b * per;
+  const int m = r % gc.nm;
+  const int n = (r / gc.nm) % gc.Nz;
+  const int f = r / ((long)gc.nm * gc.Nz);
+  st2(Xc + (size_t)b * state_doubles(gc) + soff(gc, f, n, m), ld2(Xf + (size_t)b * state_doubles(gf) + soff(gf, f, n, m)));
 }
 
-cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const double* Xf, double* Xc, cudaStream_t s) {
-  k_restrict<<<nblk(2L * gc.Nz * gc.nm, 128), 128, 0, s>>>(gf, gc, Xf, Xc);
+cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const double* Xf, double* Xc, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_restrict<<<nblk(2L * gc.Nz * gc.nm * B, 128), 128, 0, s>>>(gf, gc, Xf, Xc, B);
   count();
   return cudaGetLastError();
 }
 
-__global__ void k_prolong(Grid gf, Grid gc, const double* Xc, double* Xf) {
+__global__ void k_prolong(Grid gf, Grid gc, const double* Xc, double* Xf, int B) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2L * gf.Nz * gf.nm) return;
-  const int m = idx % gf.nm;
-  const int n = (idx / gf.nm) % gf.Nz;
-  const int f = idx / ((long)gf.nm * gf.Nz);
+  const long per = 2L * gf.Nz * gf.nm;
+  if (idx >= per * B) return;
+  const int b = (int)(idx / per);
+  const long r = idx - (long)b * per;
+  const int m = r % gf.nm;
+  const int n = (r / gf.nm) % gf.Nz;
+  const int f = r / ((long)gf.nm * gf.Nz);
   double2 v = {0.0, 0.0};
-  if (m < gc.nm && n < gc.Nz) v = ld2(Xc + soff(gc, f, n, m));
-  st2(Xf + soff(gf, f, n, m), v);
+  if (m < gc.nm && n < gc.Nz) v = ld2(Xc + (size_t)b * state_doubles(gc) + soff(gc, f, n, m));
+  st2(Xf + (size_t)b * state_doubles(gf) + soff(gf, f, n, m), v);
 }
 
-cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, cudaStream_t s) {
-  k_prolong<<<nblk(2L * gf.Nz * gf.nm, 128), 128, 0, s>>>(gf, gc, Xc, Xf);
+cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_prolong<<<nblk(2L * gf.Nz * gf.nm * B, 128), 128, 0, s>>>(gf, gc, Xc, Xf, B);
   count();
   return cudaGetLastError();
 }
 
-// U = F + (prolong(Gnew) - prolong(Gold)), elementwise in that order.
-__global__ void k_correct(Grid gf, Grid gc, const double* Ff, const double* Gnew, const double* Gold, double* U) {
+// U = F + (prolong(Gnew) - prolong(Gold)), elementwise in that order (Eq. 20).
+__global__ void k_correct(Grid gf, Grid gc, const double* Ff, const double* Gnew, const double* Gold, double* U,
+                          int B) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2L * gf.Nz * gf.nm) return;
-  const int m = idx % gf.nm;
-  const int n = (idx / gf.nm) % gf.Nz;
-  const int f = idx / ((long)gf.nm * gf.Nz);
+  const long per = 2L * gf.Nz * gf.nm;
+  if (idx >= per * B) return;
+  const int b = (int)(idx / per);
+  const long r = idx - (long)b * per;
+  const int m = r % gf.nm;
+  const int n = (r / gf.nm) % gf.Nz;
+  const int f = r / ((long)gf.nm * gf.Nz);
+  const size_t Sf = state_doubles(gf), Sc = state_doubles(gc);
   double2 d = {0.0, 0.0};
-  if (m < gc.nm && n < gc.Nz) d = ld2(Gnew + soff(gc, f, n, m)) - ld2(Gold + soff(gc, f, n, m));
-  st2(U + soff(gf, f, n, m), ld2(Ff + soff(gf, f, n, m)) + d);
+  if (m < gc.nm && n < gc.Nz)
+    d = ld2(Gnew + (size_t)b * Sc + soff(gc, f, n, m)) - ld2(Gold + (size_t)b * Sc + soff(gc, f, n, m));
+  st2(U + (size_t)b * Sf + soff(gf, f, n, m), ld2(Ff + (size_t)b * Sf + soff(gf, f, n, m)) + d);
 }
 
 cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, const double* Gnew, const double* Gold,
-                           double* Uout, cudaStream_t s) {
-  k_correct<<<nblk(2L * gf.Nz * gf.nm, 128), 128, 0, s>>>(gf, gc, Ff, Gnew, Gold, Uout);
+                           double* Uout, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_correct<<<nblk(2L * gf.Nz * gf.nm * B, 128), 128, 0, s>>>(gf, gc, Ff, Gnew, Gold, Uout, B);
   count();
   return cudaGetLastError();
 }

@@ -20,7 +20,8 @@ EXPORTS = [
     "rbc_last_error", "rbc_create", "rbc_destroy", "rbc_state_bytes", "rbc_workspace_bytes_per_state",
     "rbc_reserve", "rbc_set_state", "rbc_get_state", "rbc_step_batch", "rbc_check_diverged", "rbc_nusselt",
     "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate", "rbc_profile",
-    "rbc_profile_read", "rbc_launch_count", "rbc_nusselt_static",
+    "rbc_profile_read", "rbc_launch_count", "rbc_nusselt_static", "rbc_step_batch_ra", "rbc_restrict",
+    "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -68,6 +69,11 @@ def load():
         "rbc_profile_read": (I, [P, PD, ctypes.POINTER(ctypes.c_longlong), PD, PD]),
         "rbc_launch_count": (ctypes.c_ulonglong, []),
         "rbc_nusselt_static": (I, [P, P, PD, P]),
+        "rbc_step_batch_ra": (I, [P, P, I, PI, PD, P, P]),
+        "rbc_restrict": (I, [P, P, P, P, I, P]),
+        "rbc_prolong": (I, [P, P, P, P, I, P]),
+        "rbc_parareal_correct": (I, [P, P, P, P, P, P, I, P]),
+        "rbc_l2_diff": (I, [P, P, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -151,14 +157,22 @@ class Propagator:
         _check(load().rbc_get_state(self.h, _ptr(state), _dptr(T), _dptr(u), _dptr(w)))
         return T, u, w
 
-    def step_batch(self, states, nsteps, nu=None, stream=None):
-        """Advance states (B, *state_shape) in place; nsteps int or sequence of B ints."""
+    def step_batch(self, states, nsteps, nu=None, stream=None, ra=None):
+        """Advance states (B, *state_shape) in place; nsteps int or sequence of B ints.
+
+        ra: optional Rayleigh number per state (sequence of B floats).
+        """
         B = states.shape[0]
         ns = np.full(B, nsteps, dtype=np.int32) if np.isscalar(nsteps) else np.ascontiguousarray(nsteps, np.int32)
         assert ns.shape == (B,)
         nup = _ptr(nu) if nu is not None else None
-        _check(load().rbc_step_batch(self.h, _ptr(states), B, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                                     nup, _stream(stream)))
+        nsp = ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        if ra is None:
+            _check(load().rbc_step_batch(self.h, _ptr(states), B, nsp, nup, _stream(stream)))
+        else:
+            rr = np.ascontiguousarray(ra, dtype=np.float64)
+            assert rr.shape == (B,)
+            _check(load().rbc_step_batch_ra(self.h, _ptr(states), B, nsp, _dptr(rr), nup, _stream(stream)))
 
     def check_diverged(self, stream=None):
         return _check(load().rbc_check_diverged(self.h, _stream(stream)), allow=(RBC_EDIVERGED,))
@@ -183,6 +197,28 @@ class Propagator:
         out = np.zeros(1)
         _check(load().rbc_l2_temperature(self.h, _ptr(state), _dptr(out), _stream(stream)))
         return float(out[0])
+
+
+def restrict(fine, coarse, fine_states, coarse_states, stream=None):
+    _check(load().rbc_restrict(fine.h, coarse.h, _ptr(fine_states), _ptr(coarse_states), fine_states.shape[0],
+                               _stream(stream)))
+
+
+def prolong(fine, coarse, coarse_states, fine_states, stream=None):
+    _check(load().rbc_prolong(fine.h, coarse.h, _ptr(coarse_states), _ptr(fine_states), coarse_states.shape[0],
+                              _stream(stream)))
+
+
+def parareal_correct(fine, coarse, F, Gnew, Gold, U, stream=None):
+    """U = F + (prolong(Gnew) - prolong(Gold)) for B states (Eq. 20)."""
+    _check(load().rbc_parareal_correct(fine.h, coarse.h, _ptr(F), _ptr(Gnew), _ptr(Gold), _ptr(U), F.shape[0],
+                                       _stream(stream)))
+
+
+def l2_diff(prop, A, Bm, out, stream=None):
+    """out[b] = ||A[b] - Bm[b]||^2 (temperature, L2 over the domain); Bm may be None."""
+    _check(load().rbc_l2_diff(prop.h, _ptr(A), _ptr(Bm) if Bm is not None else None, A.shape[0], _ptr(out),
+                              _stream(stream)))
 
 
 def launch_count():
