@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -158,6 +160,8 @@ def run_gb300(args, w):
     G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dv["dtc"])
     N = w["slices"]
     P = rbc.Parareal(F, G, 0.0, dv["t_end"], N)
+    group = args.group if args.group else -(-N // 4)
+    P.set_group(group)
     stream = torch.cuda.current_stream()
     U0 = F.new_states(1)
     Th = initial_temperature(w["Nx"], w["Nz"], seed=w["seed"] + rank, Lx=w["Lx"])
@@ -187,11 +191,13 @@ def run_gb300(args, w):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    F.profile(True)
-    for _ in range(args.steps):
+    for si in range(args.steps):
         flush.zero_()                                         # L2 flush between timed steps
         torch.cuda.synchronize()
-        G.profile(True, sample=True)                          # the step's first coarse call
+        # sampled kernel timing: the step's first coarse call and first fine group
+        # are recorded kernel by kernel (without their graphs), on their own streams
+        G.profile(True, sample=True)
+        F.profile(True, sample=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         U0.copy_(U0h, non_blocking=True)
@@ -219,15 +225,18 @@ def run_gb300(args, w):
     value = world * fine_dof_steps * args.steps / t_total
     e2e_value = world * fine_dof_steps * args.steps / e2e_total
 
-    # Per-kernel time over the timed steps.  Fine sweep: every launch recorded.
-    # Coarse sweeps: the first coarse call of each step is recorded (without
-    # its graph); its mean per launch times the known launch count, 4 launches
-    # per kind per coarse step, (2N - 1) nc coarse steps per iteration.
+    # Per-kernel time over the timed steps, from the samples: mean time per
+    # launch times the known launch count.  Fine: groups of `group` slices,
+    # nf steps each, 4 stages per step; coarse: (2N - 1) nc steps per iteration
+    # (the correction sweep reuses G(U_0)), 4 stages per step.
     kern = {}
+    f_launches = 4 * (-(-N // group)) * w["steps_per_slice"] * args.steps
     for k, v in prof_f.items():
         if v["launches"]:
-            kern["fine:" + k] = dict(ms=v["ms"], launches=v["launches"], per_ms=v["ms"] / v["launches"],
-                                     flops_per=v["flops"] / v["launches"], bytes_per=v["bytes"] / v["launches"])
+            per = v["ms"] / v["launches"]
+            kern["fine:" + k] = dict(ms=per * f_launches, launches=f_launches, per_ms=per,
+                                     flops_per=v["flops"] / v["launches"], bytes_per=v["bytes"] / v["launches"],
+                                     sampled_launches=v["launches"])
     g_launches = 4 * (2 * N - 1) * dv["nc"] * args.steps
     for k, v in prof_g.items():
         if v["launches"]:
@@ -256,6 +265,8 @@ def run_gb300(args, w):
                                 fine_steps_per_slice=w["steps_per_slice"], coarse_steps_per_slice=dv["nc"],
                                 dt=w["dt"], dt_coarse=dv["dtc"], t_end=dv["t_end"], dof_per_slice=dv["dof"],
                                 step="one Parareal iteration (coarse sweep, batched fine sweep, correction, norms)",
+                                fine_group=group,
+                                schedule="coarse sweep, fine groups and correction sweep overlapped on 3 streams",
                                 l2="flushed between timed steps (256 MB write)",
                                 parallelism=f"{world} independent problems" if world > 1 else "single GPU"),
                     e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(U0h.numel() * 8),
@@ -290,6 +301,130 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+# Serving: many Parareal requests on one GPU (continuous batching).
+SERVING = {
+    "rbc_serving_256req_poisson": dict(requests=256, seed=4, fine_steps=10, coarse_ratio=2, max_iters=2,
+                                       f_chunk=10, load=0.8),
+}
+
+
+def run_serving(args, name):
+    """256 requests, Poisson arrivals at `load` x the calibrated capacity; Ra
+    log-uniform in [1e4, 1e8], a grid drawn among those with >= 6 points in the
+    thermal boundary layer, 4-64 slices, FP64 or mixed precision with p = 1/2,
+    `fine_steps` fine steps per slice and 2 Parareal iterations per request."""
+    import torch
+    cfgw = SERVING[name]
+    cpu = None
+    if not args.no_cpu_baseline:
+        w0 = dict(Ra=1e4, Pr=1.0, Lx=2.0, Nx=64, Nz=32, dt=3.125e-5, seed=0)
+        rate, d = cpu_oracle_rate(w0)
+        cpu = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
+                   sample=f"oracle fine propagator on the smallest serving grid (64x32), {d['steps']} RK443 "
+                          f"steps in {d['seconds']:.1f} s on one host thread")
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc, serving
+    from paper_2001_01609_gb300.inputs import initial_temperature
+
+    def class_config(Nx, Nz, precision):
+        return serving.default_class_config(Nx, Nz, precision, fine_steps=cfgw["fine_steps"],
+                                            coarse_ratio=cfgw["coarse_ratio"])
+
+    eng = serving.Engine(max_iters=cfgw["max_iters"], f_chunk=cfgw["f_chunk"], class_config=class_config)
+    reqs = serving.make_requests(cfgw["requests"], cfgw["seed"], rate=1.0)
+    # initial states on the host, pinned: each request's H2D copy is inside the timed run
+    for r in reqs:
+        cls = eng._class(r.key)
+        u = cls.fine.new_states(1)
+        cls.fine.set_state(u[0], initial_temperature(r.Nx, r.Nz, r.seed))
+        r.U0 = u[0].cpu().pin_memory()
+    # capacity: per-class fine cost per slice-step (batch of 32) and coarse cost per step (batch of 1)
+    cost = {}
+    for key, cls in eng.classes.items():
+        B = 32
+        st = cls.fine.new_states(B)
+        st.copy_(reqs[[r.key for r in reqs].index(key)].U0.cuda().expand_as(st))
+        cls.fine.step_batch(st, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cls.fine.step_batch(st, 4)
+        torch.cuda.synchronize()
+        tf = (time.perf_counter() - t0) / 4 / B
+        c = cls.coarse.new_states(1)
+        rbc.restrict(cls.fine, cls.coarse, st[:1], c)
+        cls.coarse.step_batch(c, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cls.coarse.step_batch(c, 4)
+        torch.cuda.synchronize()
+        cost[key] = (tf, (time.perf_counter() - t0) / 4)
+    work = []
+    for r in reqs:
+        cf = eng.config_for(r.key)
+        tf, tc = cost[r.key]
+        sweeps = cfgw["max_iters"] + 1
+        work.append(sum(r.nslices - (k - 1) for k in range(1, cfgw["max_iters"] + 1)) * cf.nf * tf
+                    + sweeps * r.nslices * cf.nc * tc)
+    capacity = len(reqs) / sum(work)
+    rate = cfgw["load"] * capacity
+    g = np.random.Generator(np.random.PCG64(cfgw["seed"] + 1000))
+    t = 0.0
+    for r in reqs:
+        t += g.exponential(1.0 / rate)
+        r.arrival = t
+    # warm-up: one request per class, arriving at once (graph captures, lazy setup)
+    for _ in range(max(1, args.warmup)):
+        seen, warm = set(), []
+        for r in reqs:
+            if r.key not in seen:
+                seen.add(r.key)
+                warm.append(serving.Request(rid=-1 - len(warm), Ra=r.Ra, Nx=r.Nx, Nz=r.Nz, nslices=4,
+                                            precision=r.precision, U0=r.U0))
+        eng.run(warm, deadline=600)
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    launches0 = rbc.launch_count()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    eng.run(reqs, deadline=3600)
+    torch.cuda.synchronize()
+    e1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    makespan = e0.elapsed_time(e1) / 1e3
+    launches = rbc.launch_count() - launches0
+    dof = serving.dof_steps(reqs, eng)
+    lat = serving.latency_stats(reqs)
+    bad = [r.rid for r in reqs if r.status != rbc.RBC_OK]
+    value = dof / makespan
+    h2d = sum(r.U0.numel() * 8 for r in reqs)
+    d2h = sum((2 * (r.nslices + 1) + r.nslices * -(-eng.config_for(r.key).nf // cfgw["f_chunk"])) * 8 * r.k_done
+              for r in reqs)
+    classes = {f"{k[0]}x{k[1]}/{'mixed' if k[2] else 'fp64'}": dict(
+        requests=sum(1 for r in reqs if r.key == k), dt=eng.config_for(k).dt_fine,
+        dt_coarse=eng.config_for(k).dt_coarse, fine_ms_per_slice_step=1e3 * cost[k][0],
+        coarse_ms_per_step=1e3 * cost[k][1]) for k in eng.classes}
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=1, steps=1, warmup=max(1, args.warmup),
+                ms_per_step=1e3 * makespan, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64+mixed", data="synthetic",
+                config=dict(workload=name, requests=len(reqs), seed=cfgw["seed"], arrivals="Poisson",
+                            rate_per_s=rate, offered_load=cfgw["load"], capacity_per_s=capacity,
+                            fine_steps_per_slice=cfgw["fine_steps"], coarse_ratio=cfgw["coarse_ratio"],
+                            parareal_iterations=cfgw["max_iters"], fine_chunk=cfgw["f_chunk"],
+                            mem_limit_bytes=eng.mem_limit, peak_committed_bytes=eng.peak_committed,
+                            peak_active_requests=eng.peak_active, classes=classes,
+                            step="the whole request stream, arrival of the first to completion of the last",
+                            l2="working set of each class batch exceeds L2 for the large grids"),
+                latency=lat, requests_per_s=len(reqs) / makespan, failed=bad,
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h)),
+                gpu_launches=int(launches), roofline=None, cpu_baseline=cpu, clocks=ck)
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 NCU_CASES = {
     # name: (Ra, Nx, Nz, dt, B) -- one RK443 step without graphs, for ncu captures
     "fine_b32": (1e6, 256, 64, 1.25e-5, 32),
@@ -321,12 +456,20 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(SERVING))
+    ap.add_argument("--group", type=int, default=0, help="slices per fine group (default: a quarter of the slices)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
+        return
+    if args.workload in SERVING:
+        if args.impl == "reference":
+            print(json.dumps(dict(impl="reference", unavailable="the serving workload has no CPU reference run: "
+                                  "the oracle would take hours for 256 requests")), flush=True)
+        else:
+            run_serving(args, args.workload)
         return
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

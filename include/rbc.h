@@ -184,9 +184,22 @@ void parareal_destroy(parareal_t p);
  * defects[k-1] = Defect_k, nus[k-1] = Nu_{k-1} (arrays of max_iters doubles,
  * either may be NULL).  Returns RBC_OK when the criterion was met (always for
  * RBC_CRIT_FIXED), RBC_ENOTCONVERGED when max_iters ran out, RBC_EDIVERGED on
- * a non-finite state.  Synchronous on `stream` (one small D2H per iteration). */
+ * a non-finite state.  Iterations stop after k = nslices, where U^k is the
+ * serial fine solution.  Synchronous on `stream` (one small D2H per iteration).
+ *
+ * Schedule (the results do not depend on it, bit for bit): the coarse sweep
+ * U^0 runs on `stream`; the fine sweep runs in groups of slices on an internal
+ * stream, each group starting as soon as the coarse sweep has produced its
+ * inputs; the correction sweep runs on a second internal stream with a second
+ * coarse handle, each slice starting when its fine group and its coarse U^0
+ * step are done.  So within an iteration the three sweeps overlap.           */
 rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_iters,
                             int* k_done, double* defects, double* nus, cudaStream_t stream);
+
+/* Slices per fine group of the schedule above (default ceil(nslices / 4));
+ * group >= nslices runs each fine sweep as one batch after the coarse sweep
+ * U^0 has finished.  RBC_EINVAL if group < 1.  Changes timing only.         */
+rbc_status parareal_set_group(parareal_t p, int group);
 
 /* ---- Instrumentation (outside the paper's method) ----
  * Kernel kinds of one RK443 stage: z-inverse transform, row kernel (x-FFTs and

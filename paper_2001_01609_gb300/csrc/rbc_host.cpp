@@ -249,14 +249,25 @@ struct rbc_s {
   cudaEvent_t pin_ev[kPinSlots] = {};
   bool pin_busy[kPinSlots] = {};
   int pin_next = 0;
+  // what the workspace holds from the last upload: a call with the same
+  // arrays (a serial sweep repeats them) queues no copy at all
+  std::vector<int> up_ns;
+  std::vector<double> up_ra;
   Prof prof;
-  // one captured RK443 step (4 stages + step counter), replayed per step
+  // Step loops: a graph whose one node is a device-side while loop over the
+  // captured RK443 step (4 stages + counter), so a call of any length is one
+  // launch.  A few bindings (states, B, nu) are kept, least recently used out.
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void* X = nullptr;
+    const void* nu = nullptr;
+    int B = -1;
+    unsigned long long used = 0;
+  };
+  static constexpr int kGraphCache = 8;
+  StepGraph graphs[kGraphCache];
+  unsigned long long graph_clock = 0;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t step_graph = nullptr;
-  const void* graph_X = nullptr;
-  const void* graph_nu = nullptr;
-  int graph_B = -1;
-  void* graph_work = nullptr;
   bool use_graphs = true;
 };
 
@@ -271,6 +282,17 @@ struct pr_s {
   double* d_C = nullptr;      // 1 coarse state
   double* d_I = nullptr;      // N doubles: Nu_V integrals of the F sweep
   double* d_norm = nullptr;   // 2N doubles
+  // Pipelined schedule: the coarse sweep U^0 (caller's stream, `coarse`), the
+  // fine sweep in groups of `group` slices (sF, `fine`) and the correction
+  // sweep (sG, `coarse2`, a second handle on the coarse grid) overlap; events
+  // carry the per-slice dependencies.
+  rbc_t coarse2 = nullptr;
+  double* d_C2 = nullptr;     // 1 coarse state of the correction sweep
+  int group = 0;
+  cudaStream_t sF = nullptr, sG = nullptr;
+  std::vector<cudaEvent_t> ev_g0;   // [N] U^0 sweep done with slice n
+  std::vector<cudaEvent_t> ev_f;    // [N] fine group j done
+  cudaEvent_t ev_begin = nullptr, ev_copy = nullptr, ev_fdone = nullptr, ev_gdone = nullptr;
 };
 
 extern "C" const char* rbc_last_error(void) { return g_err; }
@@ -590,7 +612,8 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
 extern "C" void rbc_destroy(rbc_t h) {
   if (!h) return;
   for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
-  if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
+  for (auto& sg : h->graphs)
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int i = 0; i < rbc_s::kPinSlots; ++i) {
     if (h->pin_busy[i]) cudaEventSynchronize(h->pin_ev[i]);
@@ -628,6 +651,12 @@ extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
   cudaFree(h->d_work);
   h->d_work = p;
   h->cap = B;
+  for (auto& sg : h->graphs) {   // bound to the old workspace
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    sg = rbc_s::StepGraph{};
+  }
+  h->up_ns.clear();
+  h->up_ra.clear();
   double* d = static_cast<double*>(p);
   Work& w = h->w;
   w.Xs = d; d += (size_t)B * S;
@@ -640,9 +669,15 @@ extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
   w.ra = d; d += B;
   w.small = d; d += 16;
   int* ip = reinterpret_cast<int*>(d);
+  w.maxs = ip; ip += 1;
   w.nsteps = ip; ip += B;
   w.flags = ip; ip += B;
-  w.step = ip;
+  w.step = ip; ip += 1;
+  // the counters start defined: an unset loop bound reads 0 (one step), never garbage
+  if (cudaMemset(w.maxs, 0, (size_t)(ip - w.maxs) * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RBC_ECUDA, "workspace counters");
+  }
   w.prof = &h->prof;
   return RBC_OK;
 }
@@ -709,57 +744,78 @@ extern "C" rbc_status rbc_get_state(rbc_t h, const void* d_state, double* h_T, d
   return RBC_OK;
 }
 
-// Capture one RK443 step of this (states, B, nu) binding on the handle's own
-// stream; the kernels read the step counter from device memory, so the same
-// graph serves every step of the batch.
-static rbc_status ensure_step_graph(rbc_t h, double* X, int B, double* nu) {
-  if (h->step_graph && h->graph_X == X && h->graph_B == B && h->graph_nu == nu && h->graph_work == h->d_work)
-    return RBC_OK;
-  if (h->step_graph) {
-    cudaGraphExecDestroy(h->step_graph);
-    h->step_graph = nullptr;
+// The step loop of this (states, B, nu) binding: a while node whose body is
+// one RK443 step captured on the handle's own stream, ended by the counter
+// kernel once step == maxs.  Cached per binding.
+static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExec_t* out) {
+  ++h->graph_clock;
+  rbc_s::StepGraph* victim = &h->graphs[0];
+  for (auto& sg : h->graphs) {
+    if (sg.exec && sg.X == X && sg.B == B && sg.nu == nu) {
+      sg.used = h->graph_clock;
+      *out = sg.exec;
+      return RBC_OK;
+    }
+    if (!sg.exec || sg.used < victim->used) victim = &sg;
   }
+  if (victim->exec) cudaGraphExecDestroy(victim->exec);
+  *victim = rbc_s::StepGraph{};
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t gr = nullptr;
-  const unsigned long long before = launches_so_far();
-  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaSuccess;
-  for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage) e = launch_stage(h->g, h->t, h->w, X, B, stage, nu, h->cap_stream);
-  if (e == cudaSuccess) e = launch_advance(h->w, h->cap_stream);
-  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &gr);
-  if (e != cudaSuccess || e2 != cudaSuccess) {
-    if (gr) cudaGraphDestroy(gr);
-    return fail(RBC_ECUDA, "step graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  CK(cudaGraphCreate(&gr, 0));
+  cudaGraphConditionalHandle loop;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&loop, gr, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &cp);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(gr);
+    return fail(RBC_ECUDA, "step loop node: %s", cudaGetErrorString(e));
   }
-  if (launches_so_far() - before != (unsigned long long)kStepKernels)
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const unsigned long long before = launches_so_far();
+  e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage)
+      e = launch_stage(h->g, h->t, h->w, X, B, stage, nu, h->cap_stream);
+    if (e == cudaSuccess) e = launch_advance_loop(h->w, loop, h->cap_stream);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(gr);
+    return fail(RBC_ECUDA, "step loop capture: %s", cudaGetErrorString(e));
+  }
+  if (launches_so_far() - before != (unsigned long long)kStepKernels) {
+    cudaGraphDestroy(gr);
     return fail(RBC_ECUDA, "step graph: unexpected kernel count");
+  }
   add_launches(~0ull - (unsigned long long)kStepKernels + 1ull);   // captured, not executed
-  e = cudaGraphInstantiate(&h->step_graph, gr, 0);
+  e = cudaGraphInstantiate(&victim->exec, gr, 0);
   cudaGraphDestroy(gr);
-  if (e != cudaSuccess) return fail(RBC_ECUDA, "step graph instantiate: %s", cudaGetErrorString(e));
-  h->graph_X = X;
-  h->graph_B = B;
-  h->graph_nu = nu;
-  h->graph_work = h->d_work;
+  if (e != cudaSuccess) {
+    victim->exec = nullptr;
+    return fail(RBC_ECUDA, "step graph instantiate: %s", cudaGetErrorString(e));
+  }
+  victim->X = X;
+  victim->B = B;
+  victim->nu = nu;
+  victim->used = h->graph_clock;
+  *out = victim->exec;
   return RBC_OK;
 }
 
-static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps, const double* h_ra,
-                             double* d_nu_integral, cudaStream_t stream) {
-  if (!h || B < 0 || (B > 0 && (!d_states || !h_nsteps))) return fail(RBC_EINVAL, "null argument or B < 0");
-  if (B == 0) return RBC_OK;
-  int maxs = 0;
-  for (int b = 0; b < B; ++b) {
-    if (h_nsteps[b] < 0) return fail(RBC_EINVAL, "negative step count");
-    maxs = std::max(maxs, h_nsteps[b]);
-    if (h_ra && !(h_ra[b] >= 0 && std::isfinite(h_ra[b]))) return fail(RBC_EINVAL, "Rayleigh number must be >= 0");
-  }
-  rbc_status s = rbc_reserve(h, B);
-  if (s != RBC_OK) return s;
+// Copy the per-state step counts (and their maximum) and Rayleigh numbers
+// into the workspace, through a pinned slot of the handle's ring.
+static rbc_status upload_steps(rbc_t h, int B, const int* h_nsteps, const double* h_ra, int maxs,
+                               cudaStream_t stream) {
   const Work& w = h->w;
-  double* X = static_cast<double*>(d_states);
-  double* nu = d_nu_integral ? d_nu_integral : w.nu;
-  const size_t need = ((size_t)B * (sizeof(double) + sizeof(int)) + 255) & ~(size_t)255;
+  const size_t need = ((size_t)B * (sizeof(double) + sizeof(int)) + sizeof(int) + 255) & ~(size_t)255;
   if (need > h->pin_slot) {
     for (int i = 0; i < rbc_s::kPinSlots; ++i) {
       if (h->pin_busy[i]) CK(cudaEventSynchronize(h->pin_ev[i]));
@@ -780,24 +836,55 @@ static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps
   if (!h->pin_ev[slot]) CK(cudaEventCreateWithFlags(&h->pin_ev[slot], cudaEventDisableTiming));
   if (h->pin_busy[slot]) CK(cudaEventSynchronize(h->pin_ev[slot]));
   double* pin_ra = reinterpret_cast<double*>(h->pin + slot * h->pin_slot);
-  int* pin_ns = reinterpret_cast<int*>(pin_ra + B);
+  int* pin_ns = reinterpret_cast<int*>(pin_ra + B);   // [maxs][nsteps B], as w.maxs, w.nsteps
+  pin_ns[0] = maxs;
   for (int b = 0; b < B; ++b) {
     pin_ra[b] = h_ra ? h_ra[b] : h->g.Ra;
-    pin_ns[b] = h_nsteps[b];
+    pin_ns[1 + b] = h_nsteps[b];
   }
+  static_assert(sizeof(int) == 4, "int layout");
   CK(cudaMemcpyAsync(w.ra, pin_ra, (size_t)B * sizeof(double), cudaMemcpyHostToDevice, stream));
-  CK(cudaMemcpyAsync(w.nsteps, pin_ns, (size_t)B * sizeof(int), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(w.maxs, pin_ns, (size_t)(B + 1) * sizeof(int), cudaMemcpyHostToDevice, stream));
   CK(cudaEventRecord(h->pin_ev[slot], stream));
   h->pin_busy[slot] = true;
+  h->up_ns.assign(pin_ns + 1, pin_ns + 1 + B);
+  h->up_ns.push_back(maxs);
+  h->up_ra.assign(pin_ra, pin_ra + B);
+  return RBC_OK;
+}
+
+static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps, const double* h_ra,
+                             double* d_nu_integral, cudaStream_t stream) {
+  if (!h || B < 0 || (B > 0 && (!d_states || !h_nsteps))) return fail(RBC_EINVAL, "null argument or B < 0");
+  if (B == 0) return RBC_OK;
+  int maxs = 0;
+  for (int b = 0; b < B; ++b) {
+    if (h_nsteps[b] < 0) return fail(RBC_EINVAL, "negative step count");
+    maxs = std::max(maxs, h_nsteps[b]);
+    if (h_ra && !(h_ra[b] >= 0 && std::isfinite(h_ra[b]))) return fail(RBC_EINVAL, "Rayleigh number must be >= 0");
+  }
+  rbc_status s = rbc_reserve(h, B);
+  if (s != RBC_OK) return s;
+  const Work& w = h->w;
+  double* X = static_cast<double*>(d_states);
+  double* nu = d_nu_integral ? d_nu_integral : w.nu;
+  bool same = (int)h->up_ns.size() == B + 1 && h->up_ns[B] == maxs;
+  for (int b = 0; same && b < B; ++b)
+    same = h->up_ns[b] == h_nsteps[b] && h->up_ra[b] == (h_ra ? h_ra[b] : h->g.Ra);
+  if (!same) {
+    rbc_status us = upload_steps(h, B, h_nsteps, h_ra, maxs, stream);
+    if (us != RBC_OK) return us;
+  }
   CK(cudaMemsetAsync(w.step, 0, sizeof(int), stream));
   CK(cudaMemsetAsync(w.flags, 0, (size_t)B * sizeof(int), stream));
   CK(cudaMemsetAsync(nu, 0, (size_t)B * sizeof(double), stream));
   h->last_B = B;
   const bool graphs = h->use_graphs && !h->prof.on && maxs >= 2;
   if (graphs) {
-    rbc_status gs = ensure_step_graph(h, X, B, nu);
+    cudaGraphExec_t ex = nullptr;
+    rbc_status gs = step_graph(h, X, B, nu, &ex);
     if (gs != RBC_OK) return gs;
-    for (int st = 0; st < maxs; ++st) CK(cudaGraphLaunch(h->step_graph, stream));
+    CK(cudaGraphLaunch(ex, stream));
     add_launches((unsigned long long)maxs * kStepKernels);
   } else {
     for (int st = 0; st < maxs; ++st) {
@@ -915,6 +1002,16 @@ static bool whole_steps(double len, double dt, int* n) {
 
 extern "C" void parareal_destroy(parareal_t p) {
   if (!p) return;
+  if (p->sF) cudaStreamSynchronize(p->sF);
+  if (p->sG) cudaStreamSynchronize(p->sG);
+  for (cudaEvent_t e : p->ev_g0) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_f) cudaEventDestroy(e);
+  for (cudaEvent_t e : {p->ev_begin, p->ev_copy, p->ev_fdone, p->ev_gdone})
+    if (e) cudaEventDestroy(e);
+  if (p->sF) cudaStreamDestroy(p->sF);
+  if (p->sG) cudaStreamDestroy(p->sG);
+  rbc_destroy(p->coarse2);
+  cudaFree(p->d_C2);
   cudaFree(p->d_F);
   cudaFree(p->d_Uold);
   cudaFree(p->d_Gold);
@@ -961,66 +1058,130 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
   }
   rbc_status s = rbc_reserve(fine, N);
   if (s == RBC_OK) s = rbc_reserve(coarse, 1);
+  if (s == RBC_OK)
+    s = rbc_create(gc.Ra, gc.Pr, gc.Lx, gc.Nx, gc.Nz, gc.dt, &coarse->opts, &p->coarse2);
+  if (s == RBC_OK) s = rbc_reserve(p->coarse2, 1);
   if (s != RBC_OK) {
     parareal_destroy(p);
     return s;
   }
+  bool ok2 = cudaMalloc(&p->d_C2, Sc) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&p->sF, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&p->sG, cudaStreamNonBlocking) == cudaSuccess;
+  p->ev_g0.assign(N, nullptr);
+  p->ev_f.assign(N, nullptr);
+  for (int n = 0; ok2 && n < N; ++n)
+    ok2 = cudaEventCreateWithFlags(&p->ev_g0[n], cudaEventDisableTiming) == cudaSuccess &&
+          cudaEventCreateWithFlags(&p->ev_f[n], cudaEventDisableTiming) == cudaSuccess;
+  for (cudaEvent_t* e : {&p->ev_begin, &p->ev_copy, &p->ev_fdone, &p->ev_gdone})
+    ok2 = ok2 && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok2) {
+    cudaGetLastError();
+    parareal_destroy(p);
+    return fail(RBC_ENOMEM, "Parareal streams and events");
+  }
+  p->group = std::max(1, (N + 3) / 4);
   *out = p;
+  return RBC_OK;
+}
+
+extern "C" rbc_status parareal_set_group(parareal_t p, int group) {
+  if (!p || group < 1) return fail(RBC_EINVAL, "bad handle or group < 1");
+  p->group = std::min(group, p->N);
+  return RBC_OK;
+}
+
+// Fine sweep of an iteration on slices n >= n0, on sF, in groups of slices
+// [j*group, (j+1)*group) cut at n0; group j waits for `wait_for(a, cnt)`, an
+// event of the stream that writes its inputs, and records ev_f[j].
+template <class WaitFor>
+static rbc_status fine_groups(parareal_t p, int n0, const std::vector<int>& nfv, WaitFor wait_for) {
+  rbc_t F = p->fine;
+  const size_t Sf = state_doubles(F->g);
+  for (int j = 0; j * p->group < p->N; ++j) {
+    const int a = std::max(j * p->group, n0);
+    const int cnt = std::min((j + 1) * p->group, p->N) - a;
+    if (cnt <= 0) continue;
+    CK(cudaStreamWaitEvent(p->sF, wait_for(a, cnt), 0));
+    rbc_status s = rbc_step_batch(F, p->d_F + (size_t)a * Sf, cnt, nfv.data(), p->d_I + a, p->sF);
+    if (s != RBC_OK) return s;
+    CK(cudaEventRecord(p->ev_f[j], p->sF));
+  }
   return RBC_OK;
 }
 
 extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_iters, int* k_done,
                                        double* defects, double* nus, cudaStream_t stream) {
   if (!p || !d_U0 || !d_U || max_iters < 1) return fail(RBC_EINVAL, "bad arguments");
-  rbc_t F = p->fine, G = p->coarse;
+  rbc_t F = p->fine, G = p->coarse, G2 = p->coarse2;
   const Grid &gf = F->g, &gc = G->g;
   const size_t Sf = state_doubles(gf), Sc = state_doubles(gc);
+  const size_t Bf = Sf * sizeof(double), Bc = Sc * sizeof(double);
   const int N = p->N;
   double* U = static_cast<double*>(d_U);
-  std::vector<int> ncv(1, p->nc);
+  std::vector<int> ncv(1, p->nc), nfv(N, p->nf);
   if (k_done) *k_done = 0;
-  CK(cudaMemcpyAsync(U, d_U0, Sf * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-  // k = 0: serial coarse sweep U_{n+1}^0 = G(U_n^0)
+  CK(cudaMemcpyAsync(U, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
+  CK(cudaMemcpyAsync(p->d_Uold, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
+  CK(cudaMemcpyAsync(p->d_F, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
+  CK(cudaEventRecord(p->ev_begin, stream));   // the side streams start after the caller's work and these copies
+  CK(cudaStreamWaitEvent(p->sF, p->ev_begin, 0));
+  CK(cudaStreamWaitEvent(p->sG, p->ev_begin, 0));
+  // k = 0: serial coarse sweep U_{n+1}^0 = G(U_n^0).  The coarse chain carries
+  // its own state (restricting the prolonged state gives it back exactly), so
+  // nothing here reads U while the correction sweep rewrites it.
+  CK(launch_restrict(gf, gc, U, p->d_C, 1, stream));
   for (int n = 0; n < N; ++n) {
-    CK(launch_restrict(gf, gc, U + n * Sf, p->d_C, 1, stream));
     rbc_status s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, stream);
     if (s != RBC_OK) return s;
-    CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Sc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Bc, cudaMemcpyDeviceToDevice, stream));
     CK(launch_prolong(gf, gc, p->d_C, U + (n + 1) * Sf, 1, stream));
+    CK(cudaMemcpyAsync(p->d_Uold + (n + 1) * Sf, U + (n + 1) * Sf, Bf, cudaMemcpyDeviceToDevice, stream));
+    if (n + 1 < N) CK(cudaMemcpyAsync(p->d_F + (n + 1) * Sf, U + (n + 1) * Sf, Bf, cudaMemcpyDeviceToDevice, stream));
+    CK(cudaEventRecord(p->ev_g0[n], stream));
   }
-  std::vector<int> nfv(N, p->nf);
   std::vector<double> I(N), nrm(2 * (N + 1));
   double nu_prev = 0.0;
   const int n_half = N / 2;
   const double win = (p->t1 - p->t0) * (double)(N - n_half) / N;
   rbc_status result = (p->criterion == RBC_CRIT_FIXED) ? RBC_OK : RBC_ENOTCONVERGED;
   for (int k = 1; k <= max_iters; ++k) {
-    // fine sweep on slices n >= k-1 (earlier slices are already exact)
     const int n0 = k - 1;
-    CK(cudaMemcpyAsync(p->d_F + n0 * Sf, U + n0 * Sf, (size_t)(N - n0) * Sf * sizeof(double),
-                       cudaMemcpyDeviceToDevice, stream));
-    rbc_status s = rbc_step_batch(F, p->d_F + n0 * Sf, N - n0, nfv.data(), p->d_I + n0, stream);
+    rbc_status s;
+    if (k == 1) {
+      // group inputs U_a .. U_{a+cnt-1} come from the U^0 sweep, up to its step a+cnt-2
+      s = fine_groups(p, 0, nfv, [&](int a, int cnt) { return a + cnt >= 2 ? p->ev_g0[a + cnt - 2] : p->ev_begin; });
+    } else {
+      // U^{k-1} is final: keep it for the defect and as the fine inputs
+      CK(cudaMemcpyAsync(p->d_Uold, U, (size_t)(N + 1) * Bf, cudaMemcpyDeviceToDevice, stream));
+      CK(cudaMemcpyAsync(p->d_F + n0 * Sf, U + n0 * Sf, (size_t)(N - n0) * Bf, cudaMemcpyDeviceToDevice, stream));
+      CK(cudaEventRecord(p->ev_copy, stream));
+      CK(cudaStreamWaitEvent(p->sG, p->ev_copy, 0));
+      s = fine_groups(p, n0, nfv, [&](int, int) { return p->ev_copy; });
+    }
     if (s != RBC_OK) return s;
-    s = rbc_check_diverged(F, stream);
-    if (s != RBC_OK) return s;
-    CK(cudaMemcpyAsync(p->d_Uold, U, (size_t)(N + 1) * Sf * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-    // serial correction sweep
+    // serial correction sweep on sG
     for (int n = 0; n < N; ++n) {
+      if (k == 1) CK(cudaStreamWaitEvent(p->sG, p->ev_g0[n], 0));   // Gold_n, and U^0_{n+1} written
+      if (n >= n0) CK(cudaStreamWaitEvent(p->sG, p->ev_f[n / p->group], 0));
       if (n <= k - 1) {
         // U_n unchanged since the last iteration: G(U_n) = Gold_n exactly
         CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_Gold + n * Sc, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1,
-                          stream));
+                          p->sG));
         continue;
       }
-      CK(launch_restrict(gf, gc, U + n * Sf, p->d_C, 1, stream));
-      s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, stream);
+      CK(launch_restrict(gf, gc, U + n * Sf, p->d_C2, 1, p->sG));
+      s = rbc_step_batch(G2, p->d_C2, 1, ncv.data(), nullptr, p->sG);
       if (s != RBC_OK) return s;
-      CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_C, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1, stream));
-      CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Sc * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_C2, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1, p->sG));
+      CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C2, Bc, cudaMemcpyDeviceToDevice, p->sG));
     }
-    s = rbc_check_diverged(G, stream);
-    if (s != RBC_OK) return s;
-    // Defect_k = max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k||  (L2 of T)
+    CK(cudaEventRecord(p->ev_gdone, p->sG));
+    CK(cudaEventRecord(p->ev_fdone, p->sF));
+    CK(cudaStreamWaitEvent(stream, p->ev_gdone, 0));
+    CK(cudaStreamWaitEvent(stream, p->ev_fdone, 0));
+    // Defect_k = max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k||  (L2 of T); a non-finite
+    // fine or coarse result reaches U through the correction and shows here
     CK(launch_l2_diff(gf, F->t, U, p->d_Uold, N + 1, p->d_norm, stream));
     CK(launch_l2_diff(gf, F->t, U, nullptr, N + 1, p->d_norm + N + 1, stream));
     CK(cudaMemcpyAsync(nrm.data(), p->d_norm, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -1032,7 +1193,10 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
       if (nrm[N + 1 + n] > 0) defect = std::max(defect, std::sqrt(nrm[n] / nrm[N + 1 + n]));
     }
     double nu = 0.0;
-    for (int n = n_half; n < N; ++n) nu += I[n];
+    for (int n = n_half; n < N; ++n) {
+      if (!std::isfinite(I[n])) return fail(RBC_EDIVERGED, "non-finite Nu integral");
+      nu += I[n];
+    }
     nu /= win;
     if (defects) defects[k - 1] = defect;
     if (nus) nus[k - 1] = nu;
@@ -1040,6 +1204,7 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
     if (p->criterion == RBC_CRIT_DEFECT && defect <= p->tol) return RBC_OK;
     if (p->criterion == RBC_CRIT_NU && k >= 2 && std::fabs(nu - nu_prev) <= p->tol * std::fabs(nu)) return RBC_OK;
     nu_prev = nu;
+    if (k >= N) break;   // U^N is the serial fine solution
   }
   return result;
 }

@@ -87,6 +87,7 @@ struct Work {
   double* Z;       // z-inverse output, [B][9][Mz][nm] complex (FP64, or FP32 in the first half)
   double* Q;       // row-kernel output, [B][2][Mz][nm] complex (FP64 or FP32)
   double* wT;      // [B][Mz] x-mean of w T
+  int* maxs;       // [1] max over nsteps, right before nsteps (copied with it)
   int* nsteps;     // [B]
   int* step;       // [1] step counter of the running batch
   int* flags;      // [B] non-finite flags
@@ -111,6 +112,8 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
 cudaError_t launch_explicit(const Grid& g, const Tables& t, const Work& w, const double* X, int B,
                             bool all_active, cudaStream_t s);
 cudaError_t launch_advance(const Work& w, cudaStream_t s);
+// advance the step counter and keep the enclosing graph loop running while step < maxs
+cudaError_t launch_advance_loop(const Work& w, cudaGraphConditionalHandle loop, cudaStream_t s);
 
 cudaError_t launch_nu_final(const Grid& g, const Tables& t, const Work& w, const double* X, int B,
                             double* nu, cudaStream_t s);

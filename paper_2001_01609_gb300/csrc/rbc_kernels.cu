@@ -927,6 +927,14 @@ static size_t solve_smem(const Grid& g, int B) { return (size_t)5 * g.nq * 2 * s
 
 __global__ void k_advance(int* step) { *step += 1; }
 
+// Body end of the device-side step loop: the loop ends once every state of the
+// batch has taken its steps (maxs is written by the host before each launch).
+__global__ void k_advance_loop(int* step, const int* maxs, cudaGraphConditionalHandle loop) {
+  const int s = *step + 1;
+  *step = s;
+  cudaGraphSetConditional(loop, s < *maxs ? 1u : 0u);
+}
+
 static inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 static std::atomic<unsigned long long> g_launches{0};
@@ -1086,6 +1094,12 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
 
 cudaError_t launch_advance(const Work& w, cudaStream_t s) {
   k_advance<<<1, 1, 0, s>>>(w.step);
+  count();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_loop(const Work& w, cudaGraphConditionalHandle loop, cudaStream_t s) {
+  k_advance_loop<<<1, 1, 0, s>>>(w.step, w.maxs, loop);
   count();
   return cudaGetLastError();
 }

@@ -361,7 +361,7 @@ class Engine:
         self.peak_active = max(self.peak_active, sum(len(c.runs) for c in self.classes.values()) + 1)
         r.t_admit = time.perf_counter() - self.t0
         with self.rt.on(cls.sg):
-            run.U[0].copy_(r.U0)
+            run.U[0].copy_(r.U0, non_blocking=True)   # U0 may be pinned host memory
         cls.runs.append(run)
 
     def _finish(self, run, status):

@@ -237,6 +237,44 @@ def test_parareal_stopping_criteria(rbc):
         rbc.Parareal(F, G, 0.0, T * 1.0001, N)          # not a whole number of steps
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_parareal_schedule_does_not_change_results(rbc, precision):
+    """The overlap of the coarse, fine and correction sweeps (fine groups of
+    1, 2, 4 or all slices) changes timing only: iterates, defects and Nu agree
+    bit for bit; after nslices iterations U is the serial fine solution."""
+    Ra, Nf, Zf, Nc, Zc, dtf, dtc = 3e4, 32, 16, 16, 8, 2e-3, 4e-3
+    N, nf = 6, 8
+    T = N * nf * dtf
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nf, Zf, dtf, precision)
+    G = rbc.Propagator(Ra, 1.0, 2.0, Nc, Zc, dtc, precision)
+    u0 = F.new_states(1)
+    F.set_state(u0[0], initial_temperature(Nf, Zf, seed=2, amplitude=0.3))
+    out = []
+    for group in (N, 1, 2, 4):
+        P = rbc.Parareal(F, G, 0.0, T, N)
+        P.set_group(group)
+        U = F.new_states(N + 1)
+        st, k, d, nus = P.iterate(u0[0], U, 3)
+        assert st == rbc.RBC_OK and k == 3
+        out.append((U, d, nus))
+    for U, d, nus in out[1:]:
+        assert torch.equal(U, out[0][0])
+        np.testing.assert_array_equal(d, out[0][1])
+        np.testing.assert_array_equal(nus, out[0][2])
+    # more iterations than slices: stops at k = N with the serial fine solution
+    P = rbc.Parareal(F, G, 0.0, T, N)
+    U = F.new_states(N + 1)
+    st, k, d, _ = P.iterate(u0[0], U, N + 2)
+    assert st == rbc.RBC_OK and k == N
+    ser = F.new_states(1)
+    ser.copy_(u0[0:1])
+    for n in range(1, N + 1):
+        F.step_batch(ser, nf)
+        assert torch.equal(ser[0], U[n]), n
+    with pytest.raises(rbc.RBCError):
+        P.set_group(0)
+
+
 @pytest.mark.parametrize("Nx,Nz,Ra", [(64, 32, 1e5), (32, 18, 2e5), (256, 64, 1e6)])
 def test_mixed_precision_few_steps_within_stated_tolerance(rbc, Nx, Nz, Ra):
     """RBC_MIXED: FP32 transforms and products, FP64 solves and RK combination.

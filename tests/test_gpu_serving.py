@@ -116,7 +116,7 @@ def test_parareal_building_blocks_match_oracle(rbc):
 
 def small_classes(Nx, Nz, precision):
     from paper_2001_01609_gb300.serving import ClassConfig
-    return ClassConfig(Nx, Nz, precision, 1e-3, 2e-3, 20, 10, Nx // 2, Nz // 2)
+    return ClassConfig(Nx, Nz, precision, 2.5e-4, 5e-4, 20, 10, Nx // 2, Nz // 2)
 
 
 def make_u0(rbc, eng, req, amp=0.3):
