@@ -131,6 +131,18 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------
+def fine_group_starts(N, group, first, n0=0):
+    """First slice of each fine group of parareal_iterate's schedule (and N)."""
+    a = [n0]
+    if group >= N:
+        return [n0, N]
+    size = first
+    while a[-1] < N:
+        a.append(min(N, a[-1] + size))
+        size = min(group, 2 * size)
+    return a
+
+
 def run_gb300(args, w):
     import torch
     import torch.distributed as dist
@@ -161,7 +173,8 @@ def run_gb300(args, w):
     N = w["slices"]
     P = rbc.Parareal(F, G, 0.0, dv["t_end"], N)
     group = args.group if args.group else -(-N // 4)
-    P.set_group(group)
+    first = args.first_group if args.first_group else -(-group // 4)
+    P.set_schedule(group, first, args.fine_streams, args.coarse_priority)
     stream = torch.cuda.current_stream()
     U0 = F.new_states(1)
     Th = initial_temperature(w["Nx"], w["Nz"], seed=w["seed"] + rank, Lx=w["Lx"])
@@ -194,8 +207,9 @@ def run_gb300(args, w):
     for si in range(args.steps):
         flush.zero_()                                         # L2 flush between timed steps
         torch.cuda.synchronize()
-        # sampled kernel timing: the step's first coarse call and first fine group
-        # are recorded kernel by kernel (without their graphs), on their own streams
+        # sampled kernel timing: the first 8 RK443 steps of the step's first coarse
+        # call and of its first fine group are recorded kernel by kernel, on
+        # their own streams; everything else runs on the graph loops
         G.profile(True, sample=True)
         F.profile(True, sample=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -225,18 +239,24 @@ def run_gb300(args, w):
     value = world * fine_dof_steps * args.steps / t_total
     e2e_value = world * fine_dof_steps * args.steps / e2e_total
 
-    # Per-kernel time over the timed steps, from the samples: mean time per
-    # launch times the known launch count.  Fine: groups of `group` slices,
+    # Per-kernel time over the timed steps, from the samples (8 steps each of
+    # one coarse call and one fine group): mean time per launch times the
+    # known launch count.  Fine: groups of `group` slices,
     # nf steps each, 4 stages per step; coarse: (2N - 1) nc steps per iteration
     # (the correction sweep reuses G(U_0)), 4 stages per step.
+    # The fine groups differ in size: the sample (the first group, `first`
+    # slices) gives a time per launch and slice, scaled to all N slices.
     kern = {}
-    f_launches = 4 * (-(-N // group)) * w["steps_per_slice"] * args.steps
+    starts = fine_group_starts(N, group, first)
+    f_launches = 4 * (len(starts) - 1) * w["steps_per_slice"] * args.steps
+    f_slice_launches = 4 * N * w["steps_per_slice"] * args.steps
+    b0 = starts[1] - starts[0]
     for k, v in prof_f.items():
         if v["launches"]:
             per = v["ms"] / v["launches"]
-            kern["fine:" + k] = dict(ms=per * f_launches, launches=f_launches, per_ms=per,
+            kern["fine:" + k] = dict(ms=per / b0 * f_slice_launches, launches=f_launches, per_ms=per,
                                      flops_per=v["flops"] / v["launches"], bytes_per=v["bytes"] / v["launches"],
-                                     sampled_launches=v["launches"])
+                                     sampled_launches=v["launches"], sampled_batch=b0)
     g_launches = 4 * (2 * N - 1) * dv["nc"] * args.steps
     for k, v in prof_g.items():
         if v["launches"]:
@@ -265,7 +285,8 @@ def run_gb300(args, w):
                                 fine_steps_per_slice=w["steps_per_slice"], coarse_steps_per_slice=dv["nc"],
                                 dt=w["dt"], dt_coarse=dv["dtc"], t_end=dv["t_end"], dof_per_slice=dv["dof"],
                                 step="one Parareal iteration (coarse sweep, batched fine sweep, correction, norms)",
-                                fine_group=group,
+                                fine_group=group, first_fine_group=first, fine_streams=args.fine_streams,
+                                coarse_priority=args.coarse_priority,
                                 schedule="coarse sweep, fine groups and correction sweep overlapped on 3 streams",
                                 l2="flushed between timed steps (256 MB write)",
                                 parallelism=f"{world} independent problems" if world > 1 else "single GPU"),
@@ -457,7 +478,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(SERVING))
-    ap.add_argument("--group", type=int, default=0, help="slices per fine group (default: a quarter of the slices)")
+    ap.add_argument("--group", type=int, default=0, help="largest fine group (default: a quarter of the slices)")
+    ap.add_argument("--first-group", type=int, default=0, help="first fine group (default: a quarter of --group)")
+    ap.add_argument("--fine-streams", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--coarse-priority", type=int, default=1, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
     args = ap.parse_args()

@@ -188,18 +188,27 @@ void parareal_destroy(parareal_t p);
  * serial fine solution.  Synchronous on `stream` (one small D2H per iteration).
  *
  * Schedule (the results do not depend on it, bit for bit): the coarse sweep
- * U^0 runs on `stream`; the fine sweep runs in groups of slices on an internal
- * stream, each group starting as soon as the coarse sweep has produced its
- * inputs; the correction sweep runs on a second internal stream with a second
- * coarse handle, each slice starting when its fine group and its coarse U^0
- * step are done.  So within an iteration the three sweeps overlap.           */
+ * U^0 and the correction sweep (with a second coarse handle) run on two
+ * internal streams; the fine sweep runs in groups of slices on internal
+ * streams, each group starting as soon as the coarse sweep has produced its
+ * inputs; correction step n starts when its fine group and coarse step n are
+ * done.  So the three sweeps of an iteration overlap.  `stream` waits for all
+ * of it before the norms.  parareal_set_schedule tunes it.                  */
 rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_iters,
                             int* k_done, double* defects, double* nus, cudaStream_t stream);
 
-/* Slices per fine group of the schedule above (default ceil(nslices / 4));
- * group >= nslices runs each fine sweep as one batch after the coarse sweep
- * U^0 has finished.  RBC_EINVAL if group < 1.  Changes timing only.         */
-rbc_status parareal_set_group(parareal_t p, int group);
+/* Schedule of parareal_iterate (timing only; results are the same bit for bit):
+ *  group:        largest fine group (default ceil(nslices / 4)); group >=
+ *                nslices runs each fine sweep as one batch after the coarse
+ *                sweep U^0 has finished;
+ *  first_group:  size of the first fine group (1 <= first_group <= group);
+ *                sizes then double up to group (default ceil(group / 4));
+ *  fine_streams: 1 or 2 streams (and fine handles) the groups alternate over
+ *                (default 2);
+ *  coarse_priority: 1 runs both coarse sweeps on high-priority streams
+ *                (default 1).
+ * RBC_EINVAL outside these ranges.                                          */
+rbc_status parareal_set_schedule(parareal_t p, int group, int first_group, int fine_streams, int coarse_priority);
 
 /* ---- Instrumentation (outside the paper's method) ----
  * Kernel kinds of one RK443 stage: z-inverse transform, row kernel (x-FFTs and
@@ -207,9 +216,10 @@ rbc_status parareal_set_group(parareal_t p, int group);
 enum { RBC_KERNEL_ZINV = 0, RBC_KERNEL_ROWS = 1, RBC_KERNEL_ZFWD = 2, RBC_KERNEL_SOLVE = 3, RBC_NKERNELS = 4 };
 
 /* rbc_profile(h, 1) starts recording a CUDA event pair on the launching stream
- * around every stage kernel that h launches and clears the totals; (h, 2)
- * does the same for the next rbc_step_batch call only (a sample: calls that
- * are recorded run without their CUDA graph); (h, 0) stops recording.  rbc_profile_read synchronises the device and returns, per
+ * around every stage kernel that h launches (such calls run without their
+ * CUDA graph) and clears the totals; (h, 2) records only the first 8 steps of
+ * the next rbc_step_batch call (a sample: the rest of that call runs on its
+ * graph as usual); (h, 0) stops recording.  rbc_profile_read synchronises the device and returns, per
  * kernel kind, the summed event time (ms), the launch count, and the
  * algorithmic FP operations and DRAM bytes of those launches (each operand
  * read once, each result written once, all B slices active).  Any of the

@@ -288,11 +288,19 @@ struct pr_s {
   // carry the per-slice dependencies.
   rbc_t coarse2 = nullptr;
   double* d_C2 = nullptr;     // 1 coarse state of the correction sweep
-  int group = 0;
-  cudaStream_t sF = nullptr, sG = nullptr;
+  int group = 0;              // largest fine group
+  int first_group = 0;        // first fine group
+  int fine_streams = 1;       // fine groups alternate over this many streams
+  int coarse_priority = 0;    // 1: the coarse sweeps run on high-priority streams
+  static constexpr int kFineStreams = 2;
+  rbc_t fines[kFineStreams] = {};          // fines[0] = fine; the others are copies of it
+  cudaStream_t sF[kFineStreams] = {};      // default priority
+  cudaStream_t sG0 = nullptr, sG = nullptr;        // coarse sweeps, default priority
+  cudaStream_t sG0_hi = nullptr, sG_hi = nullptr;  // the same, high priority
   std::vector<cudaEvent_t> ev_g0;   // [N] U^0 sweep done with slice n
   std::vector<cudaEvent_t> ev_f;    // [N] fine group j done
-  cudaEvent_t ev_begin = nullptr, ev_copy = nullptr, ev_fdone = nullptr, ev_gdone = nullptr;
+  cudaEvent_t ev_begin = nullptr, ev_copy = nullptr, ev_gdone = nullptr, ev_g0done = nullptr;
+  cudaEvent_t ev_fdone[kFineStreams] = {};
 };
 
 extern "C" const char* rbc_last_error(void) { return g_err; }
@@ -879,21 +887,30 @@ static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps
   CK(cudaMemsetAsync(w.flags, 0, (size_t)B * sizeof(int), stream));
   CK(cudaMemsetAsync(nu, 0, (size_t)B * sizeof(double), stream));
   h->last_B = B;
-  const bool graphs = h->use_graphs && !h->prof.on && maxs >= 2;
-  if (graphs) {
+  // Steps launched one kernel at a time: all of them while profiling every
+  // call; the first kProfileSampleSteps of a sampled call (the rest continue
+  // on the graph loop from the same device step counter); none otherwise.
+  const int eager = !h->prof.on ? 0 : h->prof.once ? std::min(maxs, kProfileSampleSteps) : maxs;
+  for (int st = 0; st < eager; ++st) {
+    for (int stage = 1; stage <= 4; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
+    CK(launch_advance(w, stream));
+  }
+  if (h->prof.once) h->prof.on = false;
+  const int rest = maxs - eager;
+  if (rest >= 2 && h->use_graphs) {
     cudaGraphExec_t ex = nullptr;
     rbc_status gs = step_graph(h, X, B, nu, &ex);
     if (gs != RBC_OK) return gs;
     CK(cudaGraphLaunch(ex, stream));
-    add_launches((unsigned long long)maxs * kStepKernels);
+    add_launches((unsigned long long)rest * kStepKernels);
   } else {
-    for (int st = 0; st < maxs; ++st) {
+    for (int st = 0; st < rest; ++st) {
       for (int stage = 1; stage <= 4; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
       CK(launch_advance(w, stream));
     }
   }
   if (maxs > 0) CK(launch_nu_final(h->g, h->t, w, X, B, nu, stream));
-  if (h->prof.once) h->prof.on = h->prof.once = false;   // sampled profiling: this call only
+  if (h->prof.once) h->prof.on = h->prof.once = false;   // sampled profiling: this call only (its first steps)
   return RBC_OK;
 }
 
@@ -1002,14 +1019,15 @@ static bool whole_steps(double len, double dt, int* n) {
 
 extern "C" void parareal_destroy(parareal_t p) {
   if (!p) return;
-  if (p->sF) cudaStreamSynchronize(p->sF);
-  if (p->sG) cudaStreamSynchronize(p->sG);
+  for (cudaStream_t st : {p->sF[0], p->sF[1], p->sG0, p->sG, p->sG0_hi, p->sG_hi})
+    if (st) cudaStreamSynchronize(st);
   for (cudaEvent_t e : p->ev_g0) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_f) cudaEventDestroy(e);
-  for (cudaEvent_t e : {p->ev_begin, p->ev_copy, p->ev_fdone, p->ev_gdone})
+  for (cudaEvent_t e : {p->ev_begin, p->ev_copy, p->ev_gdone, p->ev_g0done, p->ev_fdone[0], p->ev_fdone[1]})
     if (e) cudaEventDestroy(e);
-  if (p->sF) cudaStreamDestroy(p->sF);
-  if (p->sG) cudaStreamDestroy(p->sG);
+  for (cudaStream_t st : {p->sF[0], p->sF[1], p->sG0, p->sG, p->sG0_hi, p->sG_hi})
+    if (st) cudaStreamDestroy(st);
+  for (int i = 1; i < pr_s::kFineStreams; ++i) rbc_destroy(p->fines[i]);
   rbc_destroy(p->coarse2);
   cudaFree(p->d_C2);
   cudaFree(p->d_F);
@@ -1061,51 +1079,93 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
   if (s == RBC_OK)
     s = rbc_create(gc.Ra, gc.Pr, gc.Lx, gc.Nx, gc.Nz, gc.dt, &coarse->opts, &p->coarse2);
   if (s == RBC_OK) s = rbc_reserve(p->coarse2, 1);
+  p->fines[0] = fine;
+  for (int i = 1; s == RBC_OK && i < pr_s::kFineStreams; ++i) {
+    s = rbc_create(gf.Ra, gf.Pr, gf.Lx, gf.Nx, gf.Nz, gf.dt, &fine->opts, &p->fines[i]);
+    if (s == RBC_OK) s = rbc_reserve(p->fines[i], N);
+  }
   if (s != RBC_OK) {
     parareal_destroy(p);
     return s;
   }
-  bool ok2 = cudaMalloc(&p->d_C2, Sc) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&p->sF, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&p->sG, cudaStreamNonBlocking) == cudaSuccess;
+  int prio_lo = 0, prio_hi = 0;
+  bool ok2 = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) == cudaSuccess &&
+             cudaMalloc(&p->d_C2, Sc) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&p->sG0, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&p->sG, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&p->sG0_hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&p->sG_hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess;
+  for (int i = 0; ok2 && i < pr_s::kFineStreams; ++i)
+    ok2 = cudaStreamCreateWithFlags(&p->sF[i], cudaStreamNonBlocking) == cudaSuccess &&
+          cudaEventCreateWithFlags(&p->ev_fdone[i], cudaEventDisableTiming) == cudaSuccess;
   p->ev_g0.assign(N, nullptr);
   p->ev_f.assign(N, nullptr);
   for (int n = 0; ok2 && n < N; ++n)
     ok2 = cudaEventCreateWithFlags(&p->ev_g0[n], cudaEventDisableTiming) == cudaSuccess &&
           cudaEventCreateWithFlags(&p->ev_f[n], cudaEventDisableTiming) == cudaSuccess;
-  for (cudaEvent_t* e : {&p->ev_begin, &p->ev_copy, &p->ev_fdone, &p->ev_gdone})
+  for (cudaEvent_t* e : {&p->ev_begin, &p->ev_copy, &p->ev_gdone, &p->ev_g0done})
     ok2 = ok2 && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
   if (!ok2) {
     cudaGetLastError();
     parareal_destroy(p);
     return fail(RBC_ENOMEM, "Parareal streams and events");
   }
+  // default schedule: largest fine group N/4, first group a quarter of that,
+  // groups alternating over two fine streams, coarse sweeps at high priority
   p->group = std::max(1, (N + 3) / 4);
+  p->first_group = std::max(1, (p->group + 3) / 4);
+  p->fine_streams = 2;
+  p->coarse_priority = 1;
   *out = p;
   return RBC_OK;
 }
 
-extern "C" rbc_status parareal_set_group(parareal_t p, int group) {
-  if (!p || group < 1) return fail(RBC_EINVAL, "bad handle or group < 1");
+extern "C" rbc_status parareal_set_schedule(parareal_t p, int group, int first_group, int fine_streams,
+                                            int coarse_priority) {
+  if (!p || group < 1 || first_group < 1 || first_group > group || fine_streams < 1 ||
+      fine_streams > pr_s::kFineStreams || coarse_priority < 0 || coarse_priority > 1)
+    return fail(RBC_EINVAL, "bad schedule");
   p->group = std::min(group, p->N);
+  p->first_group = std::min(first_group, p->group);
+  p->fine_streams = fine_streams;
+  p->coarse_priority = coarse_priority;
   return RBC_OK;
 }
 
-// Fine sweep of an iteration on slices n >= n0, on sF, in groups of slices
-// [j*group, (j+1)*group) cut at n0; group j waits for `wait_for(a, cnt)`, an
-// event of the stream that writes its inputs, and records ev_f[j].
+// Fine groups of an iteration: slices n >= n0 cut into groups whose sizes
+// start at first_group and double up to `group`: a small first group lets the
+// correction sweep start early, larger later groups keep the fine sweep efficient.
+// Returns the first slice of each group (plus N at the end).
+static std::vector<int> fine_group_starts(const pr_s* p, int n0) {
+  std::vector<int> a{n0};
+  if (p->group >= p->N) {   // one batch
+    a.push_back(p->N);
+    return a;
+  }
+  int size = p->first_group;
+  while (a.back() < p->N) {
+    a.push_back(std::min(p->N, a.back() + size));
+    size = std::min(p->group, 2 * size);
+  }
+  return a;
+}
+
+// Launch the fine groups, group j on stream/handle j % kFineStreams after
+// `wait_for(a, cnt)` (an event of the stream that writes its inputs); group j
+// records ev_f[j], and slice_group[n] receives the group of slice n.
 template <class WaitFor>
-static rbc_status fine_groups(parareal_t p, int n0, const std::vector<int>& nfv, WaitFor wait_for) {
-  rbc_t F = p->fine;
-  const size_t Sf = state_doubles(F->g);
-  for (int j = 0; j * p->group < p->N; ++j) {
-    const int a = std::max(j * p->group, n0);
-    const int cnt = std::min((j + 1) * p->group, p->N) - a;
-    if (cnt <= 0) continue;
-    CK(cudaStreamWaitEvent(p->sF, wait_for(a, cnt), 0));
-    rbc_status s = rbc_step_batch(F, p->d_F + (size_t)a * Sf, cnt, nfv.data(), p->d_I + a, p->sF);
+static rbc_status fine_groups(parareal_t p, int n0, const std::vector<int>& nfv, std::vector<int>& slice_group,
+                              WaitFor wait_for) {
+  const size_t Sf = state_doubles(p->fine->g);
+  const std::vector<int> a = fine_group_starts(p, n0);
+  for (int j = 0; j + 1 < (int)a.size(); ++j) {
+    const int cnt = a[j + 1] - a[j];
+    const int i = j % p->fine_streams;
+    CK(cudaStreamWaitEvent(p->sF[i], wait_for(a[j], cnt), 0));
+    rbc_status s = rbc_step_batch(p->fines[i], p->d_F + (size_t)a[j] * Sf, cnt, nfv.data(), p->d_I + a[j], p->sF[i]);
     if (s != RBC_OK) return s;
-    CK(cudaEventRecord(p->ev_f[j], p->sF));
+    CK(cudaEventRecord(p->ev_f[j], p->sF[i]));
+    for (int n = a[j]; n < a[j + 1]; ++n) slice_group[n] = j;
   }
   return RBC_OK;
 }
@@ -1124,22 +1184,26 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
   CK(cudaMemcpyAsync(U, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
   CK(cudaMemcpyAsync(p->d_Uold, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
   CK(cudaMemcpyAsync(p->d_F, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
+  cudaStream_t s0 = p->coarse_priority ? p->sG0_hi : p->sG0;
+  cudaStream_t sg = p->coarse_priority ? p->sG_hi : p->sG;
   CK(cudaEventRecord(p->ev_begin, stream));   // the side streams start after the caller's work and these copies
-  CK(cudaStreamWaitEvent(p->sF, p->ev_begin, 0));
-  CK(cudaStreamWaitEvent(p->sG, p->ev_begin, 0));
-  // k = 0: serial coarse sweep U_{n+1}^0 = G(U_n^0).  The coarse chain carries
-  // its own state (restricting the prolonged state gives it back exactly), so
-  // nothing here reads U while the correction sweep rewrites it.
-  CK(launch_restrict(gf, gc, U, p->d_C, 1, stream));
+  for (cudaStream_t st : {p->sF[0], p->sF[1], s0, sg}) CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
+  // k = 0: serial coarse sweep U_{n+1}^0 = G(U_n^0), on s0.  The coarse chain
+  // carries its own state (restricting the prolonged state gives it back
+  // exactly), so nothing here reads U while the correction sweep rewrites it.
+  CK(launch_restrict(gf, gc, U, p->d_C, 1, s0));
   for (int n = 0; n < N; ++n) {
-    rbc_status s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, stream);
+    rbc_status s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, s0);
     if (s != RBC_OK) return s;
-    CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Bc, cudaMemcpyDeviceToDevice, stream));
-    CK(launch_prolong(gf, gc, p->d_C, U + (n + 1) * Sf, 1, stream));
-    CK(cudaMemcpyAsync(p->d_Uold + (n + 1) * Sf, U + (n + 1) * Sf, Bf, cudaMemcpyDeviceToDevice, stream));
-    if (n + 1 < N) CK(cudaMemcpyAsync(p->d_F + (n + 1) * Sf, U + (n + 1) * Sf, Bf, cudaMemcpyDeviceToDevice, stream));
-    CK(cudaEventRecord(p->ev_g0[n], stream));
+    CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Bc, cudaMemcpyDeviceToDevice, s0));
+    CK(launch_prolong(gf, gc, p->d_C, U + (n + 1) * Sf, 1, s0));
+    CK(cudaMemcpyAsync(p->d_Uold + (n + 1) * Sf, U + (n + 1) * Sf, Bf, cudaMemcpyDeviceToDevice, s0));
+    if (n + 1 < N) CK(cudaMemcpyAsync(p->d_F + (n + 1) * Sf, U + (n + 1) * Sf, Bf, cudaMemcpyDeviceToDevice, s0));
+    CK(cudaEventRecord(p->ev_g0[n], s0));
   }
+  CK(cudaEventRecord(p->ev_g0done, s0));
+  CK(cudaStreamWaitEvent(stream, p->ev_g0done, 0));
+  std::vector<int> slice_group(N, 0);
   std::vector<double> I(N), nrm(2 * (N + 1));
   double nu_prev = 0.0;
   const int n_half = N / 2;
@@ -1150,36 +1214,39 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
     rbc_status s;
     if (k == 1) {
       // group inputs U_a .. U_{a+cnt-1} come from the U^0 sweep, up to its step a+cnt-2
-      s = fine_groups(p, 0, nfv, [&](int a, int cnt) { return a + cnt >= 2 ? p->ev_g0[a + cnt - 2] : p->ev_begin; });
+      s = fine_groups(p, 0, nfv, slice_group,
+                      [&](int a, int cnt) { return a + cnt >= 2 ? p->ev_g0[a + cnt - 2] : p->ev_begin; });
     } else {
       // U^{k-1} is final: keep it for the defect and as the fine inputs
       CK(cudaMemcpyAsync(p->d_Uold, U, (size_t)(N + 1) * Bf, cudaMemcpyDeviceToDevice, stream));
       CK(cudaMemcpyAsync(p->d_F + n0 * Sf, U + n0 * Sf, (size_t)(N - n0) * Bf, cudaMemcpyDeviceToDevice, stream));
       CK(cudaEventRecord(p->ev_copy, stream));
-      CK(cudaStreamWaitEvent(p->sG, p->ev_copy, 0));
-      s = fine_groups(p, n0, nfv, [&](int, int) { return p->ev_copy; });
+      CK(cudaStreamWaitEvent(sg, p->ev_copy, 0));
+      s = fine_groups(p, n0, nfv, slice_group, [&](int, int) { return p->ev_copy; });
     }
     if (s != RBC_OK) return s;
     // serial correction sweep on sG
     for (int n = 0; n < N; ++n) {
-      if (k == 1) CK(cudaStreamWaitEvent(p->sG, p->ev_g0[n], 0));   // Gold_n, and U^0_{n+1} written
-      if (n >= n0) CK(cudaStreamWaitEvent(p->sG, p->ev_f[n / p->group], 0));
+      if (k == 1) CK(cudaStreamWaitEvent(sg, p->ev_g0[n], 0));   // Gold_n, and U^0_{n+1} written
+      if (n >= n0) CK(cudaStreamWaitEvent(sg, p->ev_f[slice_group[n]], 0));
       if (n <= k - 1) {
         // U_n unchanged since the last iteration: G(U_n) = Gold_n exactly
         CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_Gold + n * Sc, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1,
-                          p->sG));
+                          sg));
         continue;
       }
-      CK(launch_restrict(gf, gc, U + n * Sf, p->d_C2, 1, p->sG));
-      s = rbc_step_batch(G2, p->d_C2, 1, ncv.data(), nullptr, p->sG);
+      CK(launch_restrict(gf, gc, U + n * Sf, p->d_C2, 1, sg));
+      s = rbc_step_batch(G2, p->d_C2, 1, ncv.data(), nullptr, sg);
       if (s != RBC_OK) return s;
-      CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_C2, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1, p->sG));
-      CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C2, Bc, cudaMemcpyDeviceToDevice, p->sG));
+      CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_C2, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1, sg));
+      CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C2, Bc, cudaMemcpyDeviceToDevice, sg));
     }
-    CK(cudaEventRecord(p->ev_gdone, p->sG));
-    CK(cudaEventRecord(p->ev_fdone, p->sF));
+    CK(cudaEventRecord(p->ev_gdone, sg));
     CK(cudaStreamWaitEvent(stream, p->ev_gdone, 0));
-    CK(cudaStreamWaitEvent(stream, p->ev_fdone, 0));
+    for (int i = 0; i < pr_s::kFineStreams; ++i) {
+      CK(cudaEventRecord(p->ev_fdone[i], p->sF[i]));
+      CK(cudaStreamWaitEvent(stream, p->ev_fdone[i], 0));
+    }
     // Defect_k = max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k||  (L2 of T); a non-finite
     // fine or coarse result reaches U through the correction and shows here
     CK(launch_l2_diff(gf, F->t, U, p->d_Uold, N + 1, p->d_norm, stream));

@@ -137,6 +137,7 @@ cudaError_t launch_nusselt_static(const Grid& g, const Tables& t, const double* 
 unsigned long long launches_so_far();
 void add_launches(unsigned long long n);   // kernels launched through a replayed graph
 constexpr int kStepKernels = 17;           // 4 stages x 4 kernels + step counter
+constexpr int kProfileSampleSteps = 8;     // steps recorded kernel by kernel in a sampled call
 cudaError_t configure_kernels(const Grid& g);
 // tensor-core z inverse transform (rbc_tcgen05.cu)
 RBC_HD int tc_zinv_mtiles(const Grid& g, int nops);

@@ -12,6 +12,7 @@
 //            side in tau rows, UL banded solve of the implicit system
 //            (temperature first, then streamfunction with the implicit
 //            buoyancy coupling), RK accumulator updates, Nu_V accumulation.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,8 +43,10 @@ __device__ __forceinline__ void st2(double* p, double2 v) { *reinterpret_cast<do
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+// Roundings written out (explicit fma): the bits do not depend on how the
+// compiler would contract a*b + c*d in each kernel that inlines this.
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_double2(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 times_i(double2 a) { return make_double2(-a.y, a.x); }
@@ -76,7 +79,7 @@ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_fl
 __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 times_i(float2 a) { return make_float2(-a.y, a.x); }
@@ -102,41 +105,51 @@ template <typename T> __device__ __forceinline__ C2<T> cvt2(double2 a) { return 
 //   m = 0: omega = -U'),  d_x u,  d_z u,  T,  d_x T,  d_z T.
 // Output Z[b][field][j][m] (complex, real type T), fields in that order.
 // ---------------------------------------------------------------------------
+// Fields of one output row (j, m); half = 0: fields 0-3, 1: fields 4-8, -1: all.
 template <typename T>
 __device__ __forceinline__ void zinv_store(const Grid& g, T* Zb, int j, int m, T k, const C2<T>* P, C2<T> t0,
-                                           C2<T> t1) {
+                                           C2<T> t1, int half) {
   using V = C2<T>;
   const T zero = 0;
-  V u, w, dxo, dzo, dxu, dzu, dxT;
-  if (m == 0) {
-    u = mk2<T>(P[0].x, zero);
-    w = mk2<T>(zero, zero);
-    dxo = mk2<T>(zero, zero);
-    dzo = mk2<T>((T)-4 * P[2].x, zero);
-    dxu = mk2<T>(zero, zero);
-    dzu = mk2<T>((T)2 * P[1].x, zero);
-    dxT = mk2<T>(zero, zero);
-  } else {
-    u = (T)2 * P[1];
-    w = -k * times_i(P[0]);                            // -ik psi
-    const V om = (k * k) * P[0] - (T)4 * P[2];         // omega = -(4 psi'' - k^2 psi)
-    dxo = k * times_i(om);
-    dzo = ((T)2 * k * k) * P[1] - (T)8 * P[3];         // -(8 psi''' - 2 k^2 psi')
-    dxu = k * times_i(u);
-    dzu = (T)4 * P[2];
-    dxT = k * times_i(t0);
-  }
   const size_t fs = (size_t)g.Mz * g.nm * 2;
   T* zb = Zb + ((size_t)j * g.nm + m) * 2;
-  stc<T>(zb + 0 * fs, u);
-  stc<T>(zb + 1 * fs, w);
-  stc<T>(zb + 2 * fs, dxo);
-  stc<T>(zb + 3 * fs, dzo);
-  stc<T>(zb + 4 * fs, dxu);
-  stc<T>(zb + 5 * fs, dzu);
-  stc<T>(zb + 6 * fs, t0);
-  stc<T>(zb + 7 * fs, dxT);
-  stc<T>(zb + 8 * fs, (T)2 * t1);
+  if (half <= 0) {
+    V u, w, dxo, dzo;
+    if (m == 0) {
+      u = mk2<T>(P[0].x, zero);
+      w = mk2<T>(zero, zero);
+      dxo = mk2<T>(zero, zero);
+      dzo = mk2<T>((T)-4 * P[2].x, zero);
+    } else {
+      u = (T)2 * P[1];
+      w = -k * times_i(P[0]);                          // -ik psi
+      const V om = (k * k) * P[0] - (T)4 * P[2];       // omega = -(4 psi'' - k^2 psi)
+      dxo = k * times_i(om);
+      dzo = ((T)2 * k * k) * P[1] - (T)8 * P[3];       // -(8 psi''' - 2 k^2 psi')
+    }
+    stc<T>(zb + 0 * fs, u);
+    stc<T>(zb + 1 * fs, w);
+    stc<T>(zb + 2 * fs, dxo);
+    stc<T>(zb + 3 * fs, dzo);
+  }
+  if (half != 0) {
+    V dxu, dzu, dxT;
+    if (m == 0) {
+      dxu = mk2<T>(zero, zero);
+      dzu = mk2<T>((T)2 * P[1].x, zero);
+      dxT = mk2<T>(zero, zero);
+    } else {
+      const V u = (T)2 * P[1];
+      dxu = k * times_i(u);
+      dzu = (T)4 * P[2];
+      dxT = k * times_i(t0);
+    }
+    stc<T>(zb + 4 * fs, dxu);
+    stc<T>(zb + 5 * fs, dzu);
+    stc<T>(zb + 6 * fs, t0);
+    stc<T>(zb + 7 * fs, dxT);
+    stc<T>(zb + 8 * fs, (T)2 * t1);
+  }
 }
 
 template <typename T>
@@ -190,6 +203,9 @@ __device__ void zinv_item(const Grid& g, const T* __restrict__ Bz, const double*
       }
     }
   }
+  const T k = (T)(g.kfac * m);
+  T* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
+  const int jr = g.Mz - 1 - j;
   if (kp > 1) {
     if (wact) {
 #pragma unroll
@@ -199,32 +215,48 @@ __device__ void zinv_item(const Grid& g, const T* __restrict__ Bz, const double*
       }
     }
     __syncthreads();
-    if (w != 0) return;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      V e = part[q * 32 + lane], o = part[(6 + q) * 32 + lane];
-      for (int ww = 1; ww < kp; ++ww) {                // fixed order
-        e = e + part[(ww * 12 + q) * 32 + lane];
-        o = o + part[(ww * 12 + 6 + q) * 32 + lane];
-      }
-      E[q] = e;
-      O[q] = o;
+    // accumulator a (E_0..5, O_0..5) is summed by warp a % kp, over the warps'
+    // partial sums in warp order, into the first warp's slot
+    for (int a = w; a < 12; a += kp) {
+      V e = part[a * 32 + lane];
+      for (int ww = 1; ww < kp; ++ww) e = e + part[(ww * 12 + a) * 32 + lane];
+      part[a * 32 + lane] = e;
     }
-  } else if (w != 0) {
+    __syncthreads();
+    if (!valid) return;
+    // epilogue: warps take (row, half of the fields); with 2 warps one row each
+    const int nt = kp >= 4 ? 4 : kp;
+    for (int task = w; task < 4; task += nt) {
+      const int row = task & 1, half = task >> 1;
+      if (row == 1 && jr == j) continue;
+      V Ev[6], Ov[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        Ev[q] = part[q * 32 + lane];
+        Ov[q] = part[(6 + q) * 32 + lane];
+      }
+      V P[4];
+      if (row == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P[q] = Ev[q] + Ov[q];
+        zinv_store<T>(g, Zb, j, m, k, P, Ev[4] + Ov[4], Ev[5] + Ov[5], half);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P[q] = ((q & 1) ? (T)-1 : (T)1) * (Ev[q] - Ov[q]);
+        zinv_store<T>(g, Zb, jr, m, k, P, Ev[4] - Ov[4], (T)-1 * (Ev[5] - Ov[5]), half);
+      }
+    }
     return;
   }
-  if (!valid) return;
-  const T k = (T)(g.kfac * m);
-  T* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
+  if (w != 0 || !valid) return;
   V P[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) P[q] = E[q] + O[q];
-  zinv_store<T>(g, Zb, j, m, k, P, E[4] + O[4], E[5] + O[5]);
-  const int jr = g.Mz - 1 - j;
+  zinv_store<T>(g, Zb, j, m, k, P, E[4] + O[4], E[5] + O[5], -1);
   if (jr != j) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) P[q] = ((q & 1) ? (T)-1 : (T)1) * (E[q] - O[q]);
-    zinv_store<T>(g, Zb, jr, m, k, P, E[4] - O[4], (T)-1 * (E[5] - O[5]));
+    zinv_store<T>(g, Zb, jr, m, k, P, E[4] - O[4], (T)-1 * (E[5] - O[5]), -1);
   }
 }
 
@@ -295,10 +327,10 @@ __device__ C2<T>* fft_smem(C2<T>* a, C2<T>* b, int N, int na, int sign, const C2
       } else {
         const V t1 = v[1] + v[2], t2 = v[1] - v[2];
         const V m1 = v[0] - (T)0.5 * t1;
-        const V m2 = s3 * times_i(t2);
+        // m1 +- s3 i t2 with one rounding per part (explicit fma)
         ya[base] = v[0] + t1;
-        ya[base + Ns] = m1 + m2;
-        ya[base + 2 * Ns] = m1 - m2;
+        ya[base + Ns] = mk2<T>(fma(-s3, t2.y, m1.x), fma(s3, t2.x, m1.y));
+        ya[base + 2 * Ns] = mk2<T>(fma(s3, t2.y, m1.x), fma(-s3, t2.x, m1.y));
       }
     }
     __syncthreads();
@@ -423,9 +455,9 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
   double nU = 0.0, wt = 0.0;
   for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
     const T u = field(0, x), w = field(1, x);
-    const T nO = u * field(2, x) + w * field(3, x);
-    nU += (double)(u * field(4, x) + w * field(5, x));
-    const T nT = u * field(7, x) + w * field(8, x);
+    const T nO = fma(u, field(2, x), w * field(3, x));
+    nU += (double)fma(u, field(4, x), w * field(5, x));
+    const T nT = fma(u, field(7, x), w * field(8, x));
     wt += (double)(w * field(6, x));
     P[x] = mk2<T>(nT, nO);
   }
@@ -457,6 +489,109 @@ __global__ void __launch_bounds__(256) k_rows(Grid g, const C2<T>* __restrict__ 
                                               T* __restrict__ Q, double* __restrict__ wT, int B, int batched,
                                               const int* nsteps, const int* step) {
   rows_item<T>(g, tw, Z, Q, wT, B, batched, nsteps, nsteps ? *step : 0, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Row kernel for small batches (k_rows_cl): the same arithmetic as k_rows,
+// spread over a cluster of five CTAs per row so that a single slice uses five
+// times as many SMs' FP64 pipes.  CTA c runs the inverse FFT of field pair c
+// (fields 2c, 2c+1) in its shared memory; after a cluster barrier every CTA
+// forms the products for its share of the x points, reading the nine fields
+// from the five CTAs through distributed shared memory, and writes them, with
+// the per-point terms of the two x-means, into CTA 0.  After a second barrier
+// CTA 0 sums the x-means with exactly the per-thread order and tree of k_rows
+// (256 threads) and runs the forward FFT, so the results are bit for bit
+// those of k_rows.
+// ---------------------------------------------------------------------------
+constexpr int kRowsCluster = 5;
+constexpr int kRowsThreads = 256;
+
+static size_t rows_cl_bytes(const Grid& g, size_t es) {
+  // A, Bf, twiddles, P, P2 (complex) + two real per-point arrays (double)
+  return (size_t)g.Mx * 5 * 2 * es + (size_t)2 * g.Mx * 8;
+}
+static bool rows_use_cluster(const Grid& g, int B, size_t es) {
+  return (long)B * g.Mz <= 2L * 152 && rows_cl_bytes(g, es) <= 200 * 1024;
+}
+
+template <typename T>
+__global__ void __cluster_dims__(kRowsCluster, 1, 1) __launch_bounds__(kRowsThreads)
+    k_rows_cl(Grid g, const C2<T>* __restrict__ tw, const T* __restrict__ Z, T* __restrict__ Q,
+              double* __restrict__ wT, int B, const int* nsteps, const int* step) {
+  using V = C2<T>;
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char csm[];
+  __shared__ double red[kRowsThreads];
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = (int)cl.block_rank();
+  const int row = blockIdx.x / kRowsCluster;
+  const int b = row / g.Mz, j = row - b * g.Mz;
+  // uniform over the cluster (same b and step): no CTA reaches a cluster barrier alone
+  if (b >= B || !slice_active(nsteps, step, b)) return;
+  const int Mx = g.Mx, nm = g.nm;
+  V* A = reinterpret_cast<V*>(csm);
+  V* Bf = A + Mx;
+  V* tws = Bf + Mx;
+  V* P = tws + Mx;
+  V* P2 = P + Mx;
+  double* vU = reinterpret_cast<double*>(P2 + Mx);
+  double* vW = vU + Mx;
+  const size_t fs = (size_t)g.Mz * nm * 2;
+  const T* zrow = Z + (size_t)b * 9 * fs + (size_t)j * nm * 2;
+  for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
+    tws[x] = ldgc<T>(tw + x);
+    A[x] = rows_packed<T>(g, zrow, fs, c, x);
+  }
+  __syncthreads();
+  const V* res = fft_smem<T>(A, Bf, Mx, 1, +1, tws);   // same buffer in every CTA
+  cl.sync();
+  const V* fr[kRowsCluster];
+#pragma unroll
+  for (int r = 0; r < kRowsCluster; ++r) fr[r] = cl.map_shared_rank(res, r);
+  V* P0 = cl.map_shared_rank(P, 0);
+  double* vU0 = cl.map_shared_rank(vU, 0);
+  double* vW0 = cl.map_shared_rank(vW, 0);
+  auto field = [&](int fi, int x) -> T {
+    const V v = fr[fi >> 1][x];
+    return (fi & 1) ? v.y : v.x;
+  };
+  const int per = (Mx + kRowsCluster - 1) / kRowsCluster;
+  const int x0 = c * per, x1 = min(Mx, x0 + per);
+  for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+    const T u = field(0, x), w = field(1, x);
+    const T nO = fma(u, field(2, x), w * field(3, x));
+    vU0[x] = (double)fma(u, field(4, x), w * field(5, x));
+    const T nT = fma(u, field(7, x), w * field(8, x));
+    vW0[x] = (double)(w * field(6, x));
+    P0[x] = mk2<T>(nT, nO);
+  }
+  cl.sync();
+  if (c != 0) return;
+  // x-means: thread t adds x = t, t + 256, ... from 0, then the tree of k_rows
+  double nU = 0.0, wt = 0.0;
+  for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
+    nU += vU[x];
+    wt += vW[x];
+  }
+  const double sU = block_sum(nU, red);
+  const double sW = block_sum(wt, red);
+  const V* C = fft_smem<T>(P, P2, Mx, 1, -1, tws);
+  const T inv = (T)1 / (T)Mx;
+  const T half = (T)0.5 * inv;
+  const size_t qs = (size_t)g.Mz * nm * 2;
+  T* q0 = Q + (size_t)b * 2 * qs + (size_t)j * nm * 2;
+  T* q1 = q0 + qs;
+  for (int m = threadIdx.x; m < nm; m += blockDim.x) {
+    const V cm = C[m];
+    const V cn = conj2(C[m == 0 ? 0 : Mx - m]);
+    const V s2 = cm + cn, d = cm - cn;
+    stc<T>(q0 + 2 * m, mk2<T>(half * s2.x, half * s2.y));
+    if (m == 0)
+      stc<T>(q1, mk2<T>((T)(sU / Mx), (T)0));
+    else
+      stc<T>(q1 + 2 * m, mk2<T>(half * d.y, -half * d.x));
+  }
+  if (threadIdx.x == 0) wT[(size_t)b * g.Mz + j] = sW / Mx;
 }
 
 // ---------------------------------------------------------------------------
@@ -533,7 +668,7 @@ __global__ void k_zfwd(Grid g, const T* __restrict__ W, const T* __restrict__ Q,
 static int zfwd_tile(const Grid& g, int B, size_t es) {
   const int Mh = (g.Mz + 1) / 2;
   int tm = 32;
-  while (tm > 4 && (size_t)B * 2 * ((g.nm + tm - 1) / tm) < 2 * 152) tm >>= 1;
+  while (tm > 1 && (size_t)B * 2 * ((g.nm + tm - 1) / tm) < 2 * 152) tm >>= 1;
   while (tm > 4 && (size_t)2 * Mh * tm * 2 * es > 200 * 1024) tm >>= 1;
   return tm;
 }
@@ -917,11 +1052,20 @@ __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, dou
   solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, B, stage, tms, ra, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
+// Modes per k_solve block.  Every column's arithmetic is independent of the
+// tiling, so a small batch (a coarse sweep) takes single-mode tiles and spreads
+// over the SMs instead of leaving most of them idle.
 static int solve_tile(const Grid& g, int B) {
-  int tms = (B * 2 * ((g.nm + 15) / 16) >= 152) ? 16 : 8;
-  if (tms > g.nm) tms = g.nm < 8 ? g.nm : 8;
-  while (tms > 2 && (size_t)5 * g.nq * 2 * tms * 8 > 200 * 1024) tms >>= 1;
+  int tms = 16;
+  while (tms > 1 && (long)B * 2 * ((g.nm + tms - 1) / tms) < 2L * 152) tms >>= 1;
+  if (tms > g.nm) tms = g.nm;
+  while (tms > 1 && (size_t)5 * g.nq * 2 * tms * 8 > 200 * 1024) tms >>= 1;
   return tms;
+}
+// threads of a k_solve block: one per (row, column) of the tile, whole warps, at most 256
+static int solve_threads(const Grid& g, int tms) {
+  const int items = g.nq * 2 * tms;
+  return std::min(256, std::max(32, (items + 31) / 32 * 32));
 }
 static size_t solve_smem(const Grid& g, int B) { return (size_t)5 * g.nq * 2 * solve_tile(g, B) * 8; }
 
@@ -1015,7 +1159,12 @@ static cudaError_t allow_smem(F* fn, int need, int& allowed) {
 cudaError_t configure_kernels(const Grid& g) {
   static int a_rows_d = 48 * 1024, a_rows_f = 48 * 1024, a_solve = 48 * 1024;
   static int a_zfwd_d = 48 * 1024, a_zfwd_f = 48 * 1024;
+  static int a_rcl_d = 48 * 1024, a_rcl_f = 48 * 1024;
   cudaError_t e = allow_smem(k_rows<double>, (int)rows_smem_for(g, 8), a_rows_d);
+  if (e == cudaSuccess && rows_cl_bytes(g, 8) <= 200 * 1024)
+    e = allow_smem(k_rows_cl<double>, (int)rows_cl_bytes(g, 8), a_rcl_d);
+  if (e == cudaSuccess && rows_cl_bytes(g, 4) <= 200 * 1024)
+    e = allow_smem(k_rows_cl<float>, (int)rows_cl_bytes(g, 4), a_rcl_f);
   if (e == cudaSuccess) e = allow_smem(k_rows<float>, (int)rows_smem_for(g, 4), a_rows_f);
   if (e == cudaSuccess)
     e = allow_smem(k_solve, (int)std::max(solve_smem(g, 1), solve_smem(g, 1 << 20)), a_solve);
@@ -1042,8 +1191,12 @@ static void launch_transforms_in(const Grid& g, const Tables& t, const T* Bz, co
   if (pf) pf->end(RBC_KERNEL_ZINV, s, zinv_flops(g, B), zinv_bytes(g, B, sizeof(T)));
   const size_t es = sizeof(T);
   if (pf) pf->begin(RBC_KERNEL_ROWS, s);
-  k_rows<T><<<(unsigned)(B * g.Mz), 256, rows_smem_for(g, es), s>>>(g, tw, Z, Q, w.wT, B, rows_batched(g, es) ? 1 : 0,
-                                                                     ns, w.step);
+  if (rows_use_cluster(g, B, es))
+    k_rows_cl<T><<<(unsigned)(B * g.Mz * kRowsCluster), kRowsThreads, rows_cl_bytes(g, es), s>>>(g, tw, Z, Q, w.wT,
+                                                                                               B, ns, w.step);
+  else
+    k_rows<T><<<(unsigned)(B * g.Mz), kRowsThreads, rows_smem_for(g, es), s>>>(
+        g, tw, Z, Q, w.wT, B, rows_batched(g, es) ? 1 : 0, ns, w.step);
   if (pf) pf->end(RBC_KERNEL_ROWS, s, rows_flops(g, B), rows_bytes(g, B, sizeof(T)));
 }
 
@@ -1085,8 +1238,8 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   const int tms = solve_tile(g, B);
   const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
-  k_solve<<<(unsigned)(B * 2 * mtiles), 256, solve_smem(g, B), s>>>(g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags,
-                                                                    B, stage, tms, w.ra, w.nsteps, w.step);
+  k_solve<<<(unsigned)(B * 2 * mtiles), solve_threads(g, tms), solve_smem(g, B), s>>>(
+      g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags, B, stage, tms, w.ra, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);
   return cudaGetLastError();

@@ -118,6 +118,27 @@ def test_batched_uneven_steps_equal_solo_runs_and_oracle(rbc):
     assert torch.equal(st[1].cpu(), torch.from_numpy(to_abi(Xs[1])))   # 0 steps: untouched
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_small_and_large_batch_kernel_shapes_give_identical_bits(rbc, precision):
+    """A batch of 160 states takes the large-batch launch shapes (one row kernel
+    block per row, 16-mode solve tiles, 32-mode z-forward tiles); one state
+    alone takes the small-batch shapes (a cluster of five CTAs per row,
+    single-mode tiles).  The arithmetic is the same, so are the bits."""
+    Nx, Nz, B, steps = 32, 16, 160, 3
+    F = rbc.Propagator(2e4, 1.0, 2.0, Nx, Nz, 2e-4, precision)
+    st = F.new_states(B)
+    for b in range(B):
+        F.set_state(st[b], initial_temperature(Nx, Nz, seed=100 + b, amplitude=0.3))
+    solo = [st[b:b + 1].clone() for b in (0, 77, 159)]
+    nu = torch.zeros(B, dtype=torch.float64, device="cuda")
+    F.step_batch(st, steps, nu)
+    for s1, b in zip(solo, (0, 77, 159)):
+        nu1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F.step_batch(s1, steps, nu1)
+        assert torch.equal(s1[0], st[b]), b
+        assert torch.equal(nu1[0], nu[b]), b
+
+
 def test_nusselt_and_l2_match_oracle(rbc):
     o = RBC(2e5, 1.0, 2.0, 32, 24, 1e-3)
     X = developed_state(o, seed=7, amp=0.5, steps=4)
@@ -240,7 +261,8 @@ def test_parareal_stopping_criteria(rbc):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_parareal_schedule_does_not_change_results(rbc, precision):
     """The overlap of the coarse, fine and correction sweeps (fine groups of
-    1, 2, 4 or all slices) changes timing only: iterates, defects and Nu agree
+    1, 2, 4 or all slices, growing groups, one or two fine streams, coarse
+    priority on or off) changes timing only: iterates, defects and Nu agree
     bit for bit; after nslices iterations U is the serial fine solution."""
     Ra, Nf, Zf, Nc, Zc, dtf, dtc = 3e4, 32, 16, 16, 8, 2e-3, 4e-3
     N, nf = 6, 8
@@ -250,9 +272,9 @@ def test_parareal_schedule_does_not_change_results(rbc, precision):
     u0 = F.new_states(1)
     F.set_state(u0[0], initial_temperature(Nf, Zf, seed=2, amplitude=0.3))
     out = []
-    for group in (N, 1, 2, 4):
+    for sched in ((N, N, 1, 0), (1, 1, 1, 0), (2, 2, 2, 1), (4, 1, 2, 0), (4, 2, 1, 1)):
         P = rbc.Parareal(F, G, 0.0, T, N)
-        P.set_group(group)
+        P.set_schedule(*sched)
         U = F.new_states(N + 1)
         st, k, d, nus = P.iterate(u0[0], U, 3)
         assert st == rbc.RBC_OK and k == 3
@@ -271,8 +293,9 @@ def test_parareal_schedule_does_not_change_results(rbc, precision):
     for n in range(1, N + 1):
         F.step_batch(ser, nf)
         assert torch.equal(ser[0], U[n]), n
-    with pytest.raises(rbc.RBCError):
-        P.set_group(0)
+    for bad in ((0, 1, 1, 0), (2, 3, 1, 0), (2, 1, 3, 0), (2, 1, 1, 2)):
+        with pytest.raises(rbc.RBCError):
+            P.set_schedule(*bad)
 
 
 @pytest.mark.parametrize("Nx,Nz,Ra", [(64, 32, 1e5), (32, 18, 2e5), (256, 64, 1e6)])
