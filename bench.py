@@ -174,7 +174,7 @@ def run_gb300(args, w):
     P = rbc.Parareal(F, G, 0.0, dv["t_end"], N)
     group = args.group if args.group else -(-N // 4)
     first = args.first_group if args.first_group else -(-group // 4)
-    P.set_schedule(group, first, args.fine_streams, args.coarse_priority)
+    P.set_schedule(group, first, args.fine_streams, args.coarse_priority, args.coarse_sms)
     stream = torch.cuda.current_stream()
     U0 = F.new_states(1)
     Th = initial_temperature(w["Nx"], w["Nz"], seed=w["seed"] + rank, Lx=w["Lx"])
@@ -286,7 +286,7 @@ def run_gb300(args, w):
                                 dt=w["dt"], dt_coarse=dv["dtc"], t_end=dv["t_end"], dof_per_slice=dv["dof"],
                                 step="one Parareal iteration (coarse sweep, batched fine sweep, correction, norms)",
                                 fine_group=group, first_fine_group=first, fine_streams=args.fine_streams,
-                                coarse_priority=args.coarse_priority,
+                                coarse_priority=args.coarse_priority, coarse_sms=P.coarse_sms,
                                 schedule="coarse sweep, fine groups and correction sweep overlapped on 3 streams",
                                 l2="flushed between timed steps (256 MB write)",
                                 parallelism=f"{world} independent problems" if world > 1 else "single GPU"),
@@ -480,8 +480,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(SERVING))
     ap.add_argument("--group", type=int, default=0, help="largest fine group (default: a quarter of the slices)")
     ap.add_argument("--first-group", type=int, default=0, help="first fine group (default: a quarter of --group)")
-    ap.add_argument("--fine-streams", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--fine-streams", type=int, default=2, choices=[1, 2, 3, 4])
     ap.add_argument("--coarse-priority", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--coarse-sms", type=int, default=0, help="SMs of the coarse sweeps' own partition (0: shared)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
     args = ap.parse_args()

@@ -203,12 +203,25 @@ rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_i
  *                sweep U^0 has finished;
  *  first_group:  size of the first fine group (1 <= first_group <= group);
  *                sizes then double up to group (default ceil(group / 4));
- *  fine_streams: 1 or 2 streams (and fine handles) the groups alternate over
+ *  fine_streams: 1 to 4 streams (and fine handles) the groups alternate over
  *                (default 2);
  *  coarse_priority: 1 runs both coarse sweeps on high-priority streams
- *                (default 1).
+ *                (default 1);
+ *  coarse_sms:   0 (default) shares all SMs; n > 0 gives the two coarse
+ *                sweeps a partition of about n SMs of their own (a green
+ *                context; rounded up to the device's partition granularity)
+ *                and the fine groups the other SMs, so that the latency-bound
+ *                coarse kernels never wait for SMs held by fine batches.
+ *                While parareal_iterate runs, the fine and coarse handles
+ *                capture their step graphs in these partitions; they are
+ *                released on return.  RBC_ECUDA if the driver cannot
+ *                partition the device (the schedule is then unchanged).
  * RBC_EINVAL outside these ranges.                                          */
-rbc_status parareal_set_schedule(parareal_t p, int group, int first_group, int fine_streams, int coarse_priority);
+rbc_status parareal_set_schedule(parareal_t p, int group, int first_group, int fine_streams, int coarse_priority,
+                                 int coarse_sms);
+
+/* SMs of the coarse partition in use (0: none), -1 for a NULL handle.      */
+int parareal_coarse_sms(parareal_t p);
 
 /* ---- Instrumentation (outside the paper's method) ----
  * Kernel kinds of one RK443 stage: z-inverse transform, row kernel (x-FFTs and

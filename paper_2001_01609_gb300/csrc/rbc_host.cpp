@@ -13,6 +13,8 @@
 
 #include "rbc_internal.h"
 
+#include <cuda.h>   // driver types of SM partitions; the functions are resolved at run time
+
 using namespace rbc;
 
 namespace {
@@ -228,6 +230,66 @@ double ul_residual(const Mat& A, const UL& f, unsigned seed) {
 // ---------------------------------------------------------------------------
 // Handle.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// SM partitions (green contexts).  The driver entry points are looked up at run
+// time, so the library does not link libcuda and loads without a driver.
+// ---------------------------------------------------------------------------
+struct DriverApi {
+  CUresult (*get_resource)(CUdevice, CUdevResource*, CUdevResourceType) = nullptr;
+  CUresult (*split)(CUdevResource*, unsigned*, const CUdevResource*, CUdevResource*, unsigned, unsigned) = nullptr;
+  CUresult (*make_desc)(CUdevResourceDesc*, CUdevResource*, unsigned) = nullptr;
+  CUresult (*green_create)(CUgreenCtx*, CUdevResourceDesc, CUdevice, unsigned) = nullptr;
+  CUresult (*green_destroy)(CUgreenCtx) = nullptr;
+  CUresult (*from_green)(CUcontext*, CUgreenCtx) = nullptr;
+  CUresult (*ctx_get)(CUcontext*) = nullptr;
+  CUresult (*ctx_set)(CUcontext) = nullptr;
+  bool ok = false;
+};
+
+static const DriverApi& driver_api() {
+  static const DriverApi api = [] {
+    DriverApi a;
+    auto get = [](const char* name, void** fn) {
+      cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+      return cudaGetDriverEntryPointByVersion(name, fn, 13000, cudaEnableDefault, &q) == cudaSuccess &&
+             q == cudaDriverEntryPointSuccess && *fn != nullptr;
+    };
+    a.ok = get("cuDeviceGetDevResource", reinterpret_cast<void**>(&a.get_resource)) &&
+           get("cuDevSmResourceSplitByCount", reinterpret_cast<void**>(&a.split)) &&
+           get("cuDevResourceGenerateDesc", reinterpret_cast<void**>(&a.make_desc)) &&
+           get("cuGreenCtxCreate", reinterpret_cast<void**>(&a.green_create)) &&
+           get("cuGreenCtxDestroy", reinterpret_cast<void**>(&a.green_destroy)) &&
+           get("cuCtxFromGreenCtx", reinterpret_cast<void**>(&a.from_green)) &&
+           get("cuCtxGetCurrent", reinterpret_cast<void**>(&a.ctx_get)) &&
+           get("cuCtxSetCurrent", reinterpret_cast<void**>(&a.ctx_set));
+    return a;
+  }();
+  return api;
+}
+
+// Makes `ctx` (a partition's context) current for the scope; nullptr keeps
+// the current (primary) context.  ok() is false if the switch failed.
+class CtxScope {
+ public:
+  explicit CtxScope(CUcontext ctx) {
+    if (!ctx) return;
+    const DriverApi& d = driver_api();
+    if (!d.ok || d.ctx_get(&prev_) != CUDA_SUCCESS || d.ctx_set(ctx) != CUDA_SUCCESS) {
+      failed_ = true;
+      return;
+    }
+    switched_ = true;
+  }
+  ~CtxScope() {
+    if (switched_) driver_api().ctx_set(prev_);
+  }
+  bool ok() const { return !failed_; }
+
+ private:
+  CUcontext prev_ = nullptr;
+  bool switched_ = false, failed_ = false;
+};
+
 struct rbc_s {
   Grid g{};
   rbc_opts opts{};
@@ -262,12 +324,21 @@ struct rbc_s {
     const void* X = nullptr;
     const void* nu = nullptr;
     int B = -1;
+    CUcontext ctx = nullptr;   // the SM partition it was captured in (nullptr: whole GPU)
     unsigned long long used = 0;
   };
   static constexpr int kGraphCache = 8;
   StepGraph graphs[kGraphCache];
   unsigned long long graph_clock = 0;
-  cudaStream_t cap_stream = nullptr;
+  // Step graphs are captured in `bind_ctx` (set by a Parareal schedule that
+  // confines this handle to an SM partition), on a capture stream of that context.
+  CUcontext bind_ctx = nullptr;
+  struct CapStream {
+    CUcontext ctx = nullptr;
+    cudaStream_t s = nullptr;
+  };
+  static constexpr int kCapStreams = 4;
+  CapStream caps[kCapStreams];
   bool use_graphs = true;
 };
 
@@ -292,8 +363,8 @@ struct pr_s {
   int first_group = 0;        // first fine group
   int fine_streams = 1;       // fine groups alternate over this many streams
   int coarse_priority = 0;    // 1: the coarse sweeps run on high-priority streams
-  static constexpr int kFineStreams = 2;
-  rbc_t fines[kFineStreams] = {};          // fines[0] = fine; the others are copies of it
+  static constexpr int kFineStreams = 4;
+  rbc_t fines[kFineStreams] = {};          // fines[0] = fine; the others are copies of it, made on demand
   cudaStream_t sF[kFineStreams] = {};      // default priority
   cudaStream_t sG0 = nullptr, sG = nullptr;        // coarse sweeps, default priority
   cudaStream_t sG0_hi = nullptr, sG_hi = nullptr;  // the same, high priority
@@ -301,7 +372,79 @@ struct pr_s {
   std::vector<cudaEvent_t> ev_f;    // [N] fine group j done
   cudaEvent_t ev_begin = nullptr, ev_copy = nullptr, ev_gdone = nullptr, ev_g0done = nullptr;
   cudaEvent_t ev_fdone[kFineStreams] = {};
+  // Optional SM partition: the coarse sweeps on `coarse_sms` SMs of their own
+  // (green context 0), the fine groups on the rest (green context 1), so the
+  // latency-bound coarse kernels never wait for SMs held by fine batches.
+  int coarse_sms = 0;
+  CUgreenCtx green[2] = {};
+  CUcontext gctx[2] = {};
+  cudaStream_t pG0 = nullptr, pG = nullptr;   // in gctx[0]
+  cudaStream_t pF[kFineStreams] = {};         // in gctx[1]
 };
+
+static void release_context(rbc_t h, CUcontext ctx);
+
+// Remove the SM partition of a Parareal handle: its streams, the step graphs
+// its handles captured in it, and the green contexts.
+static void drop_partition(pr_s* p) {
+  if (!p->gctx[0]) return;
+  for (cudaStream_t* st : {&p->pG0, &p->pG, &p->pF[0], &p->pF[1], &p->pF[2], &p->pF[3]})
+    if (*st) {
+      cudaStreamSynchronize(*st);
+      cudaStreamDestroy(*st);
+      *st = nullptr;
+    }
+  for (int i = 0; i < 2; ++i) {
+    for (rbc_t h : {p->coarse, p->coarse2}) release_context(h, p->gctx[i]);
+    for (rbc_t h : p->fines) release_context(h, p->gctx[i]);
+    if (p->green[i]) driver_api().green_destroy(p->green[i]);
+    p->green[i] = nullptr;
+    p->gctx[i] = nullptr;
+  }
+  p->coarse_sms = 0;
+}
+
+static rbc_status make_partition(pr_s* p, int coarse_sms) {
+  const DriverApi& d = driver_api();
+  if (!d.ok) return fail(RBC_ECUDA, "SM partitions (green contexts) are not available");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CUdevResource all{}, grp{}, rest{};
+  unsigned n = 1;
+  if (d.get_resource((CUdevice)dev, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS ||
+      d.split(&grp, &n, &all, &rest, 0, (unsigned)coarse_sms) != CUDA_SUCCESS || n != 1 || rest.sm.smCount == 0)
+    return fail(RBC_ECUDA, "cannot split %d SMs off the device", coarse_sms);
+  CUdevResourceDesc desc[2];
+  if (d.make_desc(&desc[0], &grp, 1) != CUDA_SUCCESS || d.make_desc(&desc[1], &rest, 1) != CUDA_SUCCESS)
+    return fail(RBC_ECUDA, "SM partition descriptors");
+  for (int i = 0; i < 2; ++i)
+    if (d.green_create(&p->green[i], desc[i], (CUdevice)dev, CU_GREEN_CTX_DEFAULT_STREAM) != CUDA_SUCCESS ||
+        d.from_green(&p->gctx[i], p->green[i]) != CUDA_SUCCESS) {
+      drop_partition(p);
+      return fail(RBC_ECUDA, "green context creation");
+    }
+  bool ok = true;
+  {
+    CtxScope scope(p->gctx[0]);
+    int lo = 0, hi = 0;
+    ok = scope.ok() && cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&p->pG0, cudaStreamNonBlocking, hi) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&p->pG, cudaStreamNonBlocking, hi) == cudaSuccess;
+  }
+  if (ok) {
+    CtxScope scope(p->gctx[1]);
+    ok = scope.ok();
+    for (int i = 0; ok && i < pr_s::kFineStreams; ++i)
+      ok = cudaStreamCreateWithFlags(&p->pF[i], cudaStreamNonBlocking) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    drop_partition(p);
+    return fail(RBC_ECUDA, "streams of the SM partition");
+  }
+  p->coarse_sms = (int)grp.sm.smCount;
+  return RBC_OK;
+}
 
 extern "C" const char* rbc_last_error(void) { return g_err; }
 
@@ -622,7 +765,8 @@ extern "C" void rbc_destroy(rbc_t h) {
   for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
   for (auto& sg : h->graphs)
     if (sg.exec) cudaGraphExecDestroy(sg.exec);
-  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (auto& c : h->caps)
+    if (c.s) cudaStreamDestroy(c.s);
   for (int i = 0; i < rbc_s::kPinSlots; ++i) {
     if (h->pin_busy[i]) cudaEventSynchronize(h->pin_ev[i]);
     if (h->pin_ev[i]) cudaEventDestroy(h->pin_ev[i]);
@@ -755,11 +899,46 @@ extern "C" rbc_status rbc_get_state(rbc_t h, const void* d_state, double* h_T, d
 // The step loop of this (states, B, nu) binding: a while node whose body is
 // one RK443 step captured on the handle's own stream, ended by the counter
 // kernel once step == maxs.  Cached per binding.
+// Drop the step graphs and the capture stream a handle holds in `ctx`.
+static void release_context(rbc_t h, CUcontext ctx) {
+  if (!h || !ctx) return;
+  for (auto& sg : h->graphs)
+    if (sg.exec && sg.ctx == ctx) {
+      cudaGraphExecDestroy(sg.exec);
+      sg = rbc_s::StepGraph{};
+    }
+  for (auto& c : h->caps)
+    if (c.s && c.ctx == ctx) {
+      cudaStreamSynchronize(c.s);
+      cudaStreamDestroy(c.s);
+      c = rbc_s::CapStream{};
+    }
+  if (h->bind_ctx == ctx) h->bind_ctx = nullptr;
+}
+
+static rbc_status capture_stream(rbc_t h, cudaStream_t* out) {
+  rbc_s::CapStream* free_slot = nullptr;
+  for (auto& c : h->caps) {
+    if (c.s && c.ctx == h->bind_ctx) {
+      *out = c.s;
+      return RBC_OK;
+    }
+    if (!c.s && !free_slot) free_slot = &c;
+  }
+  if (!free_slot) return fail(RBC_ECUDA, "no free capture stream slot");
+  CtxScope scope(h->bind_ctx);
+  if (!scope.ok()) return fail(RBC_ECUDA, "cannot enter the SM partition's context");
+  CK(cudaStreamCreateWithFlags(&free_slot->s, cudaStreamNonBlocking));
+  free_slot->ctx = h->bind_ctx;
+  *out = free_slot->s;
+  return RBC_OK;
+}
+
 static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExec_t* out) {
   ++h->graph_clock;
   rbc_s::StepGraph* victim = &h->graphs[0];
   for (auto& sg : h->graphs) {
-    if (sg.exec && sg.X == X && sg.B == B && sg.nu == nu) {
+    if (sg.exec && sg.X == X && sg.B == B && sg.nu == nu && sg.ctx == h->bind_ctx) {
       sg.used = h->graph_clock;
       *out = sg.exec;
       return RBC_OK;
@@ -768,7 +947,13 @@ static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExe
   }
   if (victim->exec) cudaGraphExecDestroy(victim->exec);
   *victim = rbc_s::StepGraph{};
-  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cap = nullptr;
+  rbc_status cs = capture_stream(h, &cap);
+  if (cs != RBC_OK) return cs;
+  // the graph, its loop handle and the captured kernels belong to the
+  // handle's SM partition when it is bound to one
+  CtxScope scope(h->bind_ctx);
+  if (!scope.ok()) return fail(RBC_ECUDA, "cannot enter the SM partition's context");
   cudaGraph_t gr = nullptr;
   CK(cudaGraphCreate(&gr, 0));
   cudaGraphConditionalHandle loop;
@@ -786,13 +971,13 @@ static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExe
   }
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   const unsigned long long before = launches_so_far();
-  e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage)
-      e = launch_stage(h->g, h->t, h->w, X, B, stage, nu, h->cap_stream);
-    if (e == cudaSuccess) e = launch_advance_loop(h->w, loop, h->cap_stream);
+      e = launch_stage(h->g, h->t, h->w, X, B, stage, nu, cap);
+    if (e == cudaSuccess) e = launch_advance_loop(h->w, loop, cap);
     cudaGraph_t captured = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &captured);
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) {
@@ -813,6 +998,7 @@ static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExe
   victim->X = X;
   victim->B = B;
   victim->nu = nu;
+  victim->ctx = h->bind_ctx;
   victim->used = h->graph_clock;
   *out = victim->exec;
   return RBC_OK;
@@ -1019,13 +1205,16 @@ static bool whole_steps(double len, double dt, int* n) {
 
 extern "C" void parareal_destroy(parareal_t p) {
   if (!p) return;
-  for (cudaStream_t st : {p->sF[0], p->sF[1], p->sG0, p->sG, p->sG0_hi, p->sG_hi})
+  drop_partition(p);
+  for (cudaStream_t st : {p->sF[0], p->sF[1], p->sF[2], p->sF[3], p->sG0, p->sG, p->sG0_hi, p->sG_hi})
     if (st) cudaStreamSynchronize(st);
   for (cudaEvent_t e : p->ev_g0) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_f) cudaEventDestroy(e);
-  for (cudaEvent_t e : {p->ev_begin, p->ev_copy, p->ev_gdone, p->ev_g0done, p->ev_fdone[0], p->ev_fdone[1]})
+  for (cudaEvent_t e : {p->ev_begin, p->ev_copy, p->ev_gdone, p->ev_g0done})
     if (e) cudaEventDestroy(e);
-  for (cudaStream_t st : {p->sF[0], p->sF[1], p->sG0, p->sG, p->sG0_hi, p->sG_hi})
+  for (cudaEvent_t e : p->ev_fdone)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t st : {p->sF[0], p->sF[1], p->sF[2], p->sF[3], p->sG0, p->sG, p->sG0_hi, p->sG_hi})
     if (st) cudaStreamDestroy(st);
   for (int i = 1; i < pr_s::kFineStreams; ++i) rbc_destroy(p->fines[i]);
   rbc_destroy(p->coarse2);
@@ -1037,6 +1226,22 @@ extern "C" void parareal_destroy(parareal_t p) {
   cudaFree(p->d_I);
   cudaFree(p->d_norm);
   delete p;
+}
+
+// Fine handles 1 .. n-1 (copies of the caller's fine handle, for concurrent fine groups).
+static rbc_status ensure_fines(pr_s* p, int n) {
+  const Grid& gf = p->fine->g;
+  for (int i = 1; i < n; ++i) {
+    if (p->fines[i]) continue;
+    rbc_status s = rbc_create(gf.Ra, gf.Pr, gf.Lx, gf.Nx, gf.Nz, gf.dt, &p->fine->opts, &p->fines[i]);
+    if (s == RBC_OK) s = rbc_reserve(p->fines[i], p->N);
+    if (s != RBC_OK) {
+      rbc_destroy(p->fines[i]);
+      p->fines[i] = nullptr;
+      return s;
+    }
+  }
+  return RBC_OK;
 }
 
 extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, double t1, int nslices, int criterion,
@@ -1080,10 +1285,7 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
     s = rbc_create(gc.Ra, gc.Pr, gc.Lx, gc.Nx, gc.Nz, gc.dt, &coarse->opts, &p->coarse2);
   if (s == RBC_OK) s = rbc_reserve(p->coarse2, 1);
   p->fines[0] = fine;
-  for (int i = 1; s == RBC_OK && i < pr_s::kFineStreams; ++i) {
-    s = rbc_create(gf.Ra, gf.Pr, gf.Lx, gf.Nx, gf.Nz, gf.dt, &fine->opts, &p->fines[i]);
-    if (s == RBC_OK) s = rbc_reserve(p->fines[i], N);
-  }
+  if (s == RBC_OK) s = ensure_fines(p, 2);
   if (s != RBC_OK) {
     parareal_destroy(p);
     return s;
@@ -1121,16 +1323,27 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
 }
 
 extern "C" rbc_status parareal_set_schedule(parareal_t p, int group, int first_group, int fine_streams,
-                                            int coarse_priority) {
+                                            int coarse_priority, int coarse_sms) {
   if (!p || group < 1 || first_group < 1 || first_group > group || fine_streams < 1 ||
-      fine_streams > pr_s::kFineStreams || coarse_priority < 0 || coarse_priority > 1)
+      fine_streams > pr_s::kFineStreams || coarse_priority < 0 || coarse_priority > 1 || coarse_sms < 0)
     return fail(RBC_EINVAL, "bad schedule");
+  rbc_status fs = ensure_fines(p, fine_streams);
+  if (fs != RBC_OK) return fs;
+  if (coarse_sms != p->coarse_sms) {
+    drop_partition(p);
+    if (coarse_sms > 0) {
+      rbc_status st = make_partition(p, coarse_sms);
+      if (st != RBC_OK) return st;
+    }
+  }
   p->group = std::min(group, p->N);
   p->first_group = std::min(first_group, p->group);
   p->fine_streams = fine_streams;
   p->coarse_priority = coarse_priority;
   return RBC_OK;
 }
+
+extern "C" int parareal_coarse_sms(parareal_t p) { return p ? p->coarse_sms : -1; }
 
 // Fine groups of an iteration: slices n >= n0 cut into groups whose sizes
 // start at first_group and double up to `group`: a small first group lets the
@@ -1154,17 +1367,17 @@ static std::vector<int> fine_group_starts(const pr_s* p, int n0) {
 // `wait_for(a, cnt)` (an event of the stream that writes its inputs); group j
 // records ev_f[j], and slice_group[n] receives the group of slice n.
 template <class WaitFor>
-static rbc_status fine_groups(parareal_t p, int n0, const std::vector<int>& nfv, std::vector<int>& slice_group,
-                              WaitFor wait_for) {
+static rbc_status fine_groups(parareal_t p, const cudaStream_t* sF, int n0, const std::vector<int>& nfv,
+                              std::vector<int>& slice_group, WaitFor wait_for) {
   const size_t Sf = state_doubles(p->fine->g);
   const std::vector<int> a = fine_group_starts(p, n0);
   for (int j = 0; j + 1 < (int)a.size(); ++j) {
     const int cnt = a[j + 1] - a[j];
     const int i = j % p->fine_streams;
-    CK(cudaStreamWaitEvent(p->sF[i], wait_for(a[j], cnt), 0));
-    rbc_status s = rbc_step_batch(p->fines[i], p->d_F + (size_t)a[j] * Sf, cnt, nfv.data(), p->d_I + a[j], p->sF[i]);
+    CK(cudaStreamWaitEvent(sF[i], wait_for(a[j], cnt), 0));
+    rbc_status s = rbc_step_batch(p->fines[i], p->d_F + (size_t)a[j] * Sf, cnt, nfv.data(), p->d_I + a[j], sF[i]);
     if (s != RBC_OK) return s;
-    CK(cudaEventRecord(p->ev_f[j], p->sF[i]));
+    CK(cudaEventRecord(p->ev_f[j], sF[i]));
     for (int n = a[j]; n < a[j + 1]; ++n) slice_group[n] = j;
   }
   return RBC_OK;
@@ -1184,10 +1397,27 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
   CK(cudaMemcpyAsync(U, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
   CK(cudaMemcpyAsync(p->d_Uold, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
   CK(cudaMemcpyAsync(p->d_F, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
-  cudaStream_t s0 = p->coarse_priority ? p->sG0_hi : p->sG0;
-  cudaStream_t sg = p->coarse_priority ? p->sG_hi : p->sG;
+  const bool part = p->gctx[0] != nullptr;
+  cudaStream_t s0 = part ? p->pG0 : p->coarse_priority ? p->sG0_hi : p->sG0;
+  cudaStream_t sg = part ? p->pG : p->coarse_priority ? p->sG_hi : p->sG;
+  cudaStream_t sF[pr_s::kFineStreams];
+  for (int i = 0; i < pr_s::kFineStreams; ++i) sF[i] = part ? p->pF[i] : p->sF[i];
+  // with an SM partition the handles capture their step graphs in it; the
+  // caller's handles are unbound again on every return
+  struct Bind {
+    pr_s* p;
+    Bind(pr_s* q, bool part) : p(q) {
+      for (rbc_t h : {p->coarse, p->coarse2}) h->bind_ctx = part ? p->gctx[0] : nullptr;
+      for (rbc_t h : p->fines)
+        if (h) h->bind_ctx = part ? p->gctx[1] : nullptr;
+    }
+    ~Bind() {
+      for (rbc_t h : {p->fine, p->coarse}) h->bind_ctx = nullptr;
+    }
+  } bind(p, part);
   CK(cudaEventRecord(p->ev_begin, stream));   // the side streams start after the caller's work and these copies
-  for (cudaStream_t st : {p->sF[0], p->sF[1], s0, sg}) CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
+  for (cudaStream_t st : sF) CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
+  for (cudaStream_t st : {s0, sg}) CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
   // k = 0: serial coarse sweep U_{n+1}^0 = G(U_n^0), on s0.  The coarse chain
   // carries its own state (restricting the prolonged state gives it back
   // exactly), so nothing here reads U while the correction sweep rewrites it.
@@ -1214,7 +1444,7 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
     rbc_status s;
     if (k == 1) {
       // group inputs U_a .. U_{a+cnt-1} come from the U^0 sweep, up to its step a+cnt-2
-      s = fine_groups(p, 0, nfv, slice_group,
+      s = fine_groups(p, sF, 0, nfv, slice_group,
                       [&](int a, int cnt) { return a + cnt >= 2 ? p->ev_g0[a + cnt - 2] : p->ev_begin; });
     } else {
       // U^{k-1} is final: keep it for the defect and as the fine inputs
@@ -1222,7 +1452,7 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
       CK(cudaMemcpyAsync(p->d_F + n0 * Sf, U + n0 * Sf, (size_t)(N - n0) * Bf, cudaMemcpyDeviceToDevice, stream));
       CK(cudaEventRecord(p->ev_copy, stream));
       CK(cudaStreamWaitEvent(sg, p->ev_copy, 0));
-      s = fine_groups(p, n0, nfv, slice_group, [&](int, int) { return p->ev_copy; });
+      s = fine_groups(p, sF, n0, nfv, slice_group, [&](int, int) { return p->ev_copy; });
     }
     if (s != RBC_OK) return s;
     // serial correction sweep on sG
@@ -1244,7 +1474,7 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
     CK(cudaEventRecord(p->ev_gdone, sg));
     CK(cudaStreamWaitEvent(stream, p->ev_gdone, 0));
     for (int i = 0; i < pr_s::kFineStreams; ++i) {
-      CK(cudaEventRecord(p->ev_fdone[i], p->sF[i]));
+      CK(cudaEventRecord(p->ev_fdone[i], sF[i]));
       CK(cudaStreamWaitEvent(stream, p->ev_fdone[i], 0));
     }
     // Defect_k = max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k||  (L2 of T); a non-finite

@@ -21,7 +21,7 @@ EXPORTS = [
     "rbc_reserve", "rbc_set_state", "rbc_get_state", "rbc_step_batch", "rbc_check_diverged", "rbc_nusselt",
     "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate", "rbc_profile",
     "rbc_profile_read", "rbc_launch_count", "rbc_nusselt_static", "rbc_step_batch_ra", "rbc_restrict",
-    "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff", "parareal_set_schedule",
+    "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff", "parareal_set_schedule", "parareal_coarse_sms",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -74,7 +74,8 @@ def load():
         "rbc_prolong": (I, [P, P, P, P, I, P]),
         "rbc_parareal_correct": (I, [P, P, P, P, P, P, I, P]),
         "rbc_l2_diff": (I, [P, P, P, I, P, P]),
-        "parareal_set_schedule": (I, [P, I, I, I, I]),
+        "parareal_set_schedule": (I, [P, I, I, I, I, I]),
+        "parareal_coarse_sms": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -254,15 +255,19 @@ class Parareal:
         except Exception:
             pass
 
-    def set_schedule(self, group, first_group=None, fine_streams=1, coarse_priority=0):
-        """Fine group sizes, fine streams and coarse-stream priority of the overlapped
-        schedule (timing only)."""
+    def set_schedule(self, group, first_group=None, fine_streams=2, coarse_priority=1, coarse_sms=0):
+        """Fine group sizes, fine streams, coarse-stream priority and an optional SM
+        partition for the coarse sweeps, of the overlapped schedule (timing only)."""
         fg = group if first_group is None else first_group
-        _check(load().parareal_set_schedule(self.h, group, fg, fine_streams, coarse_priority))
+        _check(load().parareal_set_schedule(self.h, group, fg, fine_streams, coarse_priority, coarse_sms))
+
+    @property
+    def coarse_sms(self):
+        return load().parareal_coarse_sms(self.h)
 
     def set_group(self, group):
-        """Equal fine groups of `group` slices on one stream."""
-        self.set_schedule(group)
+        """Equal fine groups of `group` slices on one stream, no partition."""
+        self.set_schedule(group, group, 1, 0, 0)
 
     def iterate(self, U0, U, max_iters, stream=None):
         """Returns (status, k_done, defects[k], nus[k]); U (nslices+1 states) receives U^k."""

@@ -272,9 +272,11 @@ def test_parareal_schedule_does_not_change_results(rbc, precision):
     u0 = F.new_states(1)
     F.set_state(u0[0], initial_temperature(Nf, Zf, seed=2, amplitude=0.3))
     out = []
-    for sched in ((N, N, 1, 0), (1, 1, 1, 0), (2, 2, 2, 1), (4, 1, 2, 0), (4, 2, 1, 1)):
+    for sched in ((N, N, 1, 0, 0), (1, 1, 1, 0, 0), (2, 2, 2, 1, 0), (4, 1, 2, 0, 0), (4, 2, 1, 1, 0),
+                  (2, 1, 2, 1, 40)):
         P = rbc.Parareal(F, G, 0.0, T, N)
         P.set_schedule(*sched)
+        assert (P.coarse_sms > 0) == (sched[4] > 0)
         U = F.new_states(N + 1)
         st, k, d, nus = P.iterate(u0[0], U, 3)
         assert st == rbc.RBC_OK and k == 3
@@ -293,7 +295,7 @@ def test_parareal_schedule_does_not_change_results(rbc, precision):
     for n in range(1, N + 1):
         F.step_batch(ser, nf)
         assert torch.equal(ser[0], U[n]), n
-    for bad in ((0, 1, 1, 0), (2, 3, 1, 0), (2, 1, 3, 0), (2, 1, 1, 2)):
+    for bad in ((0, 1, 1, 0, 0), (2, 3, 1, 0, 0), (2, 1, 3, 0, 0), (2, 1, 1, 2, 0), (2, 1, 1, 0, -1)):
         with pytest.raises(rbc.RBCError):
             P.set_schedule(*bad)
 
