@@ -105,51 +105,45 @@ template <typename T> __device__ __forceinline__ C2<T> cvt2(double2 a) { return 
 //   m = 0: omega = -U'),  d_x u,  d_z u,  T,  d_x T,  d_z T.
 // Output Z[b][field][j][m] (complex, real type T), fields in that order.
 // ---------------------------------------------------------------------------
+// Field f (0..8, as listed above) of one output point from the operator sums
+// P[q] = d^q psi / ds^q (q < 4), t0 = T, t1 = dT/ds.  The roundings are written
+// out (explicit fma), so every kernel that forms a field gets the same bits.
+template <typename T>
+__device__ __forceinline__ C2<T> zinv_field(int f, int m, T k, const C2<T>* P, C2<T> t0, C2<T> t1) {
+  using V = C2<T>;
+  const T zero = 0;
+  const V z = mk2<T>(zero, zero);
+  switch (f) {
+    case 0: return m == 0 ? mk2<T>(P[0].x, zero) : (T)2 * P[1];                 // u (m = 0: U)
+    case 1: return m == 0 ? z : -k * times_i(P[0]);                             // w = -ik psi
+    case 2: {                                                                   // d_x omega
+      if (m == 0) return z;
+      const T kk = k * k;                                                       // omega = k^2 psi - 4 d2(psi)
+      const V om = mk2<T>(fma(kk, P[0].x, (T)-4 * P[2].x), fma(kk, P[0].y, (T)-4 * P[2].y));
+      return k * times_i(om);
+    }
+    case 3: {                                                                   // d_z omega
+      if (m == 0) return mk2<T>((T)-4 * P[2].x, zero);
+      const T kk2 = ((T)2 * k) * k;                                             // 2 k^2 d(psi) - 8 d3(psi)
+      return mk2<T>(fma(kk2, P[1].x, (T)-8 * P[3].x), fma(kk2, P[1].y, (T)-8 * P[3].y));
+    }
+    case 4: return m == 0 ? z : k * times_i((T)2 * P[1]);                       // d_x u
+    case 5: return m == 0 ? mk2<T>((T)2 * P[1].x, zero) : (T)4 * P[2];          // d_z u
+    case 6: return t0;                                                          // T
+    case 7: return m == 0 ? z : k * times_i(t0);                                // d_x T
+    case 8: return (T)2 * t1;                                                   // d_z T
+    default: return z;
+  }
+}
+
 // Fields of one output row (j, m); half = 0: fields 0-3, 1: fields 4-8, -1: all.
 template <typename T>
 __device__ __forceinline__ void zinv_store(const Grid& g, T* Zb, int j, int m, T k, const C2<T>* P, C2<T> t0,
                                            C2<T> t1, int half) {
-  using V = C2<T>;
-  const T zero = 0;
   const size_t fs = (size_t)g.Mz * g.nm * 2;
   T* zb = Zb + ((size_t)j * g.nm + m) * 2;
-  if (half <= 0) {
-    V u, w, dxo, dzo;
-    if (m == 0) {
-      u = mk2<T>(P[0].x, zero);
-      w = mk2<T>(zero, zero);
-      dxo = mk2<T>(zero, zero);
-      dzo = mk2<T>((T)-4 * P[2].x, zero);
-    } else {
-      u = (T)2 * P[1];
-      w = -k * times_i(P[0]);                          // -ik psi
-      const V om = (k * k) * P[0] - (T)4 * P[2];       // omega = -(4 psi'' - k^2 psi)
-      dxo = k * times_i(om);
-      dzo = ((T)2 * k * k) * P[1] - (T)8 * P[3];       // -(8 psi''' - 2 k^2 psi')
-    }
-    stc<T>(zb + 0 * fs, u);
-    stc<T>(zb + 1 * fs, w);
-    stc<T>(zb + 2 * fs, dxo);
-    stc<T>(zb + 3 * fs, dzo);
-  }
-  if (half != 0) {
-    V dxu, dzu, dxT;
-    if (m == 0) {
-      dxu = mk2<T>(zero, zero);
-      dzu = mk2<T>((T)2 * P[1].x, zero);
-      dxT = mk2<T>(zero, zero);
-    } else {
-      const V u = (T)2 * P[1];
-      dxu = k * times_i(u);
-      dzu = (T)4 * P[2];
-      dxT = k * times_i(t0);
-    }
-    stc<T>(zb + 4 * fs, dxu);
-    stc<T>(zb + 5 * fs, dzu);
-    stc<T>(zb + 6 * fs, t0);
-    stc<T>(zb + 7 * fs, dxT);
-    stc<T>(zb + 8 * fs, (T)2 * t1);
-  }
+  const int f0 = half == 1 ? 4 : 0, f1 = half == 0 ? 4 : 9;
+  for (int f = f0; f < f1; ++f) stc<T>(zb + f * fs, zinv_field<T>(f, m, k, P, t0, t1));
 }
 
 template <typename T>
@@ -353,14 +347,23 @@ static size_t rows_smem_for(const Grid& g, size_t es) {
 }
 size_t rows_smem_bytes(const Grid& g) { return rows_smem_for(g, 8); }
 
-// Deterministic block sum (fixed tree over blockDim.x threads, blockDim a power of two).
+// Deterministic block sum: the fixed tree red[t] += red[t + s], s = blockDim/2
+// down to 1 (blockDim a power of two, at least 32).  Levels s >= 32 go through
+// shared memory, the last five through warp shuffles with the same pairings.
 __device__ double block_sum(double v, double* red) {
   red[threadIdx.x] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+  for (int s = blockDim.x / 2; s >= 32; s >>= 1) {
     if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
+  if (threadIdx.x < 32) {
+    double x = red[threadIdx.x];
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
+    if (threadIdx.x == 0) red[0] = x;
+  }
+  __syncthreads();
   const double r = red[0];
   __syncthreads();
   return r;

@@ -295,7 +295,7 @@ def test_parareal_schedule_does_not_change_results(rbc, precision):
     for n in range(1, N + 1):
         F.step_batch(ser, nf)
         assert torch.equal(ser[0], U[n]), n
-    for bad in ((0, 1, 1, 0, 0), (2, 3, 1, 0, 0), (2, 1, 3, 0, 0), (2, 1, 1, 2, 0), (2, 1, 1, 0, -1)):
+    for bad in ((0, 1, 1, 0, 0), (2, 3, 1, 0, 0), (2, 1, 5, 0, 0), (2, 1, 1, 2, 0), (2, 1, 1, 0, -1)):
         with pytest.raises(rbc.RBCError):
             P.set_schedule(*bad)
 
