@@ -450,16 +450,35 @@ NCU_CASES = {
     # name: (Ra, Nx, Nz, dt, B) -- one RK443 step without graphs, for ncu captures
     "fine_b32": (1e6, 256, 64, 1.25e-5, 32),
     "coarse_b1": (1e6, 128, 32, 1.5625e-5, 1),
+    "parareal_small": None,   # one Parareal iteration, see run_ncu_case
 }
 
 
 def run_ncu_case(name):
-    """One plain (graph-free) RK443 step of a batch: a small, self-ending case for ncu."""
+    """A small, self-ending case for ncu: one plain (graph-free) RK443 step of a
+    batch, or one short Parareal iteration on the bench's grids."""
     import torch
     from paper_2001_01609_gb300 import build
     build.build()
     from paper_2001_01609_gb300 import rbc
     from paper_2001_01609_gb300.inputs import initial_temperature
+    if name == "parareal_small":
+        # config-1 grids and time steps, 8 slices of 25 fine / 20 coarse steps
+        # (the coarse-to-fine step ratio of the bench workload); every kernel
+        # launched from the host, so that a profiler sees each one
+        w = WORKLOADS[DEFAULT]
+        N, nf, nc = 8, 25, 20
+        F = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"], eager=True)
+        G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], nf * w["dt"] / nc, eager=True)
+        P = rbc.Parareal(F, G, 0.0, N * nf * w["dt"], N)
+        u0 = F.new_states(1)
+        F.set_state(u0[0], initial_temperature(w["Nx"], w["Nz"], seed=w["seed"], Lx=w["Lx"]))
+        U = F.new_states(N + 1)
+        st, k, _, _ = P.iterate(u0[0], U, 1)
+        torch.cuda.synchronize()
+        assert st == rbc.RBC_OK and k == 1
+        print(f"ncu case {name} ok")
+        return
     Ra, Nx, Nz, dt, B = NCU_CASES[name]
     F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt)
     st = F.new_states(B)

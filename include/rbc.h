@@ -65,6 +65,10 @@ typedef struct {
                       products in FP32, solves, RK combination, Parareal update
                       and norms in FP64.                                        */
   int bc;          /* RBC_FIXED_T only                                          */
+  int eager;       /* 0: rbc_step_batch runs its steps as one graph launch (a
+                      device-side loop); 1: every kernel is launched from the
+                      host, so per-kernel profilers see each launch (slower).
+                      Same results either way.                               */
 } rbc_opts;
 
 /* Text of the last error seen by this thread (static storage, never NULL). */

@@ -718,8 +718,9 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
     return fail(RBC_EINVAL, "need even Nx in [4, 1024] and even Nz in [8, 512]");
   if (!(dt > 0) || !(Pr > 0) || !(Lx > 0) || !(Ra >= 0) || !std::isfinite(Ra) || !std::isfinite(dt))
     return fail(RBC_EINVAL, "need dt > 0, Pr > 0, Lx > 0, Ra >= 0");
-  rbc_opts o{RBC_FP64, RBC_FIXED_T};
+  rbc_opts o{RBC_FP64, RBC_FIXED_T, 0};
   if (opts) o = *opts;
+  if (o.eager != 0 && o.eager != 1) return fail(RBC_EINVAL, "eager must be 0 or 1");
   if (o.precision != RBC_FP64 && o.precision != RBC_MIXED)
     return fail(RBC_EINVAL, "precision mode %d not available", o.precision);
   if (o.bc != RBC_FIXED_T) return fail(RBC_EINVAL, "boundary condition %d not available", o.bc);
@@ -729,6 +730,7 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   rbc_t h = new (std::nothrow) rbc_s();
   if (!h) return fail(RBC_ENOMEM, "host allocation");
   h->opts = o;
+  h->use_graphs = (o.eager == 0);
   cudaGetDevice(&h->device);
   Grid& g = h->g;
   g.Nx = Nx;

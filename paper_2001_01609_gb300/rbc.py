@@ -33,7 +33,7 @@ class RBCError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("bc", ctypes.c_int)]
+    _fields_ = [("precision", ctypes.c_int), ("bc", ctypes.c_int), ("eager", ctypes.c_int)]
 
 
 _lib = None
@@ -108,12 +108,12 @@ def _dptr(a):
 class Propagator:
     """F (or G) of Eq. 20 on one grid: rbc_create(Ra, Pr, Lx, Nx, Nz, dt)."""
 
-    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, precision=RBC_FP64):
+    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, precision=RBC_FP64, eager=False):
         lib = load()
         self.Ra, self.Pr, self.Lx, self.Nx, self.Nz, self.dt = Ra, Pr, Lx, Nx, Nz, dt
         self.precision = precision
         h = ctypes.c_void_p()
-        opts = _Opts(precision, 0)
+        opts = _Opts(precision, 0, 1 if eager else 0)
         _check(lib.rbc_create(Ra, Pr, Lx, Nx, Nz, dt, ctypes.byref(opts), ctypes.byref(h)))
         self.h = h
 

@@ -139,6 +139,28 @@ def test_small_and_large_batch_kernel_shapes_give_identical_bits(rbc, precision)
         assert torch.equal(nu1[0], nu[b]), b
 
 
+def test_eager_launches_equal_graph_loop(rbc):
+    """rbc_opts.eager (every kernel launched from the host) gives the bits of
+    the device-side step loop, alone and inside Parareal."""
+    Ra, Nf, Zf, Nc, Zc, dtf, dtc = 3e4, 32, 16, 16, 8, 2e-3, 4e-3
+    N, nf = 4, 6
+    out = []
+    for eager in (False, True):
+        F = rbc.Propagator(Ra, 1.0, 2.0, Nf, Zf, dtf, eager=eager)
+        G = rbc.Propagator(Ra, 1.0, 2.0, Nc, Zc, dtc, eager=eager)
+        u0 = F.new_states(1)
+        F.set_state(u0[0], initial_temperature(Nf, Zf, seed=9, amplitude=0.3))
+        st = u0.clone()
+        F.step_batch(st, 7)
+        U = F.new_states(N + 1)
+        s, k, d, nus = rbc.Parareal(F, G, 0.0, N * nf * dtf, N).iterate(u0[0], U, 2)
+        assert s == rbc.RBC_OK and k == 2
+        out.append((st, U, d, nus))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    np.testing.assert_array_equal(out[0][3], out[1][3])
+
+
 def test_nusselt_and_l2_match_oracle(rbc):
     o = RBC(2e5, 1.0, 2.0, 32, 24, 1e-3)
     X = developed_state(o, seed=7, amp=0.5, steps=4)
