@@ -131,6 +131,28 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------
+# DRAM bytes (read + write) per launch of the stage kernels, from one ncu
+# capture of a single RK443 step (the stage-kernel summary in profiles/),
+# valid only while the kernel sources are those that were captured.
+NCU_TRAFFIC_SOURCES = ("paper_2001_01609_gb300/csrc/rbc_kernels.cu", "paper_2001_01609_gb300/csrc/rbc_internal.h")
+NCU_TRAFFIC_SHA256 = "d59e0224428dd5531224d65c63db9019969927a986df749dcf72d0da1d842efb"
+NCU_TRAFFIC = {
+    "coarse:k_zinv": 128256, "coarse:k_rows": 493056, "coarse:k_zfwd": 117760, "coarse:k_solve": 805120,
+    "fine:k_zinv": 8526336 + 2475264, "fine:k_rows": 56695552 + 432128, "fine:k_zfwd": 12618752,
+    "fine:k_solve": 17935104 + 61696,
+}
+
+
+def ncu_traffic(kernel):
+    """Captured DRAM bytes per launch of `kernel`, or None if the sources changed since."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in NCU_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return NCU_TRAFFIC.get(kernel) if h.hexdigest() == NCU_TRAFFIC_SHA256 else None
+
+
 def fine_group_starts(N, group, first, n0=0):
     """First slice of each fine group of parareal_iterate's schedule (and N)."""
     a = [n0]
@@ -270,8 +292,10 @@ def run_gb300(args, w):
     peak_fp64 = 152 * 4 * 2070e6 / 1e12
     achieved = pk["flops_per"] / (pk["per_ms"] / 1e3) / 1e12
     total_ms = sum(v["ms"] for v in kern.values())
+    # the fine kernels are captured at 32 slices; a sampled fine group of another size has no figure
+    traffic = ncu_traffic(dom) if (dom.startswith("coarse:") or kern[dom].get("sampled_batch") == 32) else None
     roofline = dict(bound="alu", achieved=achieved, peak=peak_fp64, unit="TFLOP/s", frac=achieved / peak_fp64,
-                    traffic=None, kernel=dom, peak_source="derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz",
+                    traffic=traffic, traffic_source="ncu, one RK443 step, cold cache (profiles/)", kernel=dom, peak_source="derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz",
                     launch_us=1e3 * pk["per_ms"], flops_per_launch=pk["flops_per"],
                     algorithmic_bytes_per_launch=pk["bytes_per"],
                     kernel_share={k: v["ms"] / total_ms for k, v in kern.items()},
