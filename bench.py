@@ -153,6 +153,21 @@ def ncu_traffic(kernel):
     return NCU_TRAFFIC.get(kernel) if h.hexdigest() == NCU_TRAFFIC_SHA256 else None
 
 
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of per-rank totals over all ranks (the slowest rank times the job)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(work_per_rank, world, seconds):
+    """Work of all ranks (each rank runs its own problem of the same size) per second."""
+    return world * work_per_rank / seconds
+
+
 def fine_group_starts(N, group, first, n0=0):
     """First slice of each fine group of parareal_iterate's schedule (and N)."""
     a = [n0]
@@ -253,13 +268,10 @@ def run_gb300(args, w):
     gpu_launches = rbc.launch_count() - launches0
     if world > 1:
         dist.barrier()
-    tot = torch.tensor([sum(times), sum(e2e_times)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    t_total, e2e_total = tot[0].item(), tot[1].item()
+    t_total, e2e_total = max_over_ranks([sum(times), sum(e2e_times)], world, "cuda")
     fine_dof_steps = N * w["steps_per_slice"] * dv["dof"]
-    value = world * fine_dof_steps * args.steps / t_total
-    e2e_value = world * fine_dof_steps * args.steps / e2e_total
+    value = whole_job_rate(fine_dof_steps * args.steps, world, t_total)
+    e2e_value = whole_job_rate(fine_dof_steps * args.steps, world, e2e_total)
 
     # Per-kernel time over the timed steps, from the samples (8 steps each of
     # one coarse call and one fine group): mean time per launch times the

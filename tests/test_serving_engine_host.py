@@ -157,3 +157,27 @@ def test_deadline_stops_a_loop_that_cannot_progress():
     r = initial(eng, requests(1)[0])
     with pytest.raises(RuntimeError, match="deadline"):
         eng.run([r], deadline=0.5)
+
+
+class _Diverging(fake.FakePropagator):
+    """Steps that turn a state non-finite when its Ra is above a threshold."""
+
+    def one_step(self, X, ra):
+        Y = super().one_step(X, ra)
+        return Y * float("inf") if ra > 4e4 else Y
+
+
+def test_a_diverging_request_is_reported_and_the_others_finish():
+    lib = type("lib", (), dict(Propagator=_Diverging, restrict=fake.restrict, prolong=fake.prolong,
+                               parareal_correct=fake.parareal_correct, l2_diff=fake.l2_diff))
+    eng = engine(lib=lib)
+    reqs = [initial(eng, r) for r in requests(5, seed=11)]
+    reqs[2].Ra = 5e4
+    eng.run(reqs, deadline=60)
+    assert reqs[2].status == rbc.RBC_EDIVERGED and reqs[2].k_done == 0
+    base = engine()
+    ok = [initial(base, r) for r in requests(5, seed=11)]
+    del ok[2]
+    base.run(ok, deadline=60)
+    for a, b in zip([r for i, r in enumerate(reqs) if i != 2], ok):
+        assert b.status == rbc.RBC_OK and torch.equal(a.U, b.U)
