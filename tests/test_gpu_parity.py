@@ -75,6 +75,20 @@ def test_few_steps_match_oracle(rbc, Nx, Nz, Ra):
     assert abs(nu.item() - integ) < 1e-11 * abs(integ)
 
 
+@pytest.mark.parametrize("Nx,Nz,Ra,dt,steps", [(64, 128, 1e6, 2e-6, 2), (16, 256, 1e7, 2e-7, 2)])
+def test_long_chebyshev_expansions_match_oracle(rbc, Nx, Nz, Ra, dt, steps):
+    """Nz = 128 and 256: the band recurrences of the stage solve run over 64 and
+    128 unknowns per parity, at wavenumbers up to pi (Nx/2 - 1)."""
+    o = RBC(Ra, 1.0, 2.0, Nx, Nz, dt)
+    X0 = developed_state(o, seed=Nz + 1, amp=0.3, steps=1)
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt)
+    st = F.new_states(1)
+    put(st, 0, X0)
+    F.step_batch(st, steps)
+    ref, _ = o.run(X0, steps)
+    assert max_rel_diff(get(st, 0), ref) < 1e-10
+
+
 def test_config0_single_slice_parity_over_1000_steps(rbc):
     """Ra = 1e4, 64 x 32, dt = 1e-3, seeded IC (seed 0): one slice of t in [0, 1]."""
     o = RBC(1e4, 1.0, 2.0, 64, 32, 1e-3)
