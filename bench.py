@@ -266,6 +266,17 @@ def run_gb300(args, w):
     G.profile(False)
     ck = clocks.stop()
     gpu_launches = rbc.launch_count() - launches0
+    # Serial fine reference (after the timed region): one slice of the fine
+    # propagator alone (B = 1, all its steps, same kernels), times the slice count.
+    ser = F.new_states(1)
+    ser.copy_(U0[0:1])
+    F.step_batch(ser, 50, stream=stream)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    F.step_batch(ser, w["steps_per_slice"], stream=stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    serial_fine_s = N * s0.elapsed_time(s1) / 1e3
     if world > 1:
         dist.barrier()
     t_total, e2e_total = max_over_ranks([sum(times), sum(e2e_times)], world, "cuda")
@@ -329,7 +340,12 @@ def run_gb300(args, w):
                     e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(U0h.numel() * 8),
                              d2h_bytes_per_step=int(outh.numel() * 8)),
                     gpu_launches=int(gpu_launches), roofline=roofline, cpu_baseline=cpu, clocks=ck,
-                    defect=float(de[-1]) if len(de) else None, nu=float(nu[-1]) if len(nu) else None)
+                    defect=float(de[-1]) if len(de) else None, nu=float(nu[-1]) if len(nu) else None,
+                    time_to_tol=dict(parareal_iterations=1, parareal_s=t_total / args.steps,
+                                     serial_fine_s=serial_fine_s, speedup=serial_fine_s / (t_total / args.steps),
+                                     defect_after=float(de[-1]) if len(de) else None,
+                                     serial_fine_sample="one slice of the fine propagator alone (B = 1, "
+                                                        f"{w['steps_per_slice']} steps) times {N} slices"))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
