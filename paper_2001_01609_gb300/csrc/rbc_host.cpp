@@ -670,6 +670,14 @@ static rbc_status upload_tables(rbc_t h) {
     }
     add_floats(ph); add_floats(pl); add_floats(th); add_floats(tl);
   }
+  // tensor-core z-forward images, one pair per Chebyshev parity (mixed precision only)
+  const bool tcw = g.mixed && tc_zfwd_supported(g);
+  for (int p = 0; p < 2; ++p) {
+    std::vector<float> wh(tcw ? tc_zfwd_image_floats(g) : 0), wl(wh.size());
+    if (tcw) tc_zfwd_build_images(g, zfwd.data(), p, wh.data(), wl.data());
+    add_floats(wh);
+    add_floats(wl);
+  }
   CK(cudaMalloc(&h->d_tables, buf.size() * sizeof(double)));
   CK(cudaMemcpy(h->d_tables, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
   const double* b = h->d_tables;
@@ -707,6 +715,12 @@ static rbc_status upload_tables(rbc_t h) {
   ++i;
   T.tcA_T_lo = tc ? reinterpret_cast<const float*>(b + offs[i]) : nullptr;
   ++i;
+  for (int p = 0; p < 2; ++p) {
+    T.tcW_hi[p] = tcw ? reinterpret_cast<const float*>(b + offs[i]) : nullptr;
+    ++i;
+    T.tcW_lo[p] = tcw ? reinterpret_cast<const float*>(b + offs[i]) : nullptr;
+    ++i;
+  }
   return RBC_OK;
 }
 

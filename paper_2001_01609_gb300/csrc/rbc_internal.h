@@ -59,6 +59,9 @@ struct Tables {
   // tensor-core z-inverse operands (RBC_MIXED): TF32 hi/lo images of the
   // interleaved operator rows, pre-swizzled per 128-row tile and 32-wide K-chunk
   const float *tcA_psi_hi, *tcA_psi_lo, *tcA_T_hi, *tcA_T_lo;
+  // tensor-core z-forward operands (RBC_MIXED): TF32 hi/lo images of the rows
+  // of the forward matrix of each Chebyshev parity, per 128-row tile and K-chunk
+  const float *tcW_hi[2], *tcW_lo[2];
 };
 
 // Optional per-kernel CUDA-event timing (host side).  Event pairs come from a
@@ -147,5 +150,12 @@ void tc_zinv_build_images(const Grid& g, const double* zinv, int nops, float* hi
 bool tc_zinv_supported(const Grid& g);
 cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const double* X, int B, const int* ns,
                            cudaStream_t s);
+// tensor-core z forward transform (rbc_tcgen05.cu)
+RBC_HD int tc_zfwd_mtiles(const Grid& g);
+RBC_HD int tc_zfwd_kchunks(const Grid& g);
+size_t tc_zfwd_image_floats(const Grid& g);
+void tc_zfwd_build_images(const Grid& g, const double* zfwd, int p, float* hi, float* lo);
+bool tc_zfwd_supported(const Grid& g);
+cudaError_t launch_zfwd_tc(const Grid& g, const Tables& t, const Work& w, int B, cudaStream_t s);
 
 }  // namespace rbc

@@ -1234,7 +1234,12 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   cudaError_t e = launch_explicit(g, t, w, Xin, B, false, s);
   if (e != cudaSuccess) return e;
   Prof* pf = (w.prof && w.prof->on) ? w.prof : nullptr;
-  if (g.mixed)
+  if (g.mixed && t.tcW_hi[0] != nullptr) {
+    // tensor cores, TF32 with split compensation
+    if (pf) pf->begin(RBC_KERNEL_ZFWD, s);
+    launch_zfwd_tc(g, t, w, B, s);
+    if (pf) pf->end(RBC_KERNEL_ZFWD, s, zfwd_flops(g, B), zfwd_bytes(g, B, 4));
+  } else if (g.mixed)
     launch_zfwd<float>(g, t.zfwd32, w, B, pf, s);
   else
     launch_zfwd<double>(g, t.zfwd, w, B, pf, s);

@@ -178,17 +178,33 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
   unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [buf][hi, lo][128 x 128 B]
   // X tile -> hi/lo TF32 operands, K-major (row = column of the tile, k = n)
+  // (four consecutive columns, two modes, per item: 16-byte loads, several in flight)
   const double* Xb = X + (size_t)b * S;
-  for (int it = tid; it < kc * kChunkK * kTileN; it += blockDim.x) {
-    const int n = it / kTileN, col = it - n * kTileN;
-    const int gc = c0 + col;
-    float x = 0.f;
-    if (n < g.Nz && gc < 2 * g.nm) x = (float)Xb[soff2(g, f, n, gc >> 1) + (gc & 1)];
-    const uint32_t h = to_tf32(x);
-    const uint32_t l = to_tf32(x - __uint_as_float(h));
-    const uint32_t o = (uint32_t)(n / kChunkK) * kTileN * 128 + swz(col, n % kChunkK);
-    *reinterpret_cast<uint32_t*>(sXhi + o) = h;
-    *reinterpret_cast<uint32_t*>(sXlo + o) = l;
+#pragma unroll 4
+  for (int it = tid; it < kc * kChunkK * (kTileN / 4); it += blockDim.x) {
+    const int n = it / (kTileN / 4), col = (it - n * (kTileN / 4)) * 4;
+    const int gc = c0 + col;                  // even: columns gc .. gc+3 are modes gc/2, gc/2 + 1
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (n < g.Nz) {
+      const double* src = Xb + soff2(g, f, n, gc >> 1);
+      if (gc + 3 < 2 * g.nm) {
+        const double2 v0 = *reinterpret_cast<const double2*>(src);
+        const double2 v1 = *reinterpret_cast<const double2*>(src + 2);
+        v[0] = v0.x; v[1] = v0.y; v[2] = v1.x; v[3] = v1.y;
+      } else {
+        for (int e = 0; e < 4; ++e)
+          if (gc + e < 2 * g.nm) v[e] = src[e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float x = (float)v[e];
+      const uint32_t h = to_tf32(x);
+      const uint32_t l = to_tf32(x - __uint_as_float(h));
+      const uint32_t o = (uint32_t)(n / kChunkK) * kTileN * 128 + swz(col + e, n % kChunkK);
+      *reinterpret_cast<uint32_t*>(sXhi + o) = h;
+      *reinterpret_cast<uint32_t*>(sXlo + o) = l;
+    }
   }
   if (tid == 0) {
     for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[i])));
@@ -325,6 +341,221 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core z forward transform for the mixed-precision path.
+//
+// For one slice, one field and one Chebyshev parity p the z-forward transform
+// is F[n][col] = sum_{jh < ceil(Mz/2)} W[n][jh] fold_p[jh][col], n = 2r + p,
+// with fold_0 = Q_j + Q_{Mz-1-j} and fold_1 = Q_j - Q_{Mz-1-j} (the middle row
+// of an odd Mz once in fold_0) and col = (Fourier mode, real/imaginary part).
+// CTA per (slice, field, parity, 64-column tile): the folds are formed in FP32
+// from the row kernel's output, split into hi/lo TF32 operands in shared memory
+// (K-major, 128-byte swizzle); the rows of W of parity p are pre-split images
+// [mtile][kchunk][128 x 32]; three MMAs per 8-wide K step (hi*hi, hi*lo, lo*hi)
+// accumulate in tensor memory; the epilogue writes F in FP64 for the solve.
+// The waits, the drain and the tensor-memory release follow k_zinv_tc.
+// ---------------------------------------------------------------------------
+__host__ __device__ int tc_zfwd_mtiles(const Grid& g) { return (g.Nz / 2 + kTileM - 1) / kTileM; }
+__host__ __device__ int tc_zfwd_kchunks(const Grid& g) { return ((g.Mz + 1) / 2 + kChunkK - 1) / kChunkK; }
+size_t tc_zfwd_image_floats(const Grid& g) { return (size_t)tc_zfwd_mtiles(g) * tc_zfwd_kchunks(g) * kTileM * kChunkK; }
+
+void tc_zfwd_build_images(const Grid& g, const double* zfwd, int p, float* hi, float* lo) {
+  const int mt = tc_zfwd_mtiles(g), kc = tc_zfwd_kchunks(g), Mh = (g.Mz + 1) / 2;
+  for (int t = 0; t < mt; ++t)
+    for (int c = 0; c < kc; ++c) {
+      float* bh = hi + ((size_t)t * kc + c) * kTileM * kChunkK;
+      float* bl = lo + ((size_t)t * kc + c) * kTileM * kChunkK;
+      for (int r = 0; r < kTileM; ++r)
+        for (int k = 0; k < kChunkK; ++k) {
+          const int n = 2 * (t * kTileM + r) + p, jh = c * kChunkK + k;
+          const double v = (n < g.Nz && jh < Mh) ? zfwd[(size_t)n * g.Mz + jh] : 0.0;
+          float f = (float)v;
+          uint32_t u;
+          memcpy(&u, &f, 4);
+          u = (u + 0x1000u) & 0xFFFFE000u;
+          float h;
+          memcpy(&h, &u, 4);
+          float l = (float)(v - (double)h);
+          memcpy(&u, &l, 4);
+          u = (u + 0x1000u) & 0xFFFFE000u;
+          memcpy(&l, &u, 4);
+          const int off = r * 128 + ((((k * 4) >> 4) ^ (r & 7)) << 4) + ((k * 4) & 15);
+          bh[off / 4] = h;
+          bl[off / 4] = l;
+        }
+    }
+}
+
+size_t tc_zfwd_smem_bytes(const Grid& g) {
+  return (size_t)tc_zfwd_kchunks(g) * kTileN * 128 * 2 + 2 * 2 * (size_t)kTileM * 128 + 1024;
+}
+bool tc_zfwd_supported(const Grid& g) { return tc_zfwd_smem_bytes(g) <= 200 * 1024; }
+
+__global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict__ Whi0, const float* __restrict__ Wlo0,
+                                                 const float* __restrict__ Whi1, const float* __restrict__ Wlo1,
+                                                 const float* __restrict__ Q, double* __restrict__ F, size_t S, int B,
+                                                 const int* nsteps, const int* step, int* flags) {
+  extern __shared__ __align__(1024) unsigned char tc_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t mbar[3];   // 0, 1: A-chunk buffers free; 2: accumulator ready
+  __shared__ uint32_t tmem_base;
+  const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
+  const int per_b = 2 * 2 * ntile;
+  const int b = blockIdx.x / per_b;
+  int rem = blockIdx.x - b * per_b;
+  const int f = rem / (2 * ntile);
+  rem -= f * 2 * ntile;
+  const int p = rem / ntile;
+  const int c0 = (rem - p * ntile) * kTileN;
+  if (b >= B || !(nsteps == nullptr || *step < nsteps[b])) return;   // uniform per block
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* Ahi = p == 0 ? Whi0 : Whi1;
+  const float* Alo = p == 0 ? Wlo0 : Wlo1;
+  const int kc = tc_zfwd_kchunks(g), mtiles = tc_zfwd_mtiles(g), Mh = (g.Mz + 1) / 2;
+  unsigned char* sXhi = base;
+  unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
+  unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [buf][hi, lo][128 x 128 B]
+  // folds of parity p -> hi/lo TF32 operands, K-major (row = column of the tile, k = jh)
+  // (four consecutive columns per item: 16-byte loads, several in flight)
+  const float* q = Q + (size_t)(b * 2 + f) * g.Mz * g.nm * 2;
+  const bool vec = (2 * g.nm) % 4 == 0;
+#pragma unroll 4
+  for (int it = tid; it < kc * kChunkK * (kTileN / 4); it += blockDim.x) {
+    const int jh = it / (kTileN / 4), col = (it - jh * (kTileN / 4)) * 4;
+    const int jr = g.Mz - 1 - jh;
+    float a[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    if (jh < Mh) {
+      const float* ra = q + (size_t)jh * g.nm * 2 + c0 + col;
+      const float* rc = q + (size_t)jr * g.nm * 2 + c0 + col;
+      if (vec && c0 + col + 3 < 2 * g.nm) {
+        const float4 va = *reinterpret_cast<const float4*>(ra);
+        a[0] = va.x; a[1] = va.y; a[2] = va.z; a[3] = va.w;
+        if (jr != jh) {
+          const float4 vc = *reinterpret_cast<const float4*>(rc);
+          c[0] = vc.x; c[1] = vc.y; c[2] = vc.z; c[3] = vc.w;
+        }
+      } else {
+        for (int e = 0; e < 4; ++e)
+          if (c0 + col + e < 2 * g.nm) {
+            a[e] = ra[e];
+            if (jr != jh) c[e] = rc[e];
+          }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float x = 0.f;
+      if (jh < Mh && c0 + col + e < 2 * g.nm) x = (jr != jh) ? (p == 0 ? a[e] + c[e] : a[e] - c[e]) : (p == 0 ? a[e] : 0.f);
+      const uint32_t h = to_tf32(x);
+      const uint32_t l = to_tf32(x - __uint_as_float(h));
+      const uint32_t o = (uint32_t)(jh / kChunkK) * kTileN * 128 + swz(col + e, jh % kChunkK);
+      *reinterpret_cast<uint32_t*>(sXhi + o) = h;
+      *reinterpret_cast<uint32_t*>(sXlo + o) = l;
+    }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[i])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
+  uint32_t use[2] = {0, 0};
+  uint32_t issued[2] = {0, 0};
+  uint32_t acc_phase = 0;
+  bool ok = true;
+  double* Fb = F + (size_t)b * S;
+  for (int t = 0; t < mtiles && ok; ++t) {
+    for (int c = 0; c < kc && ok; ++c) {
+      const int gidx = t * kc + c, buf = gidx & 1;
+      if (gidx >= 2) {                        // buffer free once its previous MMAs completed
+        ok = wait_parity(&mbar[buf], use[buf] & 1);
+        use[buf]++;
+        if (!ok) break;
+      }
+      unsigned char* ah = sA + (size_t)buf * 2 * kTileM * 128;
+      unsigned char* al = ah + (size_t)kTileM * 128;
+      const float4* gh = reinterpret_cast<const float4*>(Ahi + (size_t)gidx * kTileM * kChunkK);
+      const float4* gl = reinterpret_cast<const float4*>(Alo + (size_t)gidx * kTileM * kChunkK);
+      for (int i = tid; i < kTileM * kChunkK / 4; i += blockDim.x) {
+        reinterpret_cast<float4*>(ah)[i] = __ldg(gh + i);
+        reinterpret_cast<float4*>(al)[i] = __ldg(gl + i);
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
+        const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
+        for (int ks = 0; ks < kChunkK / 8; ++ks) {
+          const uint32_t o = ks * 32;
+          const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
+          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
+          mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
+        }
+        commit(&mbar[buf]);
+        if (c == kc - 1) commit(&mbar[2]);
+      }
+      issued[buf]++;
+    }
+    if (!ok) break;
+    ok = wait_parity(&mbar[2], acc_phase & 1);
+    acc_phase++;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) break;
+    const int n = 2 * (t * kTileM + warp * 32 + lane) + p;   // tile row = TMEM lane
+    for (int cc = 0; cc < kTileN; cc += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
+      if (n >= g.Nz) continue;
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        const int gc = c0 + cc + i;
+        if (gc >= 2 * g.nm) break;
+        *reinterpret_cast<double2*>(Fb + soff2(g, f, n, gc >> 1)) = make_double2((double)v[i], (double)v[i + 1]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();                          // accumulator read before the next tile overwrites it
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (!ok && tid == 0) flags[b] = 2;          // a bounded wait gave up
+  if (tid == 0) {
+    for (int bb = 0; bb < 2; ++bb)
+      while (use[bb] < issued[bb]) {
+        if (!wait_parity(&mbar[bb], use[bb] & 1)) break;
+        use[bb]++;
+      }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
+cudaError_t launch_zfwd_tc(const Grid& g, const Tables& t, const Work& w, int B, cudaStream_t s) {
+  static int allowed = 48 * 1024;
+  const size_t smem = tc_zfwd_smem_bytes(g);
+  if ((int)smem > allowed) {
+    cudaError_t e = cudaFuncSetAttribute(k_zfwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    allowed = (int)smem;
+  }
+  const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
+  k_zfwd_tc<<<(unsigned)(B * 2 * 2 * ntile), 128, smem, s>>>(g, t.tcW_hi[0], t.tcW_lo[0], t.tcW_hi[1], t.tcW_lo[1],
+                                                             reinterpret_cast<const float*>(w.Q), w.F,
+                                                             state_doubles(g), B, w.nsteps, w.step, w.flags);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const double* X, int B, const int* ns,
