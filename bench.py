@@ -503,6 +503,7 @@ NCU_CASES = {
     "fine_b32": (1e6, 256, 64, 1.25e-5, 32),
     "coarse_b1": (1e6, 128, 32, 1.5625e-5, 1),
     "parareal_small": None,   # one Parareal iteration, see run_ncu_case
+    "mixed_b8": (1e7, 512, 128, 7.8125e-7, 8),   # RBC_MIXED: tensor-core z transforms
 }
 
 
@@ -532,7 +533,8 @@ def run_ncu_case(name):
         print(f"ncu case {name} ok")
         return
     Ra, Nx, Nz, dt, B = NCU_CASES[name]
-    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt)
+    prec = rbc.RBC_MIXED if name.startswith("mixed") else rbc.RBC_FP64
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt, prec)
     st = F.new_states(B)
     for b in range(B):
         F.set_state(st[b], initial_temperature(Nx, Nz, seed=b, amplitude=0.3))
