@@ -75,7 +75,8 @@ def test_few_steps_match_oracle(rbc, Nx, Nz, Ra):
     assert abs(nu.item() - integ) < 1e-11 * abs(integ)
 
 
-@pytest.mark.parametrize("Nx,Nz,Ra,dt,steps", [(64, 128, 1e6, 2e-6, 2), (16, 256, 1e7, 2e-7, 2)])
+@pytest.mark.parametrize("Nx,Nz,Ra,dt,steps", [(64, 128, 1e6, 2e-6, 2), (16, 256, 1e7, 2e-7, 2),
+                                                 (256, 128, 1e8, 1.5625e-7, 2)])
 def test_long_chebyshev_expansions_match_oracle(rbc, Nx, Nz, Ra, dt, steps):
     """Nz = 128 and 256: the band recurrences of the stage solve run over 64 and
     128 unknowns per parity, at wavenumbers up to pi (Nx/2 - 1)."""
