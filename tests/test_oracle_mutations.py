@@ -1,0 +1,112 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each test plants one mistake in the oracle (on the CPU, through monkeypatch)
+and checks that the pin meant to guard against it now fails: a flipped sign,
+a dropped term, a missing factor, a transposed operand, a wrong tableau entry,
+a wrong quadrature weight.  A pin that still passed with the mistake in place
+would not be pinning anything.
+"""
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+import test_oracle_pins as pins
+import test_oracle_tableau as tableau
+from oracle import rbc as orbc
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def test_flipped_buoyancy_sign_fails_the_onset_pin(monkeypatch):
+    orig = orbc.RBC.ops_psi
+
+    def ops_psi(self, k):
+        M, L, Cpl = orig(self, k)
+        return M, L, -Cpl
+    monkeypatch.setattr(orbc.RBC, "ops_psi", ops_psi)
+    with pytest.raises(AssertionError):
+        pins.test_P4_oracle_operators_match_collocation_growth_rate(2500.0)
+
+
+def test_dropped_k2_in_the_temperature_laplacian_fails_the_diffusion_pin(monkeypatch):
+    monkeypatch.setattr(orbc.RBC, "ops_T", lambda self, k: (self.S2, 4.0 * self.D2))
+    with pytest.raises(AssertionError):
+        pins.test_P2_temperature_diffusion_decays_by_the_stability_function()
+
+
+def test_missing_prandtl_in_the_mean_flow_fails_its_decay_pin(monkeypatch):
+    monkeypatch.setattr(orbc.RBC, "ops_U", lambda self: (self.S2, 4.0 * self.D2))
+    with pytest.raises(AssertionError):
+        pins.test_P2_mean_flow_viscous_decay_with_Pr()
+
+
+def test_wrong_slope_boundary_row_fails_the_onset_pin(monkeypatch):
+    orig = orbc.RBC.__init__
+
+    def init(self, *a, **k):
+        orig(self, *a, **k)
+        # the wall-slope row with n instead of n^2 (d T_n / ds at s = 1): a different constraint
+        self.bc_slope_hi = self.bc_slope_hi / np.maximum(1.0, np.arange(self.Nz))
+        self._factor()
+    monkeypatch.setattr(orbc.RBC, "__init__", init)
+    with pytest.raises(AssertionError):
+        pins.test_P4_oracle_operators_match_collocation_growth_rate(2500.0)
+
+
+def test_transposed_advection_operands_fail_the_dealiasing_pin(monkeypatch):
+    orig = orbc.RBC.nonlinear
+
+    def nonlinear(self, X):
+        # u d_x T + w d_z T planted as u d_z T + w d_x T: swap T's two derivatives
+        Xs = orbc.State(X.T.copy(), X.psi, X.U)
+        ik = 1j * self.k[:, None]
+        dzT = X.T @ self.Dz.T
+        # a state whose d/dx is the true d/dz and vice versa is not available in
+        # general; emulate the swap on the product by recomputing with ik and Dz exchanged
+        NT, NO, NU, wT = orig(self, Xs)
+        g = self._spec_to_padded_grid
+        u = X.psi @ self.Dz.T
+        u[0] = X.U
+        w = -ik * X.psi
+        w[0] = 0.0
+        NT = self._padded_grid_to_spec(g(u) * g(dzT) + g(w) * g(ik * X.T))
+        return NT, NO, NU, wT
+    monkeypatch.setattr(orbc.RBC, "nonlinear", nonlinear)
+    with pytest.raises(AssertionError):
+        pins.test_P5_dealiased_products_equal_exact_truncated_convolution()
+
+
+def test_wrong_tableau_entry_fails_the_order_conditions(monkeypatch):
+    AE = [row[:] for row in tableau.AE]
+    AE[2][1], AE[2][0] = AE[2][0], AE[2][1]           # two explicit weights of stage 2 swapped
+    monkeypatch.setattr(tableau, "AE", AE)
+    monkeypatch.setattr(tableau, "bE", AE[4])
+    failures = 0
+    for name in dir(tableau):
+        if name.startswith("test_"):
+            try:
+                getattr(tableau, name)()
+            except AssertionError:
+                failures += 1
+    assert failures >= 1
+
+
+def test_reversed_quadrature_weights_fail_the_nusselt_pin(monkeypatch):
+    orig = orbc.RBC.__init__
+
+    def init(self, *a, **k):
+        orig(self, *a, **k)
+        self.cc_weights = self.cc_weights[::-1] * np.linspace(0.5, 1.5, len(self.cc_weights))
+    monkeypatch.setattr(orbc.RBC, "__init__", init)
+    with pytest.raises(AssertionError):
+        pins.test_nusselt_volume_term_against_brute_force_quadrature()
+
+
+def test_unmutated_oracle_passes_the_same_pins():
+    pins.test_P4_oracle_operators_match_collocation_growth_rate(2500.0)
+    pins.test_P2_temperature_diffusion_decays_by_the_stability_function()
+    pins.test_P2_mean_flow_viscous_decay_with_Pr()
+    pins.test_P5_dealiased_products_equal_exact_truncated_convolution()
+    pins.test_nusselt_volume_term_against_brute_force_quadrature()
+    assert Fr(1, 2) == tableau.AI[1][1]
