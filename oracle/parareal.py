@@ -13,16 +13,20 @@ import numpy as np
 
 
 def parareal(U0, nslices, F, G, max_iters, diff_norm, nu_window=None,
-             criterion="fixed", tol=0.0):
+             criterion="fixed", tol=0.0, summarize=None, change=None):
     """Run Parareal.
 
     F(U) -> (U_end, nu_integral); G(U) -> U_end; states support + and -.
     diff_norm(a, b) -> ||a - b|| / ||a||.  nu_window = (first slice, window
     length) for Nu_k = sum of the Nu_V integrals over those slices / length.
+    With ``summarize``, F returns (U_end, integrals) of any kind and
+    Nu_k = summarize(list of the window slices' integrals) instead.
 
     criterion: "fixed" (max_iters iterations, the paper's Sec. 3.7 practice),
-    "defect" (stop at the first k with Defect_k <= tol) or "nu" (stop at the
-    first k with |Nu_k - Nu_{k-1}| / |Nu_k| <= tol).
+    "defect" (stop at the first k with Defect_k <= tol), "nu" (stop at the
+    first k with |Nu_k - Nu_{k-1}| / |Nu_k| <= tol) or "stat" (stop at the
+    first k with change(Nu_k, Nu_{k-1}) <= tol, for summaries of several
+    statistics; Sec. 5.2).
 
     Returns dict(U=list of U_n^k, k=iterations done, defects=[...], nus=[...],
     F=list of the last F results, serial_coarse=U^0).
@@ -44,7 +48,7 @@ def parareal(U0, nslices, F, G, max_iters, diff_norm, nu_window=None,
             Fres[n], Inu[n] = F(U[n])
         if nu_window is not None:
             n0, length = nu_window
-            nus.append(sum(Inu[n0:]) / length)
+            nus.append(sum(Inu[n0:]) / length if summarize is None else summarize(Inu[n0:]))
         Unew = [U0]
         for n in range(N):
             gnew = G(Unew[n])
@@ -56,6 +60,8 @@ def parareal(U0, nslices, F, G, max_iters, diff_norm, nu_window=None,
         if criterion == "defect" and defects[-1] <= tol:
             break
         if criterion == "nu" and len(nus) >= 2 and abs(nus[-1] - nus[-2]) <= tol * abs(nus[-1]):
+            break
+        if criterion == "stat" and len(nus) >= 2 and change(nus[-1], nus[-2]) <= tol:
             break
     return dict(U=U, k=k_done, defects=defects, nus=nus, F=Fres, serial_coarse=U_coarse)
 

@@ -301,6 +301,46 @@ class RBC:
     def nusselt(self, X):
         return self.nusselt_from(X, self.nonlinear(X)[3])
 
+    def diagnostics(self, X):
+        """Instantaneous averages behind the consistency checks of Sec. 2.2.
+
+        Fields on the padded grid, products there, exact x-means (the 3/2 rule
+        integrates products of the truncated Fourier series exactly), and the
+        Clenshaw-Curtis rule over the padded Lobatto points in z (Lz = 1, so
+        <f>_V = (1/2) sum_j cc_j <f>_x(s_j)):
+
+          KE2 = <u^2 + w^2>_V        (Re from its square root, Sec. 2.2)
+          eps = <u . lap u>_V         (viscous term of the energy balance, Eq. 14)
+          wT  = <w T>_V               (buoyancy production P = Ra <w T>_V, Eq. 14)
+          nu  = (Nu_V, Nu_b, Nu_t)    (Eqs. 9-11)
+          Tm  = <T>_x (Mz,)           at the padded points s_j = cos(pi j/(Mz-1))
+          Tv  = <(T - <T>_x)^2>_x (Mz,)
+
+        lap u = (-d_z omega, d_x omega) with omega = -lap psi.
+        """
+        ik = 1j * self.k[:, None]
+        dz = lambda c: c @ self.Dz.T
+        u = dz(X.psi)
+        u[0] = X.U
+        w = -ik * X.psi
+        w[0] = 0.0
+        om = ik * w - dz(u)
+        g = self._spec_to_padded_grid
+        ug, wg, Tg = g(u), g(w), g(X.T)
+        lap_u, lap_w = -g(dz(om)), g(ik * om)
+        vol = lambda f: 0.5 * np.dot(self.cc_weights, f.mean(axis=1))
+        KE2 = vol(ug * ug + wg * wg)
+        eps = vol(ug * lap_u + wg * lap_w)
+        wT_mean = (wg * Tg).mean(axis=1)
+        Tm = Tg.mean(axis=1)
+        Tv = ((Tg - Tm[:, None]) ** 2).mean(axis=1)
+        return dict(KE2=KE2, eps=eps, wT=0.5 * np.dot(self.cc_weights, wT_mean),
+                    nu=self.nusselt_from(X, wT_mean), Tm=Tm, Tv=Tv)
+
+    def padded_z(self):
+        """z of the padded Lobatto points, z_j = cos(pi j/(Mz-1))/2 (descending)."""
+        return 0.5 * np.cos(np.pi * np.arange(self.Mz) / (self.Mz - 1))
+
     def l2_T(self, X):
         """||T||_{L2(Omega)}: Parseval in x, exact Chebyshev Gram matrix in z."""
         G = us.cheb_gram(self.Nz)

@@ -11,9 +11,11 @@ from fractions import Fraction as Fr
 import numpy as np
 import pytest
 
+import test_oracle_diagnostics as diag
 import test_oracle_pins as pins
 import test_oracle_tableau as tableau
 from oracle import rbc as orbc
+from oracle import statistics as ost
 
 pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
 
@@ -103,10 +105,67 @@ def test_reversed_quadrature_weights_fail_the_nusselt_pin(monkeypatch):
         pins.test_nusselt_volume_term_against_brute_force_quadrature()
 
 
+def _planted_diagnostics(monkeypatch, change):
+    orig = orbc.RBC.diagnostics
+
+    def diagnostics(self, X):
+        d = dict(orig(self, X))
+        change(d)
+        return d
+    monkeypatch.setattr(orbc.RBC, "diagnostics", diagnostics)
+
+
+def test_flipped_viscous_term_fails_the_energy_budget_pin(monkeypatch):
+    def change(d):
+        d["eps"] = -d["eps"]
+    _planted_diagnostics(monkeypatch, change)
+    with pytest.raises(AssertionError):
+        diag.test_D3_kinetic_energy_budget_along_the_dynamics()
+
+
+def test_halved_kinetic_energy_fails_the_energy_budget_pin(monkeypatch):
+    def change(d):
+        d["KE2"] = 0.5 * d["KE2"]                     # (1/2)|u|^2 in place of |u|^2
+    _planted_diagnostics(monkeypatch, change)
+    with pytest.raises(AssertionError):
+        diag.test_D3_kinetic_energy_budget_along_the_dynamics()
+
+
+def test_variance_about_zero_fails_the_brute_force_variance_pin(monkeypatch):
+    def change(d):
+        d["Tv"] = d["Tv"] + d["Tm"] ** 2              # <T^2>_x, the plane mean not removed
+    _planted_diagnostics(monkeypatch, change)
+    with pytest.raises(AssertionError):
+        diag.test_D5_plane_mean_and_variance_by_brute_force()
+
+
+def test_left_endpoint_time_rule_fails_the_trapezoid_pin(monkeypatch):
+    def run_sampled(rbc, X, nsteps, every):
+        prev = ost.sample(rbc, X)
+        acc = {q: 0.0 * v for q, v in prev.items()}
+        s = 0
+        while s < nsteps:
+            c = min(every, nsteps - s)
+            for _ in range(c):
+                X, _ = rbc.step(X)
+            for q in acc:
+                acc[q] = acc[q] + c * rbc.dt * prev[q]
+            prev = ost.sample(rbc, X)
+            s += c
+        acc["T"] = nsteps * rbc.dt
+        return X, acc
+    monkeypatch.setattr(ost, "run_sampled", run_sampled)
+    with pytest.raises(AssertionError):
+        diag.test_D7_trapezoid_integrals_of_pure_diffusion()
+
+
 def test_unmutated_oracle_passes_the_same_pins():
     pins.test_P4_oracle_operators_match_collocation_growth_rate(2500.0)
     pins.test_P2_temperature_diffusion_decays_by_the_stability_function()
     pins.test_P2_mean_flow_viscous_decay_with_Pr()
     pins.test_P5_dealiased_products_equal_exact_truncated_convolution()
     pins.test_nusselt_volume_term_against_brute_force_quadrature()
+    diag.test_D3_kinetic_energy_budget_along_the_dynamics()
+    diag.test_D5_plane_mean_and_variance_by_brute_force()
+    diag.test_D7_trapezoid_integrals_of_pure_diffusion()
     assert Fr(1, 2) == tableau.AI[1][1]
