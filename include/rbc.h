@@ -151,6 +151,27 @@ rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double out[3], cudaS
 /* ||T||_{L2(Omega)} of one device state (exact in x and z), host out.       */
 rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream);
 
+/* rbc_diagnostics: the instantaneous averages behind the consistency checks
+ * of Sec. 2.2, for B contiguous device states, into the device array
+ * d_out[B][rbc_diag_size(h)] (FP64), asynchronously on `stream`.  Per state:
+ *   [0] <u^2 + w^2>_V      (the characteristic speed U is the time mean of its
+ *                           square root; Re = U / Pr)
+ *   [1] <u . lap u>_V       (viscous term of the energy balance, Eq. 14)
+ *   [2] <w T>_V             (buoyancy production P = Ra <w T>_V, Eq. 14)
+ *   [3] Nu_V  [4] Nu_b  [5] Nu_t   (Eqs. 9-11)
+ *   [6, 6 + Mz)           <T>_x at the padded points z_j = cos(pi j/(Mz-1))/2
+ *   [6 + Mz, 6 + 2 Mz)    <(T - <T>_x)^2>_x at the same points (the integrand
+ *                         of T_rms, Eq. 16)
+ * with Mz = 3 Nz / 2 and j ascending (z descending from the top wall).  The
+ * x-means are exact (Parseval over the kept Fourier modes); z-integrals use
+ * the Clenshaw-Curtis rule on the Mz padded Lobatto points (Lz = 1).  The
+ * transforms run in FP64 whatever the handle's precision.  Uses the handle's
+ * workspace and grows it to B states when it is smaller (as rbc_step_batch
+ * does); RBC_EINVAL for a null handle or pointer or B < 0; B = 0 does nothing.
+ * rbc_diag_size returns 6 + 2 Mz (0 for a null handle).                     */
+size_t     rbc_diag_size(rbc_t h);
+rbc_status rbc_diagnostics(rbc_t h, const void* d_states, int B, double* d_out, cudaStream_t stream);
+
 /* Building blocks of Eq. 20 for callers that drive Parareal themselves (the
  * serving engine interleaves many runs).  All act on B contiguous states on
  * `stream`, asynchronously; the coarse grid must be no finer than the fine.

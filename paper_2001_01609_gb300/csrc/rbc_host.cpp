@@ -1196,6 +1196,17 @@ extern "C" rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double ou
   return RBC_OK;
 }
 
+extern "C" size_t rbc_diag_size(rbc_t h) { return h ? (size_t)6 + 2 * (size_t)h->g.Mz : 0; }
+
+extern "C" rbc_status rbc_diagnostics(rbc_t h, const void* d_states, int B, double* d_out, cudaStream_t stream) {
+  if (!h || B < 0 || (B > 0 && (!d_states || !d_out))) return fail(RBC_EINVAL, "null argument or B < 0");
+  if (B == 0) return RBC_OK;
+  rbc_status s = rbc_reserve(h, B);
+  if (s != RBC_OK) return s;
+  CK(launch_diagnostics(h->g, h->t, h->w, static_cast<const double*>(d_states), B, d_out, stream));
+  return RBC_OK;
+}
+
 extern "C" rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream) {
   if (!h || !d_state || !out) return fail(RBC_EINVAL, "null argument");
   rbc_status s = rbc_reserve(h, 1);

@@ -122,6 +122,9 @@ cudaError_t launch_nu_final(const Grid& g, const Tables& t, const Work& w, const
                             double* nu, cudaStream_t s);
 cudaError_t launch_nusselt(const Grid& g, const Tables& t, const Work& w, const double* X, double* out3,
                            cudaStream_t s);
+// Sec. 2.2 averages of B states into out[B][6 + 2 Mz] (layout as rbc_diagnostics)
+cudaError_t launch_diagnostics(const Grid& g, const Tables& t, const Work& w, const double* X, int B, double* out,
+                               cudaStream_t s);
 cudaError_t launch_l2_diff(const Grid& g, const Tables& t, const double* A, const double* Bm, int nst,
                            double* out, cudaStream_t s);
 cudaError_t launch_set_state(const Grid& g, const Tables& t, const double* gT, const double* gu,

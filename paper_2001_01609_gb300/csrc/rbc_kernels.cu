@@ -1316,6 +1316,99 @@ cudaError_t launch_nusselt(const Grid& g, const Tables& t, const Work& w, const 
   return cudaGetLastError();
 }
 
+// Consistency-check averages of Sec. 2.2, pass 1.  Z holds the FP64 z inverse
+// of every state (fields u, w, d_x omega, d_z omega, ..., T, ... at the padded
+// rows).  Block per (state, padded row j): x-means by Parseval over the kept
+// modes (weight 1 for m = 0, 2 otherwise; Re(a conj b) for a pair of fields):
+//   u^2 + w^2,   u.lap u = -u d_z omega + w d_x omega,   w T,
+//   (T - <T>_x)^2 (modes m >= 1),   <T>_x = Re T_0(s_j).
+// rows[b][q][j], q = 0..4 in that order.
+__global__ void __launch_bounds__(128) k_diag_rows(Grid g, const double* __restrict__ Z, double* __restrict__ rows) {
+  __shared__ double red[128];
+  const int b = blockIdx.x / g.Mz, j = blockIdx.x - b * g.Mz;
+  const size_t fs = (size_t)g.Mz * g.nm * 2;
+  const double* zb = Z + (size_t)b * 9 * fs + (size_t)j * g.nm * 2;
+  double ke = 0.0, ep = 0.0, wt = 0.0, tv = 0.0;
+  for (int m = threadIdx.x; m < g.nm; m += blockDim.x) {
+    const double c = m == 0 ? 1.0 : 2.0;
+    const double2 u = ld2(zb + 2 * m), w = ld2(zb + fs + 2 * m);
+    const double2 dxo = ld2(zb + 2 * fs + 2 * m), dzo = ld2(zb + 3 * fs + 2 * m);
+    const double2 t = ld2(zb + 6 * fs + 2 * m);
+    ke += c * (u.x * u.x + u.y * u.y + w.x * w.x + w.y * w.y);
+    ep += c * (w.x * dxo.x + w.y * dxo.y - u.x * dzo.x - u.y * dzo.y);
+    wt += c * (w.x * t.x + w.y * t.y);
+    if (m > 0) tv += 2.0 * (t.x * t.x + t.y * t.y);
+  }
+  ke = block_sum(ke, red);
+  ep = block_sum(ep, red);
+  wt = block_sum(wt, red);
+  tv = block_sum(tv, red);
+  if (threadIdx.x == 0) {
+    double* r = rows + (size_t)b * 5 * g.Mz + j;
+    r[0] = ke;
+    r[g.Mz] = ep;
+    r[2 * g.Mz] = wt;
+    r[3 * g.Mz] = tv;
+    r[4 * g.Mz] = zb[6 * fs];
+  }
+}
+
+// Pass 2, block per state: <f>_V = (1/2) sum_j cc_j <f>_x(s_j) (Lz = 1) for the
+// first three rows, the Nusselt numbers of Eqs. 9-11 (conduction part of Nu_V
+// and the wall slopes from the mean temperature coefficients), the profiles.
+__global__ void __launch_bounds__(128) k_diag_final(Grid g, const double* __restrict__ cc, const double* __restrict__ X,
+                                                    const double* __restrict__ rows, double* __restrict__ out) {
+  __shared__ double red[128];
+  const int b = blockIdx.x;
+  const double* r = rows + (size_t)b * 5 * g.Mz;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int j = threadIdx.x; j < g.Mz; j += blockDim.x) {
+    const double c = cc[j];
+    s0 += c * r[j];
+    s1 += c * r[g.Mz + j];
+    s2 += c * r[2 * g.Mz + j];
+  }
+  s0 = block_sum(s0, red);
+  s1 = block_sum(s1, red);
+  s2 = block_sum(s2, red);
+  double* o = out + (size_t)b * (6 + 2 * g.Mz);
+  if (threadIdx.x == 0) {
+    const double* Xb = X + (size_t)b * state_doubles(g);
+    double cond = 0.0, nb = 0.0, nt = 0.0;
+    for (int n = 0; n < g.Nz; ++n) {
+      const double a = Xb[soff(g, 0, n, 0)];
+      if (n & 1) cond -= 2.0 * a;
+      const double n2 = (double)n * n;
+      nb -= 2.0 * a * ((n & 1) ? n2 : -n2);
+      nt -= 2.0 * a * n2;
+    }
+    o[0] = 0.5 * s0;
+    o[1] = 0.5 * s1;
+    o[2] = 0.5 * s2;
+    o[3] = cond + 0.5 * s2;
+    o[4] = nb;
+    o[5] = nt;
+  }
+  for (int j = threadIdx.x; j < g.Mz; j += blockDim.x) {
+    o[6 + j] = r[4 * g.Mz + j];
+    o[6 + g.Mz + j] = r[3 * g.Mz + j];
+  }
+}
+
+cudaError_t launch_diagnostics(const Grid& g, const Tables& t, const Work& w, const double* X, int B, double* out,
+                               cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const int kp = zinv_warps(g);
+  const unsigned zb = (unsigned)(B * ((g.Mz + 1) / 2) * ((g.nm + 31) / 32));
+  // FP64 z inverse of all states (no step mask), whatever the handle's precision
+  k_zinv<double><<<zb, 32 * kp, kp > 1 ? (size_t)kp * 12 * 32 * 2 * sizeof(double) : 0, s>>>(
+      g, t.zinv, X, state_doubles(g), w.Z, B, nullptr, w.step);
+  k_diag_rows<<<(unsigned)(B * g.Mz), 128, 0, s>>>(g, w.Z, w.Q);
+  k_diag_final<<<(unsigned)B, 128, 0, s>>>(g, t.cc, X, w.Q, out);
+  count(3);
+  return cudaGetLastError();
+}
+
 // ||A_b - B_b||^2 (or ||A_b||^2 when Bm is null) of the temperature field of nst
 // states: Parseval in x (weights 1 for m = 0, 2 otherwise), exact Chebyshev
 // Gram matrix in z, times Lx / 2 (z in [-1/2, 1/2]).  Block per state,

@@ -22,6 +22,7 @@ EXPORTS = [
     "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate", "rbc_profile",
     "rbc_profile_read", "rbc_launch_count", "rbc_nusselt_static", "rbc_step_batch_ra", "rbc_restrict",
     "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff", "parareal_set_schedule", "parareal_coarse_sms",
+    "rbc_diag_size", "rbc_diagnostics",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -76,6 +77,8 @@ def load():
         "rbc_l2_diff": (I, [P, P, P, I, P, P]),
         "parareal_set_schedule": (I, [P, I, I, I, I, I]),
         "parareal_coarse_sms": (I, [P]),
+        "rbc_diag_size": (S, [P]),
+        "rbc_diagnostics": (I, [P, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -194,6 +197,26 @@ class Propagator:
         n = (ctypes.c_longlong * K)()
         _check(load().rbc_profile_read(self.h, _dptr(ms), n, _dptr(fl), _dptr(by)))
         return {KERNEL_NAMES[k]: dict(ms=ms[k], launches=n[k], flops=fl[k], bytes=by[k]) for k in range(K)}
+
+    @property
+    def diag_size(self):
+        """Doubles per state written by diagnostics(): 6 + 2 Mz."""
+        return load().rbc_diag_size(self.h)
+
+    def diagnostics(self, states, out=None, stream=None):
+        """rbc_diagnostics: Sec. 2.2 averages of states (B, *state_shape) into a
+        (B, diag_size) FP64 device tensor, asynchronously on the stream.
+
+        Columns: <u^2+w^2>_V, <u.lap u>_V, <wT>_V, Nu_V, Nu_b, Nu_t, then <T>_x and
+        <(T - <T>_x)^2>_x at the Mz padded points z_j = cos(pi j/(Mz-1))/2.
+        """
+        import torch
+        B = states.shape[0]
+        if out is None:
+            out = torch.empty((B, self.diag_size), dtype=torch.float64, device=states.device)
+        assert out.shape == (B, self.diag_size) and out.dtype == torch.float64 and out.is_contiguous()
+        _check(load().rbc_diagnostics(self.h, _ptr(states), B, _ptr(out), _stream(stream)))
+        return out
 
     def l2_temperature(self, state, stream=None):
         out = np.zeros(1)

@@ -50,6 +50,8 @@ def test_invalid_arguments_are_rejected_without_touching_the_device(lib):
     assert lib.rbc_state_bytes(None) == 0
     assert lib.rbc_step_batch(None, None, 1, None, None, None) == rbc.RBC_EINVAL
     assert lib.parareal_create(None, None, 0.0, 1.0, 4, 0, 0.0, ctypes.byref(h)) == rbc.RBC_EINVAL
+    assert lib.rbc_diagnostics(None, None, 1, None, None) == rbc.RBC_EINVAL
+    assert lib.rbc_diag_size(None) == 0
     assert b"need" in lib.rbc_last_error() or len(lib.rbc_last_error()) > 0
 
 
