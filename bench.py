@@ -209,8 +209,8 @@ def run_gb300(args, w):
     G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dv["dtc"])
     N = w["slices"]
     P = rbc.Parareal(F, G, 0.0, dv["t_end"], N)
-    group = args.group if args.group else -(-N // 4)
-    first = args.first_group if args.first_group else -(-group // 4)
+    group = args.group if args.group else N
+    first = args.first_group if args.first_group else (group if group >= N else -(-group // 4))
     P.set_schedule(group, first, args.fine_streams, args.coarse_priority, args.coarse_sms)
     stream = torch.cuda.current_stream()
     U0 = F.new_states(1)
@@ -277,6 +277,19 @@ def run_gb300(args, w):
     s1.record(stream)
     torch.cuda.synchronize()
     serial_fine_s = N * s0.elapsed_time(s1) / 1e3
+    # Sec. 2.2 diagnostics of all fine states (one rbc_diagnostics call), after the timed region
+    dout = F.diagnostics(U[:N])
+    for _ in range(3):
+        F.diagnostics(U[:N], out=dout)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(10):
+        F.diagnostics(U[:N], out=dout)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    diag_s = d0.elapsed_time(d1) / 1e3 / 10
+    Mz, nm = 3 * w["Nz"] // 2, w["Nx"] // 2
+    diag_flops = N * (24.0 * ((Mz + 1) // 2) * nm * w["Nz"] + 20.0 * Mz * nm)
     if world > 1:
         dist.barrier()
     t_total, e2e_total = max_over_ranks([sum(times), sum(e2e_times)], world, "cuda")
@@ -334,13 +347,20 @@ def run_gb300(args, w):
                                 step="one Parareal iteration (coarse sweep, batched fine sweep, correction, norms)",
                                 fine_group=group, first_fine_group=first, fine_streams=args.fine_streams,
                                 coarse_priority=args.coarse_priority, coarse_sms=P.coarse_sms,
-                                schedule="coarse sweep, fine groups and correction sweep overlapped on 3 streams",
+                                schedule=("serial order: coarse sweep, one batched fine sweep, correction sweep"
+                                          if group >= N else
+                                          "coarse sweep, fine groups and correction sweep overlapped on 3 streams"),
                                 l2="flushed between timed steps (256 MB write)",
                                 parallelism=f"{world} independent problems" if world > 1 else "single GPU"),
                     e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(U0h.numel() * 8),
                              d2h_bytes_per_step=int(outh.numel() * 8)),
                     gpu_launches=int(gpu_launches), roofline=roofline, cpu_baseline=cpu, clocks=ck,
                     defect=float(de[-1]) if len(de) else None, nu=float(nu[-1]) if len(nu) else None,
+                    diagnostics=dict(states=N, us_per_call=1e6 * diag_s, flops_per_call=diag_flops,
+                                     tflops=diag_flops / diag_s / 1e12,
+                                     frac_fp64=diag_flops / diag_s / 1e12 / peak_fp64,
+                                     note="rbc_diagnostics (Sec. 2.2 averages) of all slices' fine states, "
+                                          "FP64 z inverse plus Parseval and Clenshaw-Curtis reductions"),
                     time_to_tol=dict(parareal_iterations=1, parareal_s=t_total / args.steps,
                                      serial_fine_s=serial_fine_s, speedup=serial_fine_s / (t_total / args.steps),
                                      defect_after=float(de[-1]) if len(de) else None,
@@ -551,9 +571,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(SERVING))
-    ap.add_argument("--group", type=int, default=0, help="largest fine group (default: a quarter of the slices)")
-    ap.add_argument("--first-group", type=int, default=0, help="first fine group (default: a quarter of --group)")
-    ap.add_argument("--fine-streams", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--group", type=int, default=0,
+                    help="largest fine group (default: all slices, one fine batch after the coarse sweep)")
+    ap.add_argument("--first-group", type=int, default=0,
+                    help="first fine group (default: --group when it covers all slices, else a quarter of it)")
+    ap.add_argument("--fine-streams", type=int, default=1, choices=[1, 2, 3, 4])
     ap.add_argument("--coarse-priority", type=int, default=1, choices=[0, 1])
     ap.add_argument("--coarse-sms", type=int, default=0, help="SMs of the coarse sweeps' own partition (0: shared)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
