@@ -3,8 +3,10 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 Physics (Sec. 2.1, Eqs. 3-6): Oberbeck-Boussinesq equations in a box
-x in [0, Lx) (periodic), z in [-1/2, 1/2], no-slip isothermal walls
-T(-1/2) = 1, T(1/2) = 0, time in thermal-diffusion units.  Eq. 3 times Pr:
+x in [0, Lx) (periodic), z in [-1/2, 1/2], no-slip walls, isothermal
+T(-1/2) = 1, T(1/2) = 0 (Eq. 6) or with fixed flux dT/dz = -1 (Eq. 7, Ra then
+being the flux Rayleigh number of Eq. 8), time in thermal-diffusion units.
+Eq. 3 times Pr:
 
     u_t + u.grad u = -grad p + Pr Ra T z^ + Pr lap u,    div u = 0,
     T_t + u.grad T = lap T.
@@ -85,10 +87,16 @@ def native_points(Nx, Nz, Lx):
 class RBC:
     """Fine (or coarse) propagator of Sec. 3.2 on one grid with one time step."""
 
-    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt):
+    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, bc="fixed_T"):
+        """bc: "fixed_T" (Eq. 6: T = 1, 0 at z = -1/2, 1/2) or "fixed_flux"
+        (Eq. 7: dT/dz = -1 at both walls, with Ra read as the flux Rayleigh
+        number Ra_f of Eq. 8); no-slip walls in both."""
         if Nx % 2 or Nx < 4 or Nz < 8 or Nz % 2 or dt <= 0:
             raise ValueError("need even Nx >= 4, even Nz >= 8, dt > 0")
+        if bc not in ("fixed_T", "fixed_flux"):
+            raise ValueError("bc must be fixed_T or fixed_flux")
         self.Ra, self.Pr, self.Lx, self.Nx, self.Nz, self.dt = Ra, Pr, Lx, Nx, Nz, dt
+        self.bc = bc
         self.nm = Nx // 2
         self.Mx = 3 * Nx // 2
         self.Mz = 3 * Nz // 2
@@ -112,6 +120,11 @@ class RBC:
         self.bc_val_hi = us.value_row(Nz, +1)
         self.bc_slope_lo = us.slope_row(Nz, -1)
         self.bc_slope_hi = us.slope_row(Nz, +1)
+        # temperature boundary rows and values (d/ds rows: dT/dz = 2 dT/ds = -1)
+        if bc == "fixed_T":
+            self.T_bc_lo, self.T_bc_hi, self.T_bc_val = self.bc_val_lo, self.bc_val_hi, (1.0, 0.0)
+        else:
+            self.T_bc_lo, self.T_bc_hi, self.T_bc_val = self.bc_slope_lo, self.bc_slope_hi, (-0.5, -0.5)
         self._factor()
 
     # ---- linear operators, per Fourier mode (Eq. 3 x Pr and Eq. 5, d/dz = 2 d/ds) ----
@@ -139,7 +152,7 @@ class RBC:
         h = 0.5 * self.dt
         Nz = self.Nz
         M, L = self.ops_T(0.0)
-        A = np.vstack([M - h * L, self.bc_val_lo, self.bc_val_hi])
+        A = np.vstack([M - h * L, self.T_bc_lo, self.T_bc_hi])
         self.lu_T0 = sla.lu_factor(A)
         M, L = self.ops_U()
         A = np.vstack([M - h * L, self.bc_val_lo, self.bc_val_hi])
@@ -151,8 +164,8 @@ class RBC:
             MP, LP, Cpl = self.ops_psi(k)
             A = np.zeros((2 * Nz, 2 * Nz), dtype=complex)
             A[: Nz - 2, :Nz] = MT - h * LT
-            A[Nz - 2, :Nz] = self.bc_val_lo
-            A[Nz - 1, :Nz] = self.bc_val_hi
+            A[Nz - 2, :Nz] = self.T_bc_lo
+            A[Nz - 1, :Nz] = self.T_bc_hi
             A[Nz : 2 * Nz - 4, :Nz] = -h * Cpl
             A[Nz : 2 * Nz - 4, Nz:] = MP - h * LP
             A[2 * Nz - 4, Nz:] = self.bc_val_lo
@@ -229,11 +242,11 @@ class RBC:
         return State(T, P, U), wT
 
     def solve_stage(self, r):
-        """Solve (M - dt/2 L) X = r in tau rows, boundary rows of Eq. 6."""
+        """Solve (M - dt/2 L) X = r in tau rows, boundary rows of Eq. 6 (or Eq. 7)."""
         Nz = self.Nz
         T = np.zeros((self.nm, Nz), dtype=complex)
         psi = np.zeros((self.nm, Nz), dtype=complex)
-        b = np.concatenate([r.T[0].real, [1.0, 0.0]])      # T(z=-1/2)=1, T(z=1/2)=0
+        b = np.concatenate([r.T[0].real, self.T_bc_val])   # the mean profile's wall values or slopes
         T[0] = sla.lu_solve(self.lu_T0, b)
         U = sla.lu_solve(self.lu_U, np.concatenate([r.U, [0.0, 0.0]]))
         for m in range(1, self.nm):

@@ -8,9 +8,13 @@ u = 0, in the same variables (psi, T) and units as Eqs. 3-6:
     sigma lap_k psi = Pr lap_k^2 psi - i k Pr Ra theta
     sigma theta     = lap_k theta + (-dT0/dz) w = lap_k theta - i k psi,
 
-psi = psi' = 0 and theta = 0 on z = +-1/2.  It shares no code with ``oracle``.
-Chandrasekhar's marginal curve for two rigid walls has its minimum
-Ra_c = 1707.76 at k_c = 3.117; the paper reports agreement within 0.1%.
+psi = psi' = 0 and theta = 0 on z = +-1/2 (fixed temperature, Eq. 6), or
+theta' = 0 there (fixed flux, Eq. 7: the conduction profile has the same
+slope, so only the temperature boundary rows change).  It shares no code with
+``oracle``.  Chandrasekhar's marginal curve for two rigid walls has its minimum
+Ra_c = 1707.76 at k_c = 3.117; the paper reports agreement within 0.1%.  With
+fixed flux at two rigid walls the marginal curve decreases to Ra_c = 720 as
+k -> 0 (Sparrow, Goldstein & Jonsson 1964; Hurle, Jakeman & Pike 1967).
 """
 import numpy as np
 import scipy.linalg as sla
@@ -30,7 +34,7 @@ def cheb_collocation(N):
     return D, x
 
 
-def growth_rates(Ra, k, Pr=1.0, N=40):
+def growth_rates(Ra, k, Pr=1.0, N=40, bc="fixed_T"):
     """All finite eigenvalues sigma of the linearised problem at wavenumber k."""
     D, s = cheb_collocation(N)
     Dz = 2.0 * D                       # z = s/2
@@ -50,22 +54,25 @@ def growth_rates(Ra, k, Pr=1.0, N=40):
         A[r, :] = 0.0
         B[r, :] = 0.0
         A[r, :n] = row
-    for r in (n, n + N):
+    for r, j in ((n, 0), (n + N, N)):
         A[r, :] = 0.0
         B[r, :] = 0.0
-        A[r, n + (r - n)] = 1.0
+        if bc == "fixed_T":
+            A[r, n + j] = 1.0
+        else:
+            A[r, n:] = Dz[j]
     w = sla.eig(A, B, right=False)
     w = w[np.isfinite(w)]
     return w[np.abs(w) < 1e8]
 
 
-def max_growth(Ra, k, Pr=1.0, N=40):
-    return np.max(growth_rates(Ra, k, Pr, N).real)
+def max_growth(Ra, k, Pr=1.0, N=40, bc="fixed_T"):
+    return np.max(growth_rates(Ra, k, Pr, N, bc).real)
 
 
-def critical_Ra(k, Pr=1.0, N=40):
+def critical_Ra(k, Pr=1.0, N=40, bc="fixed_T", lo=1000.0, hi=5000.0):
     """Ra at which the leading growth rate crosses zero for wavenumber k."""
-    return brentq(lambda Ra: max_growth(Ra, k, Pr, N), 1000.0, 5000.0, xtol=1e-10)
+    return brentq(lambda Ra: max_growth(Ra, k, Pr, N, bc), lo, hi, xtol=1e-10)
 
 
 def critical_point(Pr=1.0, N=40):

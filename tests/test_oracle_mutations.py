@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import test_oracle_diagnostics as diag
+import test_oracle_fixed_flux as ff
 import test_oracle_pins as pins
 import test_oracle_tableau as tableau
 from oracle import rbc as orbc
@@ -159,6 +160,33 @@ def test_left_endpoint_time_rule_fails_the_trapezoid_pin(monkeypatch):
         diag.test_D7_trapezoid_integrals_of_pure_diffusion()
 
 
+def _planted_flux_rows(monkeypatch, change):
+    orig = orbc.RBC.__init__
+
+    def init(self, *a, **k):
+        orig(self, *a, **k)
+        if self.bc == "fixed_flux":
+            change(self)
+            self._factor()
+    monkeypatch.setattr(orbc.RBC, "__init__", init)
+
+
+def test_flipped_wall_flux_fails_the_fixed_flux_conduction_pin(monkeypatch):
+    def change(r):
+        r.T_bc_val = (0.5, 0.5)                         # dT/dz = +1: heat drawn out at the bottom
+    _planted_flux_rows(monkeypatch, change)
+    with pytest.raises(AssertionError):
+        ff.test_FF1_conduction_is_a_fixed_point()
+
+
+def test_value_rows_for_fixed_flux_fail_the_neumann_decay_pin(monkeypatch):
+    def change(r):
+        r.T_bc_lo, r.T_bc_hi = r.bc_val_lo, r.bc_val_hi
+    _planted_flux_rows(monkeypatch, change)
+    with pytest.raises(AssertionError):
+        ff.test_FF2_neumann_mode_decays_by_the_stability_function(1)
+
+
 def test_unmutated_oracle_passes_the_same_pins():
     pins.test_P4_oracle_operators_match_collocation_growth_rate(2500.0)
     pins.test_P2_temperature_diffusion_decays_by_the_stability_function()
@@ -168,4 +196,6 @@ def test_unmutated_oracle_passes_the_same_pins():
     diag.test_D3_kinetic_energy_budget_along_the_dynamics()
     diag.test_D5_plane_mean_and_variance_by_brute_force()
     diag.test_D7_trapezoid_integrals_of_pure_diffusion()
+    ff.test_FF1_conduction_is_a_fixed_point()
+    ff.test_FF2_neumann_mode_decays_by_the_stability_function(1)
     assert Fr(1, 2) == tableau.AI[1][1]
