@@ -57,14 +57,19 @@ typedef enum {
 } rbc_status;
 
 enum { RBC_FP64 = 0, RBC_MIXED = 1 };         /* rbc_opts.precision */
-enum { RBC_FIXED_T = 0 };                    /* rbc_opts.bc (Eq. 6) */
+enum { RBC_FIXED_T = 0, RBC_FIXED_FLUX = 1 }; /* rbc_opts.bc (Eqs. 6, 7) */
 enum { RBC_CRIT_FIXED = 0, RBC_CRIT_DEFECT = 1, RBC_CRIT_NU = 2 };
 
 typedef struct {
   int precision;   /* RBC_FP64: every step in FP64.  RBC_MIXED: transforms and
                       products in FP32, solves, RK combination, Parareal update
                       and norms in FP64.                                        */
-  int bc;          /* RBC_FIXED_T only                                          */
+  int bc;          /* RBC_FIXED_T: T = 1, 0 at the bottom and top walls (Eq. 6).
+                      RBC_FIXED_FLUX: dT/dz = -1 at both walls (Eq. 7); Ra is
+                      then the flux Rayleigh number Ra_f of Eq. 8.  No-slip
+                      walls in both.  With fixed flux, Nu_b = Nu_t = 1 and the
+                      Nusselt number is 1 / (T_bottom - T_top) (the plane
+                      means at the walls, rbc_diagnostics' profile ends).      */
   int eager;       /* 0: rbc_step_batch runs its steps as one graph launch (a
                       device-side loop); 1: every kernel is launched from the
                       host, so per-kernel profilers see each launch (slower).

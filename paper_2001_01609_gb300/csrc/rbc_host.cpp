@@ -551,9 +551,13 @@ static rbc_status upload_tables(rbc_t h) {
   for (int p = 0; p < 2; ++p) {
     for (int m = 0; m < nm; ++m) {
       const double k = g.kfac * m;
-      // temperature: BC row (all ones), tau rows of S2 - h (4 D2 - k^2 S2)
+      // temperature: BC row (wall values: all ones; wall slopes: n^2), tau rows
+      // of S2 - h (4 D2 - k^2 S2)
       Mat A((size_t)nq * nq, 0.0);
-      for (int q = 0; q < nq; ++q) A[q] = 1.0;
+      for (int q = 0; q < nq; ++q) {
+        const double n = 2 * q + p;
+        A[q] = (g.bc == RBC_FIXED_FLUX) ? n * n : 1.0;
+      }
       for (int t = 0; t + 1 < nq; ++t)
         for (int q = 0; q < nq; ++q) {
           const int r = 2 * t + p, c = 2 * q + p;
@@ -737,7 +741,7 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   if (o.eager != 0 && o.eager != 1) return fail(RBC_EINVAL, "eager must be 0 or 1");
   if (o.precision != RBC_FP64 && o.precision != RBC_MIXED)
     return fail(RBC_EINVAL, "precision mode %d not available", o.precision);
-  if (o.bc != RBC_FIXED_T) return fail(RBC_EINVAL, "boundary condition %d not available", o.bc);
+  if (o.bc != RBC_FIXED_T && o.bc != RBC_FIXED_FLUX) return fail(RBC_EINVAL, "boundary condition %d not available", o.bc);
   // padded x length 3 Nx / 2 must be 3 * 2^p for the FFT
   int Mx = 3 * Nx / 2, r = Mx / 3;
   if (Mx % 3 || (r & (r - 1))) return fail(RBC_EINVAL, "Nx must be a power of two (3/2-padded FFT length 3*2^p)");
@@ -759,6 +763,7 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   g.dt = dt;
   g.kfac = 2.0 * M_PI / Lx;
   g.mixed = (o.precision == RBC_MIXED) ? 1 : 0;
+  g.bc = o.bc;
   rbc_status s = upload_tables(h);
   if (s == RBC_OK) {
     cudaError_t e = configure_kernels(g);
@@ -1128,7 +1133,7 @@ extern "C" rbc_status rbc_step_batch_ra(rbc_t h, void* d_states, int B, const in
 }
 
 static bool compatible(rbc_t fine, rbc_t coarse) {
-  return fine && coarse && coarse->g.Nx <= fine->g.Nx && coarse->g.Nz <= fine->g.Nz;
+  return fine && coarse && coarse->g.Nx <= fine->g.Nx && coarse->g.Nz <= fine->g.Nz && coarse->g.bc == fine->g.bc;
 }
 
 extern "C" rbc_status rbc_restrict(rbc_t fine, rbc_t coarse, const void* d_fine, void* d_coarse, int B,
@@ -1279,7 +1284,8 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
   if (criterion < RBC_CRIT_FIXED || criterion > RBC_CRIT_NU || !(tol >= 0)) return fail(RBC_EINVAL, "bad criterion");
   const Grid &gf = fine->g, &gc = coarse->g;
   if (gc.Nx > gf.Nx || gc.Nz > gf.Nz) return fail(RBC_EINVAL, "coarse grid finer than fine grid");
-  if (gc.Ra != gf.Ra || gc.Pr != gf.Pr || gc.Lx != gf.Lx) return fail(RBC_EINVAL, "Ra, Pr, Lx differ");
+  if (gc.Ra != gf.Ra || gc.Pr != gf.Pr || gc.Lx != gf.Lx || gc.bc != gf.bc)
+    return fail(RBC_EINVAL, "Ra, Pr, Lx or boundary conditions differ");
   const double len = (t1 - t0) / nslices;
   int nf = 0, nc = 0;
   if (!whole_steps(len, gf.dt, &nf)) return fail(RBC_EINVAL, "slice length is not a whole number of fine steps");

@@ -21,7 +21,22 @@ struct Grid {
   double Ra, Pr, Lx, dt;
   double kfac;    // 2 pi / Lx, k_m = kfac * m
   int mixed;      // 1: transforms and products in FP32 (RBC_MIXED)
+  int bc;         // RBC_FIXED_T or RBC_FIXED_FLUX (temperature boundary rows)
 };
+
+// Right-hand side of the temperature boundary row of the mean profile (m = 0)
+// for Chebyshev parity p.  The rows are the parity combinations
+// (f(1) + f(-1)) / 2 (even n) and (f(1) - f(-1)) / 2 (odd n) of the wall
+// values (Eq. 6: T(-1/2) = 1, T(1/2) = 0), or, with fixed flux, of the wall
+// slopes in s = 2z with the even / odd roles swapped (Eq. 7: dT/ds = -1/2 at
+// both walls): 1/2, -1/2 and 0, -1/2.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline double t_wall_rhs(const Grid& g, int p) {
+  if (g.bc == RBC_FIXED_FLUX) return p == 0 ? 0.0 : -0.5;
+  return p == 0 ? 0.5 : -0.5;
+}
 
 // Device-resident operator tables (built on the host in FP64 once per grid/dt).
 // Parity-split tables are laid out [p][row][j][m] so that threads with

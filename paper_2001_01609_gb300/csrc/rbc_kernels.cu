@@ -830,8 +830,8 @@ __device__ __forceinline__ bool solve_recurrence(const Grid& g, const Tables& tb
       for (int r2 = 0; r2 < D; ++r2) bd[r2] = fma(-md[k][r2], bc, bd[r2]);
     }
   }
-  // boundary rows (Eq. 6): parity combinations of f(1) +- f(-1)
-  if (KIND == KT && m == 0 && c == 0) bd[0] += (p == 0) ? 0.5 : -0.5;   // T(-1/2) = 1, T(1/2) = 0
+  // boundary rows: parity combinations of the wall values (Eq. 6) or slopes (Eq. 7)
+  if (KIND == KT && m == 0 && c == 0) bd[0] += t_wall_rhs(g, p);
   const double* Dinv = SY::Dinv(tb);
   const double* Lb = SY::Lb(tb);
   const double* invd = SY::invd(tb);
@@ -990,15 +990,15 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
     __syncthreads();
     const bool dense = g.nq <= kDenseSolveMaxNq;
     if (dense) {
-      // boundary rows of b (Eq. 6): T(-1/2) = 1, T(1/2) = 0 in the parity
-      // combinations f(1) +- f(-1); zero for T at m >= 1, psi and U
+      // boundary rows of b: the mean temperature's wall values (Eq. 6) or
+      // slopes (Eq. 7) in parity combinations; zero for T at m >= 1, psi and U
       for (int it = threadIdx.x; it < 2 * W; it += blockDim.x) {
         const int r = it / W, col = it - r * W;
         if (col >= ncol) continue;
         const int m = m0 + col / 2, c = col & 1;
         const int D = (sys == 1 && m != 0) ? 2 : 1;
         if (r >= D) continue;
-        sm.y[r * W + col] = (sys == 0 && m == 0 && c == 0) ? ((p == 0) ? 0.5 : -0.5) : 0.0;
+        sm.y[r * W + col] = (sys == 0 && m == 0 && c == 0) ? t_wall_rhs(g, p) : 0.0;
       }
       __syncthreads();
       for (int it = threadIdx.x; it < nq * W; it += blockDim.x) {

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "librbc.so")
 
 RBC_OK, RBC_EINVAL, RBC_ENOMEM, RBC_ECUDA, RBC_EDIVERGED, RBC_ETIMEOUT, RBC_ENOTCONVERGED = 0, -1, -2, -3, -4, -5, 1
 RBC_FP64, RBC_MIXED = 0, 1
+RBC_FIXED_T, RBC_FIXED_FLUX = 0, 1
 CRIT_FIXED, CRIT_DEFECT, CRIT_NU = 0, 1, 2
 
 EXPORTS = [
@@ -111,12 +112,13 @@ def _dptr(a):
 class Propagator:
     """F (or G) of Eq. 20 on one grid: rbc_create(Ra, Pr, Lx, Nx, Nz, dt)."""
 
-    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, precision=RBC_FP64, eager=False):
+    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, precision=RBC_FP64, eager=False, bc=RBC_FIXED_T):
+        """bc: RBC_FIXED_T (Eq. 6) or RBC_FIXED_FLUX (Eq. 7, Ra = Ra_f of Eq. 8)."""
         lib = load()
         self.Ra, self.Pr, self.Lx, self.Nx, self.Nz, self.dt = Ra, Pr, Lx, Nx, Nz, dt
-        self.precision = precision
+        self.precision, self.bc = precision, bc
         h = ctypes.c_void_p()
-        opts = _Opts(precision, 0, 1 if eager else 0)
+        opts = _Opts(precision, bc, 1 if eager else 0)
         _check(lib.rbc_create(Ra, Pr, Lx, Nx, Nz, dt, ctypes.byref(opts), ctypes.byref(h)))
         self.h = h
 

@@ -55,6 +55,28 @@ def test_invalid_arguments_are_rejected_without_touching_the_device(lib):
     assert b"need" in lib.rbc_last_error() or len(lib.rbc_last_error()) > 0
 
 
+def test_stage_factors_of_both_boundary_conditions_pass_the_residual_check(lib):
+    """rbc_create builds and factors every stage matrix on the host, checks the
+    solve residual (else RBC_EINVAL), and only then allocates on the device.
+    Without a GPU that first allocation fails (RBC_ECUDA): reaching it means
+    the unpivoted factors of the fixed-temperature and fixed-flux systems of
+    these grids passed the check."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("the check needs the device allocation to fail")
+    h = ctypes.c_void_p()
+    for bc in (rbc.RBC_FIXED_T, rbc.RBC_FIXED_FLUX):
+        for Nx, Nz, dt, Ra in ((32, 16, 1e-3, 1e4), (256, 64, 2e-4, 1e6), (512, 128, 5e-5, 1e7),
+                               (1024, 256, 2e-5, 1e8), (64, 8, 1e-2, 1e4)):
+            o = rbc._Opts(rbc.RBC_FP64, bc, 0)
+            st = lib.rbc_create(Ra, 1.0, 2.0, Nx, Nz, dt, ctypes.byref(o), ctypes.byref(h))
+            assert st == rbc.RBC_ECUDA, (bc, Nx, Nz, lib.rbc_last_error())
+            assert b"cudaMalloc" in lib.rbc_last_error()
+            assert h.value is None
+    o = rbc._Opts(rbc.RBC_FP64, 2, 0)
+    assert lib.rbc_create(1e4, 1.0, 2.0, 32, 16, 1e-3, ctypes.byref(o), ctypes.byref(h)) == rbc.RBC_EINVAL
+
+
 def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(rbc, "_lib", None)
     monkeypatch.setattr(rbc, "LIB_PATH", str(tmp_path / "missing.so"))
