@@ -46,7 +46,7 @@ def oracle_row(o, X):
     return np.concatenate([[d["KE2"], d["eps"], d["wT"]], d["nu"], d["Tm"], d["Tv"]])
 
 
-@pytest.mark.parametrize("Nx,Nz", [(32, 16), (48, 20), (24, 36), (96, 64)])
+@pytest.mark.parametrize("Nx,Nz", [(32, 16), (64, 20), (16, 36), (128, 64)])
 def test_diagnostics_match_oracle(rbc, Nx, Nz):
     o = RBC(2e5, 0.9, 2.0, Nx, Nz, 1e-3)
     Xs = random_states(o, 3, seed=Nx + Nz)
