@@ -131,15 +131,16 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------
-# DRAM bytes (read + write) per launch of the stage kernels, from one ncu
-# capture of a single RK443 step (the stage-kernel summary in profiles/),
+# DRAM bytes (read + write) per launch of the stage kernels: the mean over the
+# four stages of one RK443 step captured with ncu (fine: 32 slices of 256 x 64;
+# coarse: one slice of 128 x 32; the stage-kernel traffic summary in profiles/),
 # valid only while the kernel sources are those that were captured.
 NCU_TRAFFIC_SOURCES = ("paper_2001_01609_gb300/csrc/rbc_kernels.cu", "paper_2001_01609_gb300/csrc/rbc_internal.h")
-NCU_TRAFFIC_SHA256 = "d59e0224428dd5531224d65c63db9019969927a986df749dcf72d0da1d842efb"
+NCU_TRAFFIC_SHA256 = "296cd94db1f3676ad69d1a318435f4f31967abcecbebda345941d172be97d685"
 NCU_TRAFFIC = {
-    "coarse:k_zinv": 128256, "coarse:k_rows": 493056, "coarse:k_zfwd": 117760, "coarse:k_solve": 805120,
-    "fine:k_zinv": 8526336 + 2475264, "fine:k_rows": 56695552 + 432128, "fine:k_zfwd": 12618752,
-    "fine:k_solve": 17935104 + 61696,
+    "coarse:k_zinv": 128384, "coarse:k_rows": 493568, "coarse:k_zfwd": 116544, "coarse:k_solve": 826688,
+    "fine:k_zinv": 8542144 + 681280, "fine:k_rows": 56724032 + 832, "fine:k_zfwd": 12629120,
+    "fine:k_solve": 23544128,
 }
 
 
@@ -209,7 +210,7 @@ def run_gb300(args, w):
     G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dv["dtc"])
     N = w["slices"]
     P = rbc.Parareal(F, G, 0.0, dv["t_end"], N)
-    group = args.group if args.group else N
+    group = args.group if args.group else -(-N // 4)
     first = args.first_group if args.first_group else (group if group >= N else -(-group // 4))
     P.set_schedule(group, first, args.fine_streams, args.coarse_priority, args.coarse_sms)
     stream = torch.cuda.current_stream()
@@ -572,10 +573,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(SERVING))
     ap.add_argument("--group", type=int, default=0,
-                    help="largest fine group (default: all slices, one fine batch after the coarse sweep)")
+                    help="largest fine group (default: a quarter of the slices; the number of slices gives "
+                         "one fine batch after the coarse sweep)")
     ap.add_argument("--first-group", type=int, default=0,
                     help="first fine group (default: --group when it covers all slices, else a quarter of it)")
-    ap.add_argument("--fine-streams", type=int, default=1, choices=[1, 2, 3, 4])
+    ap.add_argument("--fine-streams", type=int, default=2, choices=[1, 2, 3, 4])
     ap.add_argument("--coarse-priority", type=int, default=1, choices=[0, 1])
     ap.add_argument("--coarse-sms", type=int, default=0, help="SMs of the coarse sweeps' own partition (0: shared)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
