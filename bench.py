@@ -19,6 +19,7 @@ Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|refere
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -528,6 +529,74 @@ NCU_CASES = {
 }
 
 
+# Coarsening and slice-count study (Sec. 3.6; Fig. 9 plots speedup against the
+# number of slices): config 1's fine propagator over a tenth of its horizon,
+# Parareal with coarse propagators coarsened in space (CF 2, 4) and time, for
+# several slice counts; iteration time, defects and final error against the
+# serial fine run on the same GPU.
+STUDY = dict(Ra=1e6, Pr=1.0, Lx=2.0, Nx=256, Nz=64, dt=1.25e-5, total_steps=9600, seed=1, iters=4,
+             slices=(8, 16, 32), coarse=((128, 32, 1.5625e-5), (64, 16, 1.5625e-5), (64, 16, 3.125e-5)))
+
+
+def run_coarsening_study():
+    import torch
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc
+    from paper_2001_01609_gb300.inputs import initial_temperature
+    s = STUDY
+    F = rbc.Propagator(s["Ra"], s["Pr"], s["Lx"], s["Nx"], s["Nz"], s["dt"])
+    U0 = F.new_states(1)
+    F.set_state(U0[0], initial_temperature(s["Nx"], s["Nz"], seed=s["seed"], Lx=s["Lx"]))
+    T = s["total_steps"] * s["dt"]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ser = F.new_states(1)
+    ser.copy_(U0)
+    F.step_batch(ser, 20)                                  # graphs for B = 1
+    ser.copy_(U0)
+    e0.record(stream)
+    F.step_batch(ser, s["total_steps"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    serial_s = e0.elapsed_time(e1) / 1e3
+    nrm = torch.zeros(2, dtype=torch.float64, device="cuda")
+
+    def finite(x):
+        return float(x) if math.isfinite(float(x)) else None
+
+    rows = []
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    for Nxc, Nzc, dtc in s["coarse"]:
+        G = rbc.Propagator(s["Ra"], s["Pr"], s["Lx"], Nxc, Nzc, dtc)
+        for N in s["slices"]:
+            P = rbc.Parareal(F, G, 0.0, T, N)
+            U = F.new_states(N + 1)
+            e0.record(stream)
+            st, k, de, _ = P.iterate(U0[0], U, min(s["iters"], N))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            el = e0.elapsed_time(e1) / 1e3
+            rbc.l2_diff(F, U[N:N + 1], ser, nrm[0:1])
+            rbc.l2_diff(F, ser, None, nrm[1:2])
+            a, b = nrm.cpu().tolist()
+            err = math.sqrt(a / b) if math.isfinite(a) and b > 0 else None
+            rows.append(dict(coarse_grid=f"{Nxc}x{Nzc}", coarse_dt=dtc, slices=N,
+                             fine_steps_per_slice=s["total_steps"] // N,
+                             coarse_steps_per_slice=int(round(T / N / dtc)), iterations=k, status=st,
+                             seconds=el, seconds_per_iteration=el / max(k, 1),
+                             defects=[finite(x) for x in de], final_error_vs_serial=err,
+                             speedup_vs_serial_fine=serial_s / el))
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            P.close()
+        G.close()
+    ck = clocks.stop()
+    print(json.dumps(dict(study="parareal_coarsening_and_slices", Ra=s["Ra"], grid=f"{s['Nx']}x{s['Nz']}",
+                          dt=s["dt"], t_end=T, total_fine_steps=s["total_steps"], serial_fine_s=serial_s,
+                          iterations_max=s["iters"], clocks=ck, rows=rows)), flush=True)
+
+
 def run_ncu_case(name):
     """A small, self-ending case for ncu: one plain (graph-free) RK443 step of a
     batch, or one short Parareal iteration on the bench's grids."""
@@ -582,9 +651,13 @@ def main():
     ap.add_argument("--coarse-sms", type=int, default=0, help="SMs of the coarse sweeps' own partition (0: shared)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
+    ap.add_argument("--study", choices=["coarsening"], help="the coarsening and slice-count study, not a bench line")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
+        return
+    if args.study:
+        run_coarsening_study()
         return
     if args.workload in SERVING:
         if args.impl == "reference":
