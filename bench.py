@@ -597,6 +597,48 @@ def run_coarsening_study():
                           iterations_max=s["iters"], clocks=ck, rows=rows)), flush=True)
 
 
+def run_statistics_study():
+    """StatisticalParareal (Sec. 2.2 statistics sampled along every fine sweep,
+    statistical stopping) against the library's parareal_iterate on the study's
+    fine grid: 16 slices of 600 fine steps, CF 2 coarse propagator."""
+    import torch
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc
+    from paper_2001_01609_gb300 import statistics as pst
+    from paper_2001_01609_gb300.inputs import initial_temperature
+    s = STUDY
+    N, every, K = 16, 50, 3
+    Nxc, Nzc, dtc = s["coarse"][0]
+    F = rbc.Propagator(s["Ra"], s["Pr"], s["Lx"], s["Nx"], s["Nz"], s["dt"])
+    G = rbc.Propagator(s["Ra"], s["Pr"], s["Lx"], Nxc, Nzc, dtc)
+    U0 = F.new_states(1)
+    F.set_state(U0[0], initial_temperature(s["Nx"], s["Nz"], seed=s["seed"], Lx=s["Lx"]))
+    T = s["total_steps"] * s["dt"]
+    P = pst.StatisticalParareal(F, G, 0.0, T, N, every=every, tol=1e-2)
+    U = F.new_states(N + 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = P.iterate(U0[0], U, K)
+    torch.cuda.synchronize()
+    t_stat = time.perf_counter() - t0
+    L = rbc.Parareal(F, G, 0.0, T, N)
+    U2 = F.new_states(N + 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, k, de, nus = L.iterate(U0[0], U2, res["k"])
+    torch.cuda.synchronize()
+    t_lib = time.perf_counter() - t0
+    keep = ("NuV", "Nub", "Nut", "Re", "P", "eps_U", "Nu_int", "balance", "delta_T", "N_BL", "delta_t")
+    stats = [{q: (float(a[q]) if q != "N_BL" else int(a[q])) for q in keep} for a in res["stats"]]
+    print(json.dumps(dict(study="statistical_parareal", grid=f"{s['Nx']}x{s['Nz']}", coarse_grid=f"{Nxc}x{Nzc}",
+                          Ra=s["Ra"], slices=N, fine_steps_per_slice=s["total_steps"] // N, sample_every=every,
+                          criterion="stat", tol=1e-2, status=res["status"], iterations=res["k"],
+                          defects=res["defects"], stats=stats, seconds=t_stat,
+                          library_parareal=dict(iterations=k, seconds=t_lib, defects=list(map(float, de))),
+                          same_iterates_as_library=bool(torch.equal(U, U2)))), flush=True)
+
+
 def run_ncu_case(name):
     """A small, self-ending case for ncu: one plain (graph-free) RK443 step of a
     batch, or one short Parareal iteration on the bench's grids."""
@@ -651,13 +693,14 @@ def main():
     ap.add_argument("--coarse-sms", type=int, default=0, help="SMs of the coarse sweeps' own partition (0: shared)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
-    ap.add_argument("--study", choices=["coarsening"], help="the coarsening and slice-count study, not a bench line")
+    ap.add_argument("--study", choices=["coarsening", "statistics"],
+                    help="the coarsening and slice-count study, or the statistical Parareal run (not bench lines)")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
         return
     if args.study:
-        run_coarsening_study()
+        run_coarsening_study() if args.study == "coarsening" else run_statistics_study()
         return
     if args.workload in SERVING:
         if args.impl == "reference":
