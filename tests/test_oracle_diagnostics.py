@@ -86,13 +86,23 @@ def test_D3_kinetic_energy_budget_along_the_dynamics():
     """Dotting Eq. 3 (times Pr) with u: d<u^2 + w^2>_V/dt = 2 Pr (Ra <wT>_V + <u.lap u>_V);
     pressure and advection integrate to zero.  Checked during the growth of the
     first rolls (Ra = 1e4, Pr = 0.7), with a five-point difference in time."""
+    energy_budget("fixed_T", 30)
+
+
+def test_D3_kinetic_energy_budget_with_fixed_flux():
+    """The same budget with fixed-flux walls (it does not involve the temperature
+    boundary condition)."""
+    energy_budget("fixed_flux", 28)
+
+
+def energy_budget(bc, nsteps):
     Pr = 0.7
-    r = RBC(1e4, Pr, 2.0, 16, 32, 5e-3)
+    r = RBC(1e4, Pr, 2.0, 16, 32, 5e-3, bc=bc)
     X = conduction(r)
     X.T[1] = 1e-3 * cos_pi_z(r.Nz)
-    for _ in range(30):
+    for _ in range(nsteps):
         X, _ = r.step(X)
-    h = RBC(1e4, Pr, 2.0, 16, 32, 1e-5)
+    h = RBC(1e4, Pr, 2.0, 16, 32, 1e-5, bc=bc)
     Xs = [X]
     for _ in range(4):
         Xs.append(h.step(Xs[-1])[0])
