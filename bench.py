@@ -538,7 +538,7 @@ STUDY = dict(Ra=1e6, Pr=1.0, Lx=2.0, Nx=256, Nz=64, dt=1.25e-5, total_steps=9600
              slices=(8, 16, 32), coarse=((128, 32, 1.5625e-5), (64, 16, 1.5625e-5), (64, 16, 3.125e-5)))
 
 
-def run_coarsening_study():
+def run_coarsening_study(coarse=None, slices=None):
     import torch
     from paper_2001_01609_gb300 import build
     build.build()
@@ -568,9 +568,9 @@ def run_coarsening_study():
     rows = []
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    for Nxc, Nzc, dtc in s["coarse"]:
+    for Nxc, Nzc, dtc in (coarse or s["coarse"]):
         G = rbc.Propagator(s["Ra"], s["Pr"], s["Lx"], Nxc, Nzc, dtc)
-        for N in s["slices"]:
+        for N in (slices or s["slices"]):
             P = rbc.Parareal(F, G, 0.0, T, N)
             U = F.new_states(N + 1)
             e0.record(stream)
@@ -695,12 +695,21 @@ def main():
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
     ap.add_argument("--study", choices=["coarsening", "statistics"],
                     help="the coarsening and slice-count study, or the statistical Parareal run (not bench lines)")
+    ap.add_argument("--study-coarse", default="",
+                    help="coarse propagators of the coarsening study, e.g. 32x8:3.125e-5,64x16:1.5625e-5")
+    ap.add_argument("--study-slices", default="", help="slice counts of the coarsening study, e.g. 8,32")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
         return
-    if args.study:
-        run_coarsening_study() if args.study == "coarsening" else run_statistics_study()
+    if args.study == "coarsening":
+        coarse = [(int(g.split(":")[0].split("x")[0]), int(g.split(":")[0].split("x")[1]), float(g.split(":")[1]))
+                  for g in args.study_coarse.split(",") if g]
+        slices = [int(n) for n in args.study_slices.split(",") if n]
+        run_coarsening_study(coarse or None, slices or None)
+        return
+    if args.study == "statistics":
+        run_statistics_study()
         return
     if args.workload in SERVING:
         if args.impl == "reference":
