@@ -530,10 +530,10 @@ NCU_CASES = {
 
 
 # Coarsening and slice-count study (Sec. 3.6; Fig. 9 plots speedup against the
-# number of slices): config 1's fine propagator over a tenth of its horizon,
-# Parareal with coarse propagators coarsened in space (CF 2, 4) and time, for
-# several slice counts; iteration time, defects and final error against the
-# serial fine run on the same GPU.
+# number of slices): the 256 x 64, Ra 1e6 fine propagator over a tenth of the
+# Parareal workload's horizon, with coarse propagators coarsened in space
+# (CF 2, 4, 8) and in time, for several slice counts; iteration time, defects
+# and final error against the serial fine run on the same GPU.
 STUDY = dict(Ra=1e6, Pr=1.0, Lx=2.0, Nx=256, Nz=64, dt=1.25e-5, total_steps=9600, seed=1, iters=4,
              slices=(8, 16, 32), coarse=((128, 32, 1.5625e-5), (64, 16, 1.5625e-5), (64, 16, 3.125e-5)))
 
@@ -648,7 +648,7 @@ def run_ncu_case(name):
     from paper_2001_01609_gb300 import rbc
     from paper_2001_01609_gb300.inputs import initial_temperature
     if name == "parareal_small":
-        # config-1 grids and time steps, 8 slices of 25 fine / 20 coarse steps
+        # the Parareal workload's grids and time steps, 8 slices of 25 fine / 20 coarse steps
         # (the coarse-to-fine step ratio of the bench workload); every kernel
         # launched from the host, so that a profiler sees each one
         w = WORKLOADS[DEFAULT]

@@ -3,7 +3,7 @@ statistical stopping rule for Parareal (Sec. 3.7, Sec. 5.2).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Sec. 2.2 judges a run by time averages (the overbar) of volume and plane
+Sec. 2.2 assesses a run by time averages (the overbar) of volume and plane
 averages:
 
 * the characteristic speed U = mean of <u^2 + w^2>_V^(1/2); with velocities in
