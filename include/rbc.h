@@ -157,8 +157,9 @@ rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double out[3], cudaS
 rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream);
 
 /* rbc_diagnostics: the instantaneous averages behind the consistency checks
- * of Sec. 2.2, for B contiguous device states, into the device array
- * d_out[B][rbc_diag_size(h)] (FP64), asynchronously on `stream`.  Per state:
+ * of Sec. 2.2, for B contiguous device states (read only), into the
+ * caller-owned device array d_out[B][rbc_diag_size(h)] (FP64, row per state),
+ * asynchronously on `stream`.  Per state:
  *   [0] <u^2 + w^2>_V      (the characteristic speed U is the time mean of its
  *                           square root; Re = U / Pr)
  *   [1] <u . lap u>_V       (viscous term of the energy balance, Eq. 14)
