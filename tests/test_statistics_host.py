@@ -134,3 +134,40 @@ def test_sampled_run_partial_last_chunk():
         np.testing.assert_allclose(I[b, :6], [refs[b][q] for q in ost.SCALARS], rtol=1e-13)
         np.testing.assert_allclose(I[b, 6:6 + Mz], refs[b]["Tm"], rtol=1e-13, atol=1e-18)
         np.testing.assert_allclose(I[b, 6 + Mz:], refs[b]["T2"], rtol=1e-13)
+
+
+def test_single_slice_is_exact_after_one_iteration():
+    """N = 1: the first fine sweep starts from U0 itself, so U_1^1 is the serial fine
+    state and the statistics are those of the one fine trajectory."""
+    from layout import from_abi, to_abi
+    F, G, U0, _, oF, *_ = setup(N=1)
+    t1 = 6 * F.dt
+    P = pst.StatisticalParareal(F, G, 0.0, t1, 1, every=4, lib=ob, criterion="fixed")
+    U = F.new_states(2)
+    res = P.iterate(U0[0], U, 5)
+    assert res["k"] == 1 and res["status"] == rbc.RBC_OK and P.window_first == 0
+    Xend, I = oF(from_abi(U0[0].numpy()))
+    np.testing.assert_array_equal(U[1].numpy(), to_abi(Xend))
+    ref = ost.averages(I, F.Ra, F.Pr, F.o.padded_z(), F.Nz)
+    for q in pst.STAT_QUANTITIES:
+        assert abs(res["stats"][0][q] - ref[q]) <= 1e-13 * abs(ref[q]), q
+
+
+def test_sampling_interval_longer_than_a_slice():
+    """every > steps per slice: one trapezoid over each slice's end points."""
+    F, *_ = setup()
+    X = F.new_states(1)
+    F.set_state(X[0], initial_temperature(16, 16, seed=3, amplitude=0.3))
+    from layout import from_abi
+    ref = ost.run_sampled(F.o, from_abi(X[0].numpy()), 5, 5)[1]
+    I = pst.sampled_run(F, X, 5, 50)
+    np.testing.assert_allclose(I[0, :6], [ref[q] for q in ost.SCALARS], rtol=1e-13)
+
+
+def test_statistical_rule_runs_out_at_the_slice_count():
+    """With an unreachable tolerance the rule is not met; iterations stop at k = N."""
+    F, G, U0, t1, *_ = setup(N=2)
+    P = pst.StatisticalParareal(F, G, 0.0, 2 * 6 * F.dt, 2, every=3, tol=0.0, lib=ob)
+    U = F.new_states(3)
+    res = P.iterate(U0[0], U, 10)
+    assert res["k"] == 2 and res["status"] == rbc.RBC_ENOTCONVERGED and len(res["stats"]) == 2
