@@ -12,7 +12,13 @@ It is a slow, obviously-correct restatement of the method in NumPy/SciPy:
   Fourier(x) x Chebyshev(z) collocation with 3/2-rule dealiasing, IMEX RK443
   time stepping (Sec. 3.2, Sec. 3.6), the Nusselt numbers (Eqs. 9-11).
 * ``parareal``       - the Parareal iteration (Eq. 20) with the defect and
-  Nusselt stopping norms (Sec. 3.7).
+  Nusselt stopping norms (Sec. 3.7) and a statistical stopping rule.
+* ``statistics``     - sampled time means and the consistency checks of
+  Sec. 2.2 (Re, Nu_int, the P / eps_U balance, T_rms, delta_T, N_BL).
+* ``survey_dt``      - a time-step stability survey of one propagator.
+
+``rbc`` also takes fixed-flux walls (Eq. 7) and forms the instantaneous
+averages of Sec. 2.2 (``RBC.diagnostics``).
 
 Every function cites the passage of the paper it follows.  The oracle shares no
 code with the CUDA library; only the seeded input generator
