@@ -3,9 +3,11 @@
  * convection (Clarke, Davies, Ruprecht, Tobias, Oishi: "Performance of
  * parallel-in-time integration for Rayleigh Benard Convection").
  *
- * Problem (Sec. 2.1, Eqs. 3-6): Oberbeck-Boussinesq equations, Prandtl number
+ * Problem (Sec. 2.1, Eqs. 3-7): Oberbeck-Boussinesq equations, Prandtl number
  * Pr, Rayleigh number Ra, periodic x in [0, Lx), z in [-1/2, 1/2], no-slip walls
- * with T(-1/2) = 1, T(1/2) = 0; time in thermal-diffusion units.
+ * with T(-1/2) = 1, T(1/2) = 0 (or, by option, the fixed flux dT/dz = -1 of
+ * Eq. 7); time in thermal-diffusion units.  The consistency diagnostics of
+ * Sec. 2.2 come from rbc_diagnostics.
  * Discretisation (Sec. 3.2): Fourier modes in x, Chebyshev polynomials in z,
  * products in grid space (3/2-rule padded), linear terms implicit (ultraspherical
  * tau), nonlinear terms explicit, IMEX RK443 (Sec. 3.6).  Parareal (Sec. 3.1,
