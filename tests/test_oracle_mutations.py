@@ -15,8 +15,11 @@ import test_oracle_diagnostics as diag
 import test_oracle_fixed_flux as ff
 import test_oracle_pins as pins
 import test_oracle_tableau as tableau
+import test_oracle_transfer as transfer
 from oracle import rbc as orbc
 from oracle import statistics as ost
+
+ORIG_RESTRICT, ORIG_PROLONG = orbc.restrict, orbc.prolong
 
 pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
 
@@ -199,3 +202,42 @@ def test_unmutated_oracle_passes_the_same_pins():
     ff.test_FF1_conduction_is_a_fixed_point()
     ff.test_FF2_neumann_mode_decays_by_the_stability_function(1)
     assert Fr(1, 2) == tableau.AI[1][1]
+
+
+def _restrict_without_mean_flow(X, Nx_c, Nz_c):
+    Xc = ORIG_RESTRICT(X, Nx_c, Nz_c)
+    Xc.U = np.zeros_like(Xc.U)
+    return Xc
+
+
+def _restrict_wrong_modes(X, Nx_c, Nz_c):
+    # keeps the last Fourier modes instead of the first
+    mc = Nx_c // 2
+    return orbc.State(X.T[-mc:, :Nz_c].copy(), X.psi[-mc:, :Nz_c].copy(), X.U[:Nz_c].copy())
+
+
+@pytest.mark.parametrize("mistake", [_restrict_without_mean_flow, _restrict_wrong_modes])
+def test_broken_restriction_fails_the_projection_pin(monkeypatch, mistake):
+    monkeypatch.setattr(orbc, "restrict", mistake)
+    with pytest.raises(AssertionError):
+        transfer.test_restriction_residual_is_orthogonal_to_the_coarse_space((16, 12), (8, 8))
+
+
+def test_prolongation_without_mean_flow_fails_the_point_evaluation_pin(monkeypatch):
+    def prolong(X, Nx, Nz):
+        Xf = ORIG_PROLONG(X, Nx, Nz)
+        Xf.U = np.zeros_like(Xf.U)
+        return Xf
+    monkeypatch.setattr(orbc, "prolong", prolong)
+    with pytest.raises(AssertionError):
+        transfer.test_prolongation_represents_the_same_fields((8, 8), (16, 12))
+
+
+def test_prolongation_with_shifted_chebyshev_modes_fails_the_point_evaluation_pin(monkeypatch):
+    def prolong(X, Nx, Nz):
+        Xf = ORIG_PROLONG(X, Nx, Nz)
+        Xf.T = np.roll(Xf.T, 1, axis=1)
+        return Xf
+    monkeypatch.setattr(orbc, "prolong", prolong)
+    with pytest.raises(AssertionError):
+        transfer.test_prolongation_represents_the_same_fields((8, 8), (16, 12))
