@@ -54,7 +54,10 @@ typedef enum {
   RBC_ECUDA = -3,       /* a CUDA runtime call failed (see rbc_last_error)     */
   RBC_EDIVERGED = -4,   /* a NaN/Inf appeared in a state (Sec. 3.6 warns that
                            Parareal can be unstable with stable F and G)       */
-  RBC_ETIMEOUT = -5,    /* reserved: a bounded device-side wait gave up       */
+  RBC_ETIMEOUT = -5,    /* a bounded device-side wait gave up (the mbarrier
+                           waits of the mixed-precision tensor-core kernels);
+                           the states concerned are left as they were at the
+                           start of the failing step                          */
   RBC_ENOTCONVERGED = 1 /* Parareal reached max_iters without meeting tol      */
 } rbc_status;
 
@@ -127,12 +130,29 @@ rbc_status rbc_step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps,
 rbc_status rbc_step_batch_ra(rbc_t h, void* d_states, int B, const int* h_nsteps, const double* h_ra,
                              double* d_nu_integral, cudaStream_t stream);
 
-/* Synchronises `stream`; RBC_EDIVERGED if any state of the batch went
- * non-finite since the last rbc_step_batch, else RBC_OK.                   */
+/* Synchronises `stream` and reports the device-side errors of the handle:
+ * those of the states of the last rbc_step_batch call and those of every
+ * call since the previous rbc_check_diverged (whose record it clears).
+ * RBC_ETIMEOUT if a bounded device-side wait gave up (a state whose transform
+ * timed out is left as it was at the start of the failing step and its Nu
+ * integral is unspecified), else RBC_EDIVERGED if a state went non-finite,
+ * else RBC_OK.                                                              */
 rbc_status rbc_check_diverged(rbc_t h, cudaStream_t stream);
 
+/* Test hook, outside the paper's method: the number of polls after which
+ * every bounded mbarrier wait of the tensor-core kernels (RBC_MIXED) gives
+ * up, on the current device and for every handle (a device variable, read
+ * by each kernel launch, graph replays included).  0 makes each such wait
+ * give up at once, so that a test can exercise the RBC_ETIMEOUT path without
+ * a fault; a negative value restores the default (2^24 polls).  The waits
+ * that drain work already issued before tensor memory is released always
+ * keep the default limit.                                                  */
+rbc_status rbc_set_wait_limit(long long polls);
+
 /* rbc_nusselt: Nu_V (Eq. 9), Nu_b and Nu_t (Eqs. 10, 11) of one device state,
- * written to host out[3].  Synchronous on `stream`.                         */
+ * written to host out[3].  Synchronous on `stream`.  RBC_ETIMEOUT (out
+ * unspecified) if a tensor-core transform gave up waiting; the record read by
+ * rbc_check_diverged is not touched.                                        */
 rbc_status rbc_nusselt(rbc_t h, const void* d_state, double out[3], cudaStream_t stream);
 
 /* rbc_nusselt_static: the same three Nusselt numbers as rbc_nusselt, from a
@@ -152,7 +172,10 @@ rbc_status rbc_nusselt(rbc_t h, const void* d_state, double out[3], cudaStream_t
  * streams, or different host threads) race and must be serialised by the
  * caller.  Every element a call reads is written by that call first, so no
  * clearing is needed and the leftover contents of an earlier call do not
- * matter.  Synchronous on `stream`; out[3] = (Nu_V, Nu_b, Nu_t) on the host. */
+ * matter, except the call's error word, which it clears first.  Synchronous
+ * on `stream`; out[3] = (Nu_V, Nu_b, Nu_t) on the host; RBC_ETIMEOUT (out
+ * unspecified) if a tensor-core transform of a mixed-precision handle gave
+ * up waiting.                                                               */
 rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double out[3], cudaStream_t stream);
 
 /* ||T||_{L2(Omega)} of one device state (exact in x and z), host out.       */
@@ -217,7 +240,8 @@ void parareal_destroy(parareal_t p);
  * defects[k-1] = Defect_k, nus[k-1] = Nu_{k-1} (arrays of max_iters doubles,
  * either may be NULL).  Returns RBC_OK when the criterion was met (always for
  * RBC_CRIT_FIXED), RBC_ENOTCONVERGED when max_iters ran out, RBC_EDIVERGED on
- * a non-finite state.  Iterations stop after k = nslices, where U^k is the
+ * a non-finite state, RBC_ETIMEOUT if a bounded device-side wait of a
+ * tensor-core kernel gave up.  Iterations stop after k = nslices, where U^k is the
  * serial fine solution.  Synchronous on `stream` (one small D2H per iteration).
  *
  * Schedule (the results do not depend on it, bit for bit): the coarse sweep

@@ -846,6 +846,8 @@ extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
   w.nsteps = ip; ip += B;
   w.flags = ip; ip += B;
   w.step = ip; ip += 1;
+  w.err = ip; ip += 1;
+  w.dflag = ip; ip += 1;
   // the counters start defined: an unset loop bound reads 0 (one step), never garbage
   if (cudaMemset(w.maxs, 0, (size_t)(ip - w.maxs) * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -1170,14 +1172,36 @@ extern "C" rbc_status rbc_l2_diff(rbc_t h, const void* d_A, const void* d_B, int
   return RBC_OK;
 }
 
+// Error bits of the handle: the per-state flags of the last rbc_step_batch
+// call OR-ed with the sticky bits of every call since the last read, which
+// are cleared.  Synchronises `stream`.
+static rbc_status read_errors(rbc_t h, cudaStream_t stream, int* bits) {
+  *bits = 0;
+  CK(cudaStreamSynchronize(stream));
+  if (h->cap == 0) return RBC_OK;
+  std::vector<int> f((size_t)h->last_B + 1, 0);
+  if (h->last_B > 0) CK(cudaMemcpy(f.data(), h->w.flags, (size_t)h->last_B * sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&f[h->last_B], h->w.err, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(h->w.err, 0, sizeof(int)));
+  for (int v : f) *bits |= v;
+  return RBC_OK;
+}
+
+static rbc_status status_of_bits(int bits) {
+  if (bits & kFlagTimeout) return fail(RBC_ETIMEOUT, "a bounded device-side wait gave up");
+  if (bits & kFlagNonFinite) return fail(RBC_EDIVERGED, "non-finite state");
+  return RBC_OK;
+}
+
 extern "C" rbc_status rbc_check_diverged(rbc_t h, cudaStream_t stream) {
   if (!h) return fail(RBC_EINVAL, "null handle");
-  CK(cudaStreamSynchronize(stream));
-  if (h->last_B == 0) return RBC_OK;
-  std::vector<int> f(h->last_B);
-  CK(cudaMemcpy(f.data(), h->w.flags, f.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  for (int v : f)
-    if (v) return fail(RBC_EDIVERGED, "non-finite state");
+  int bits = 0;
+  rbc_status s = read_errors(h, stream, &bits);
+  return s != RBC_OK ? s : status_of_bits(bits);
+}
+
+extern "C" rbc_status rbc_set_wait_limit(long long polls) {
+  CK(tc_set_wait_limit(polls));
   return RBC_OK;
 }
 
@@ -1185,10 +1209,15 @@ extern "C" rbc_status rbc_nusselt(rbc_t h, const void* d_state, double out[3], c
   if (!h || !d_state || !out) return fail(RBC_EINVAL, "null argument");
   rbc_status s = rbc_reserve(h, 1);
   if (s != RBC_OK) return s;
-  CK(launch_nusselt(h->g, h->t, h->w, static_cast<const double*>(d_state), h->w.small, stream));
-  CK(cudaMemcpyAsync(out, h->w.small, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  Work w = h->w;   // the call's own error bits, apart from the batch's
+  w.flags = w.err = h->w.dflag;
+  CK(cudaMemsetAsync(w.dflag, 0, sizeof(int), stream));
+  CK(launch_nusselt(h->g, h->t, w, static_cast<const double*>(d_state), w.small, stream));
+  int bits = 0;
+  CK(cudaMemcpyAsync(out, w.small, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(&bits, w.dflag, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
-  return RBC_OK;
+  return status_of_bits(bits);
 }
 
 extern "C" rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double out[3], cudaStream_t stream) {
@@ -1197,8 +1226,9 @@ extern "C" rbc_status rbc_nusselt_static(rbc_t h, const void* d_state, double ou
   if (need > kStaticScratchCapacity)
     return fail(RBC_EINVAL, "grid %dx%d needs %zu doubles of scratch; the static array holds %zu (3 MiB)",
                 h->g.Nx, h->g.Nz, need, kStaticScratchCapacity);
-  CK(launch_nusselt_static(h->g, h->t, static_cast<const double*>(d_state), out, stream));
-  return RBC_OK;
+  int bits = 0;
+  CK(launch_nusselt_static(h->g, h->t, static_cast<const double*>(d_state), out, &bits, stream));
+  return status_of_bits(bits);
 }
 
 extern "C" size_t rbc_diag_size(rbc_t h) { return h ? (size_t)6 + 2 * (size_t)h->g.Mz : 0; }
@@ -1448,6 +1478,12 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
       for (rbc_t h : {p->fine, p->coarse}) h->bind_ctx = nullptr;
     }
   } bind(p, part);
+  // sticky error bits of every handle in use, read after each iteration
+  std::vector<rbc_t> used{G, G2};
+  for (rbc_t h : p->fines)
+    if (h) used.push_back(h);
+  for (rbc_t h : used)
+    if (h->cap > 0) CK(cudaMemsetAsync(h->w.err, 0, sizeof(int), stream));
   CK(cudaEventRecord(p->ev_begin, stream));   // the side streams start after the caller's work and these copies
   for (cudaStream_t st : sF) CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
   for (cudaStream_t st : {s0, sg}) CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
@@ -1517,6 +1553,13 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
     CK(cudaMemcpyAsync(nrm.data(), p->d_norm, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
     CK(cudaMemcpyAsync(I.data(), p->d_I, N * sizeof(double), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    int bits = 0;
+    for (rbc_t h : used) {
+      int b = 0;
+      if (h->cap > 0) CK(cudaMemcpy(&b, h->w.err, sizeof(int), cudaMemcpyDeviceToHost));
+      bits |= b;
+    }
+    if (bits & kFlagTimeout) return status_of_bits(bits);
     double defect = 0.0;
     for (int n = 1; n <= N; ++n) {
       if (!std::isfinite(nrm[n]) || !std::isfinite(nrm[N + 1 + n])) return fail(RBC_EDIVERGED, "non-finite iterate");

@@ -79,6 +79,10 @@ struct Tables {
   const float *tcW_hi[2], *tcW_lo[2];
 };
 
+// Error bits a kernel sets for a state (Work::flags) and for the handle (Work::err).
+constexpr int kFlagNonFinite = 1;   // a stage solve produced NaN/Inf
+constexpr int kFlagTimeout = 2;     // a bounded device-side wait gave up
+
 // Optional per-kernel CUDA-event timing (host side).  Event pairs come from a
 // pool; when it runs out, the stream is synchronised and the elapsed times are
 // folded into the totals so that the pool can be reused.
@@ -108,7 +112,9 @@ struct Work {
   int* maxs;       // [1] max over nsteps, right before nsteps (copied with it)
   int* nsteps;     // [B]
   int* step;       // [1] step counter of the running batch
-  int* flags;      // [B] non-finite flags
+  int* flags;      // [B] error bits of the running batch: kFlagNonFinite, kFlagTimeout
+  int* err;        // [1] the same bits, OR-ed over every call since the last read (sticky)
+  int* dflag;      // [1] error bits of a diagnostic call (rbc_nusselt)
   double* nu;      // [B] internal Nu integral when the caller passes none
   double* small;   // [16] scalars
   double* ra;      // [B] Rayleigh number of each state
@@ -152,9 +158,11 @@ cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, con
 cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, int B, cudaStream_t s);
 size_t rows_smem_bytes(const Grid& g);
 size_t static_scratch_doubles_needed(const Grid& g);
-constexpr size_t kStaticScratchCapacity = (size_t)3 << 17;   // doubles in the static scratch array
+constexpr size_t kStaticScratchCapacity = (size_t)3 << 17;   // doubles in the static scratch array (3 MiB)
+// Nusselt numbers with all scratch in the static array; *host_flags receives
+// the error bits of the call (kFlagTimeout when a bounded wait gave up).
 cudaError_t launch_nusselt_static(const Grid& g, const Tables& t, const double* X, double* host_out3,
-                                  cudaStream_t s);
+                                  int* host_flags, cudaStream_t s);
 unsigned long long launches_so_far();
 void add_launches(unsigned long long n);   // kernels launched through a replayed graph
 constexpr int kStepKernels = 17;           // 4 stages x 4 kernels + step counter
@@ -175,5 +183,9 @@ size_t tc_zfwd_image_floats(const Grid& g);
 void tc_zfwd_build_images(const Grid& g, const double* zfwd, int p, float* hi, float* lo);
 bool tc_zfwd_supported(const Grid& g);
 cudaError_t launch_zfwd_tc(const Grid& g, const Tables& t, const Work& w, int B, cudaStream_t s);
+// Spin limit of the bounded mbarrier waits of the tensor-core kernels on the
+// current device (limit < 0: the default).  Waits that drain work already
+// issued before tensor memory is freed keep their own, default limit.
+cudaError_t tc_set_wait_limit(long long limit);
 
 }  // namespace rbc

@@ -19,6 +19,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "rbc_internal.h"
 
@@ -925,7 +926,7 @@ __device__ __forceinline__ void solve_lx(const Grid& g, const Tables& tb, int st
 }
 
 __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* Xs, const double* F, double* R,
-                           size_t S, const double* wT, double* nu, int* flags, int B, int stage, int tms,
+                           size_t S, const double* wT, double* nu, int* flags, int* err, int B, int stage, int tms,
                            const double* ra, const int* nsteps, int stepidx, int blk) {
   extern __shared__ double sbuf[];
   const int mt = (g.nm + tms - 1) / tms;
@@ -934,6 +935,9 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
   const int p = rem / mt;
   const int m0 = (rem - p * mt) * tms;
   if (b >= B || !slice_active_at(nsteps, stepidx, b)) return;   // uniform per block
+  // a transform of this state gave up waiting (the tensor-core kernels): leave
+  // the state as it was at the start of the failing step
+  if (flags[b] & kFlagTimeout) return;
   const int nq = g.nq;
   const int W = 2 * tms;
   const int ncol = 2 * min(tms, g.nm - m0);
@@ -1046,13 +1050,17 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
     }
     __syncthreads();
   }
-  if (!ok) flags[b] = 1;
+  if (!ok) {
+    atomicOr(flags + b, kFlagNonFinite);
+    atomicOr(err, kFlagNonFinite);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, double* Xs, const double* F, double* R,
-                                               size_t S, const double* wT, double* nu, int* flags, int B, int stage,
-                                               int tms, const double* ra, const int* nsteps, const int* step) {
-  solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, B, stage, tms, ra, nsteps, nsteps ? *step : 0, blockIdx.x);
+                                               size_t S, const double* wT, double* nu, int* flags, int* err, int B,
+                                               int stage, int tms, const double* ra, const int* nsteps,
+                                               const int* step) {
+  solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, err, B, stage, tms, ra, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
 // Modes per k_solve block.  Every column's arithmetic is independent of the
@@ -1247,7 +1255,7 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
   k_solve<<<(unsigned)(B * 2 * mtiles), solve_threads(g, tms), solve_smem(g, B), s>>>(
-      g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags, B, stage, tms, w.ra, w.nsteps, w.step);
+      g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags, w.err, B, stage, tms, w.ra, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);
   return cudaGetLastError();
@@ -1269,9 +1277,9 @@ cudaError_t launch_advance_loop(const Work& w, cudaGraphConditionalHandle loop, 
 // Diagnostics.
 // ---------------------------------------------------------------------------
 __global__ void k_nu_final(Grid g, const double* cc, const double* X, size_t S, const double* wT, double* nu,
-                           const int* nsteps, int B) {
+                           const int* nsteps, const int* flags, int B) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B || nsteps[b] <= 0) return;
+  if (b >= B || nsteps[b] <= 0 || (flags[b] & kFlagTimeout)) return;
   const double* X0 = X + (size_t)b * S;
   double cond = 0.0;
   for (int n = 1; n < g.Nz; n += 2) cond -= 2.0 * X0[soff(g, 0, n, 0)];
@@ -1284,7 +1292,7 @@ cudaError_t launch_nu_final(const Grid& g, const Tables& t, const Work& w, const
                             cudaStream_t s) {
   cudaError_t e = launch_explicit(g, t, w, X, B, true, s);
   if (e != cudaSuccess) return e;
-  k_nu_final<<<nblk(B, 128), 128, 0, s>>>(g, t.cc, X, state_doubles(g), w.wT, nu, w.nsteps, B);
+  k_nu_final<<<nblk(B, 128), 128, 0, s>>>(g, t.cc, X, state_doubles(g), w.wT, nu, w.nsteps, w.flags, B);
   count();
   return cudaGetLastError();
 }
@@ -1638,39 +1646,49 @@ cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, con
 // device.  Its device address is looked up once per device, with that device
 // current, on the first call there.
 // ---------------------------------------------------------------------------
-constexpr size_t kStaticScratchDoubles = (size_t)3 << 17;   // 3 MiB
-static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+static __device__ __align__(256) double g_static_scratch[kStaticScratchCapacity];
 constexpr int kMaxDevices = 64;
-static double* g_static_ptr[kMaxDevices] = {};
+static std::atomic<double*> g_static_ptr[kMaxDevices] = {};
 
+// Layout: Z, Q, the <wT>_x profile (Mz rounded up to even), then 8 doubles:
+// the three Nusselt numbers and, in the fifth, the int error bits of the call.
 size_t static_scratch_doubles_needed(const Grid& g) {
   return z_doubles(g) + q_doubles(g) + (size_t)((g.Mz + 1) & ~1) + 8;
 }
 
 cudaError_t launch_nusselt_static(const Grid& g, const Tables& t, const double* X, double* host_out3,
-                                  cudaStream_t s) {
+                                  int* host_flags, cudaStream_t s) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (g_static_ptr[dev] == nullptr) {
-    double* ptr = nullptr;
-    e = cudaGetSymbolAddress((void**)&ptr, g_static_scratch);
+  double* base = g_static_ptr[dev].load();
+  if (base == nullptr) {
+    // two threads may both look it up; they store the same address
+    e = cudaGetSymbolAddress((void**)&base, g_static_scratch);
     if (e != cudaSuccess) return e;
-    g_static_ptr[dev] = ptr;
+    g_static_ptr[dev].store(base);
   }
-  double* base = g_static_ptr[dev];
   Work w{};
   w.Z = base;
   w.Q = w.Z + z_doubles(g);
   w.wT = w.Q + q_doubles(g);
   w.small = w.wT + ((g.Mz + 1) & ~1);
+  w.flags = reinterpret_cast<int*>(w.small + 4);   // the call's error bits (the tensor-core waits)
+  w.err = w.flags;
   w.prof = nullptr;
-  e = launch_nusselt(g, t, w, X, w.small, s);       // every element it reads is written first
+  e = cudaMemsetAsync(w.flags, 0, sizeof(int), s);   // the only element read before this call writes it
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(host_out3, w.small, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = launch_nusselt(g, t, w, X, w.small, s);
   if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(s);
+  double res[5];
+  e = cudaMemcpyAsync(res, w.small, sizeof(res), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < 3; ++i) host_out3[i] = res[i];
+  std::memcpy(host_flags, &res[4], sizeof(int));
+  return cudaSuccess;
 }
 
 }  // namespace rbc

@@ -33,7 +33,7 @@ namespace {
 constexpr int kTileN = 64;       // columns per CTA (32 Fourier modes x re/im)
 constexpr int kTileM = 128;      // rows per MMA tile
 constexpr int kChunkK = 32;      // TF32 elements per 128-byte swizzle row
-constexpr long kWaitLimit = 1L << 24;
+constexpr long long kWaitLimit = 1LL << 24;   // default spin limit of a bounded wait
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -71,10 +71,11 @@ __device__ __forceinline__ void commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar)));
 }
 
-// bounded wait for the completion of phase `parity` of an mbarrier
-__device__ __forceinline__ bool wait_parity(uint64_t* mbar, uint32_t parity) {
+// bounded wait for the completion of phase `parity` of an mbarrier: at most
+// `limit` polls (limit 0: gives up at once)
+__device__ __forceinline__ bool wait_parity(uint64_t* mbar, uint32_t parity, long long limit) {
   uint32_t done = 0;
-  for (long it = 0; it < kWaitLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -105,7 +106,36 @@ __device__ __forceinline__ void store_c(float* Zb, const Grid& g, int field, int
   *reinterpret_cast<float2*>(Zb + field * fs + ((size_t)j * g.nm + m) * 2) = make_float2(re, im);
 }
 
+// Spin limit of the waits that wait for MMAs to complete before the kernel goes
+// on (set by tc_set_wait_limit; tests lower it to make the waits give up).
+__device__ long long g_wait_limit = kWaitLimit;
+
+// Error bits of a state and of its handle (kFlagTimeout when a wait gave up).
+__device__ __forceinline__ void flag_timeout(int* flags, int* err, int b) {
+  atomicOr(flags + b, kFlagTimeout);
+  if (err) atomicOr(err, kFlagTimeout);
+}
+
+// Before tensor memory is freed, thread 0 waits (with the default limit, never
+// the lowered one) for the commits it issued on the two A buffers, so no MMA
+// is still in flight when the kernel releases its tensor memory and exits.
+// use[i] / issued[i]: completions observed / commits issued on mbarrier i
+// (0, 1: the A buffers; 2: the accumulator).  A wait that gave up observed
+// nothing, so the phases are drained in order.
+__device__ __forceinline__ void drain(uint64_t* mbar, uint32_t* use, const uint32_t* issued) {
+  for (int bb = 0; bb < 3; ++bb)
+    while (use[bb] < issued[bb]) {
+      if (!wait_parity(&mbar[bb], use[bb] & 1, kWaitLimit)) break;
+      use[bb]++;
+    }
+}
+
 }  // namespace
+
+cudaError_t tc_set_wait_limit(long long limit) {
+  const long long v = limit < 0 ? kWaitLimit : limit;
+  return cudaMemcpyToSymbol(g_wait_limit, &v, sizeof(v));
+}
 
 // Number of 128-row tiles and K-chunks of the operator images (host and device agree).
 __host__ __device__ int tc_zinv_mtiles(const Grid& g, int nops) { return (nops * g.Mz + kTileM - 1) / kTileM; }
@@ -157,7 +187,7 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
                                                  const float* __restrict__ Alo_psi, const float* __restrict__ Ahi_T,
                                                  const float* __restrict__ Alo_T, const double* __restrict__ X,
                                                  size_t S, float* __restrict__ Z, int B, const int* nsteps,
-                                                 const int* step, int* flags) {
+                                                 const int* step, int* flags, int* err) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t mbar[3];   // 0, 1: A-chunk buffers free; 2: accumulator ready
@@ -220,9 +250,9 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
-  uint32_t use[2] = {0, 0};                   // completions of each A buffer already waited for
-  uint32_t issued[2] = {0, 0};                // commits issued on each A buffer
-  uint32_t acc_phase = 0;
+  const long long limit = g_wait_limit;
+  uint32_t use[3] = {0, 0, 0};                // completions observed: A buffers 0, 1, accumulator
+  uint32_t issued[3] = {0, 0, 0};             // commits issued on them
   bool ok = true;
   float* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
   const int rows_per_j = nops, jper = kTileM / nops;
@@ -230,8 +260,9 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
     for (int c = 0; c < kc && ok; ++c) {
       const int gidx = t * kc + c, buf = gidx & 1;
       if (gidx >= 2) {                        // buffer free once its previous MMAs completed
-        ok = wait_parity(&mbar[buf], use[buf] & 1);
-        use[buf]++;
+        const bool done = wait_parity(&mbar[buf], use[buf] & 1, limit);
+        if (done) use[buf]++;
+        ok = __syncthreads_and(done) != 0;    // one decision for the whole block
         if (!ok) break;
       }
       unsigned char* ah = sA + (size_t)buf * 2 * kTileM * 128;
@@ -259,11 +290,13 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
         if (c == kc - 1) commit(&mbar[2]);
       }
       issued[buf]++;
+      if (c == kc - 1) issued[2]++;
     }
     if (!ok) break;
     // accumulator of tile t ready
-    ok = wait_parity(&mbar[2], acc_phase & 1);
-    acc_phase++;
+    const bool acc_done = wait_parity(&mbar[2], use[2] & 1, limit);
+    if (acc_done) use[2]++;
+    ok = __syncthreads_and(acc_done) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok) break;
     const int r = warp * 32 + lane;           // tile row = TMEM lane
@@ -328,15 +361,8 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
     __syncthreads();                          // accumulator read before the next tile overwrites it
     asm volatile("tcgen05.fence::after_thread_sync;");
   }
-  if (!ok && tid == 0) flags[b] = 2;          // a bounded wait gave up
-  // drain: let outstanding MMAs finish (bounded) before freeing tensor memory
-  if (tid == 0) {
-    for (int bb = 0; bb < 2; ++bb)
-      while (use[bb] < issued[bb]) {
-        if (!wait_parity(&mbar[bb], use[bb] & 1)) break;
-        use[bb]++;
-      }
-  }
+  if (!ok && tid == 0) flag_timeout(flags, err, b);   // a bounded wait gave up
+  if (tid == 0) drain(mbar, use, issued);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -396,7 +422,7 @@ bool tc_zfwd_supported(const Grid& g) { return tc_zfwd_smem_bytes(g) <= 200 * 10
 __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict__ Whi0, const float* __restrict__ Wlo0,
                                                  const float* __restrict__ Whi1, const float* __restrict__ Wlo1,
                                                  const float* __restrict__ Q, double* __restrict__ F, size_t S, int B,
-                                                 const int* nsteps, const int* step, int* flags) {
+                                                 const int* nsteps, const int* step, int* flags, int* err) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t mbar[3];   // 0, 1: A-chunk buffers free; 2: accumulator ready
@@ -469,17 +495,18 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
-  uint32_t use[2] = {0, 0};
-  uint32_t issued[2] = {0, 0};
-  uint32_t acc_phase = 0;
+  const long long limit = g_wait_limit;
+  uint32_t use[3] = {0, 0, 0};                // completions observed: A buffers 0, 1, accumulator
+  uint32_t issued[3] = {0, 0, 0};             // commits issued on them
   bool ok = true;
   double* Fb = F + (size_t)b * S;
   for (int t = 0; t < mtiles && ok; ++t) {
     for (int c = 0; c < kc && ok; ++c) {
       const int gidx = t * kc + c, buf = gidx & 1;
       if (gidx >= 2) {                        // buffer free once its previous MMAs completed
-        ok = wait_parity(&mbar[buf], use[buf] & 1);
-        use[buf]++;
+        const bool done = wait_parity(&mbar[buf], use[buf] & 1, limit);
+        if (done) use[buf]++;
+        ok = __syncthreads_and(done) != 0;    // one decision for the whole block
         if (!ok) break;
       }
       unsigned char* ah = sA + (size_t)buf * 2 * kTileM * 128;
@@ -507,10 +534,12 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
         if (c == kc - 1) commit(&mbar[2]);
       }
       issued[buf]++;
+      if (c == kc - 1) issued[2]++;
     }
     if (!ok) break;
-    ok = wait_parity(&mbar[2], acc_phase & 1);
-    acc_phase++;
+    const bool acc_done = wait_parity(&mbar[2], use[2] & 1, limit);
+    if (acc_done) use[2]++;
+    ok = __syncthreads_and(acc_done) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok) break;
     const int n = 2 * (t * kTileM + warp * 32 + lane) + p;   // tile row = TMEM lane
@@ -529,14 +558,8 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
     __syncthreads();                          // accumulator read before the next tile overwrites it
     asm volatile("tcgen05.fence::after_thread_sync;");
   }
-  if (!ok && tid == 0) flags[b] = 2;          // a bounded wait gave up
-  if (tid == 0) {
-    for (int bb = 0; bb < 2; ++bb)
-      while (use[bb] < issued[bb]) {
-        if (!wait_parity(&mbar[bb], use[bb] & 1)) break;
-        use[bb]++;
-      }
-  }
+  if (!ok && tid == 0) flag_timeout(flags, err, b);   // a bounded wait gave up
+  if (tid == 0) drain(mbar, use, issued);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -554,7 +577,7 @@ cudaError_t launch_zfwd_tc(const Grid& g, const Tables& t, const Work& w, int B,
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
   k_zfwd_tc<<<(unsigned)(B * 2 * 2 * ntile), 128, smem, s>>>(g, t.tcW_hi[0], t.tcW_lo[0], t.tcW_hi[1], t.tcW_lo[1],
                                                              reinterpret_cast<const float*>(w.Q), w.F,
-                                                             state_doubles(g), B, w.nsteps, w.step, w.flags);
+                                                             state_doubles(g), B, w.nsteps, w.step, w.flags, w.err);
   return cudaGetLastError();
 }
 
@@ -570,7 +593,7 @@ cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const 
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
   k_zinv_tc<<<(unsigned)(B * 2 * ntile), 128, smem, s>>>(g, t.tcA_psi_hi, t.tcA_psi_lo, t.tcA_T_hi, t.tcA_T_lo, X,
                                                          state_doubles(g), reinterpret_cast<float*>(w.Z), B, ns,
-                                                         w.step, w.flags);
+                                                         w.step, w.flags, w.err);
   return cudaGetLastError();
 }
 

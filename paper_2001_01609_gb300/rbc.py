@@ -23,7 +23,7 @@ EXPORTS = [
     "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate", "rbc_profile",
     "rbc_profile_read", "rbc_launch_count", "rbc_nusselt_static", "rbc_step_batch_ra", "rbc_restrict",
     "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff", "parareal_set_schedule", "parareal_coarse_sms",
-    "rbc_diag_size", "rbc_diagnostics",
+    "rbc_diag_size", "rbc_diagnostics", "rbc_set_wait_limit",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -80,6 +80,7 @@ def load():
         "parareal_coarse_sms": (I, [P]),
         "rbc_diag_size": (S, [P]),
         "rbc_diagnostics": (I, [P, P, I, P, P]),
+        "rbc_set_wait_limit": (I, [ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -182,7 +183,9 @@ class Propagator:
             _check(load().rbc_step_batch_ra(self.h, _ptr(states), B, nsp, _dptr(rr), nup, _stream(stream)))
 
     def check_diverged(self, stream=None):
-        return _check(load().rbc_check_diverged(self.h, _stream(stream)), allow=(RBC_EDIVERGED,))
+        """RBC_OK, RBC_EDIVERGED (a non-finite state) or RBC_ETIMEOUT (a bounded
+        device-side wait gave up) since the last check."""
+        return _check(load().rbc_check_diverged(self.h, _stream(stream)), allow=(RBC_EDIVERGED, RBC_ETIMEOUT))
 
     def nusselt(self, state, stream=None):
         out = np.zeros(3)
@@ -248,6 +251,12 @@ def l2_diff(prop, A, Bm, out, stream=None):
                               _stream(stream)))
 
 
+def set_wait_limit(polls):
+    """Test hook: polls before a tensor-core mbarrier wait gives up (0: at once;
+    negative: the default), on the current device."""
+    _check(load().rbc_set_wait_limit(int(polls)))
+
+
 def launch_count():
     return int(load().rbc_launch_count())
 
@@ -301,5 +310,5 @@ class Parareal:
         nu = np.zeros(max_iters)
         st = load().parareal_iterate(self.h, _ptr(U0), _ptr(U), max_iters, ctypes.byref(k), _dptr(de), _dptr(nu),
                                      _stream(stream))
-        _check(st, allow=(RBC_ENOTCONVERGED, RBC_EDIVERGED))
+        _check(st, allow=(RBC_ENOTCONVERGED, RBC_EDIVERGED, RBC_ETIMEOUT))
         return st, k.value, de[: k.value], nu[: k.value]

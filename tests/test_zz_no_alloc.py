@@ -44,6 +44,37 @@ def test_static_scratch_nusselt_matches_rbc_nusselt_on_consecutive_calls():
                 np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-13)
 
 
+def test_static_scratch_nusselt_on_a_fresh_mixed_precision_handle_allocates_nothing():
+    """A mixed-precision handle runs the tensor-core z-inverse, whose bounded
+    waits report through an error word: the call keeps that word in the static
+    array too.  The handle is fresh (it never reserved a workspace) and the
+    device's free memory does not change across the calls."""
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc
+    from paper_2001_01609_gb300.inputs import initial_temperature
+
+    Nx, Nz, Ra = 64, 32, 1e5
+    prep = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, 1e-5, precision=rbc.RBC_MIXED)
+    st = prep.new_states(2)
+    for b in range(2):
+        prep.set_state(st[b], initial_temperature(Nx, Nz, seed=20 + b, amplitude=0.3))
+    prep.step_batch(st, 3)
+    refs = [np.array(prep.nusselt(st[b])) for b in range(2)]   # the allocating entry point
+    status, _ = _static_nusselt(rbc, prep, st[0])               # module and array loaded before measuring
+    assert status == rbc.RBC_OK
+    fresh = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, 1e-5, precision=rbc.RBC_MIXED)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for b in (0, 1):
+        for _ in range(2):                                      # two calls in a row
+            status, out = _static_nusselt(rbc, fresh, st[b])
+            assert status == rbc.RBC_OK
+            np.testing.assert_allclose(out, refs[b], rtol=1e-12, atol=1e-13)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_static_scratch_nusselt_rejects_grids_beyond_its_size():
     from paper_2001_01609_gb300 import rbc
 
