@@ -242,15 +242,22 @@ void parareal_destroy(parareal_t p);
  * RBC_CRIT_FIXED), RBC_ENOTCONVERGED when max_iters ran out, RBC_EDIVERGED on
  * a non-finite state, RBC_ETIMEOUT if a bounded device-side wait of a
  * tensor-core kernel gave up.  Iterations stop after k = nslices, where U^k is the
- * serial fine solution.  Synchronous on `stream` (one small D2H per iteration).
+ * serial fine solution.  Synchronous on `stream` (a few small D2H per iteration).
  *
- * Schedule (the results do not depend on it, bit for bit): the coarse sweep
- * U^0 and the correction sweep (with a second coarse handle) run on two
- * internal streams; the fine sweep runs in groups of slices on internal
- * streams, each group starting as soon as the coarse sweep has produced its
- * inputs; correction step n starts when its fine group and coarse step n are
- * done.  So the three sweeps of an iteration overlap.  `stream` waits for all
- * of it before the norms.  parareal_set_schedule tunes it.                  */
+ * Schedule (the results do not depend on it, bit for bit).  Iteration k's
+ * fine sweep F(U_n^{k-1}) runs in groups of slices; its correction sweep
+ * U_{n+1}^k = F(U_n^{k-1}) + (G(U_n^k) - G(U_n^{k-1})) runs on its own coarse
+ * handle and stream, each step fused with the step's norms (one kernel forms
+ * U_{n+1}^k, the coarse input of the next step, the next iteration's fine
+ * input and ||U_{n+1}^k - U_{n+1}^{k-1}||, ||U_{n+1}^k||).  Every step waits
+ * only for the data it reads: the previous iteration's step n and the fine
+ * group of slice n.  So the sweeps of one iteration overlap, and so do
+ * successive iterations: the host evaluates iteration k (defect, Nu,
+ * criterion) while iterations k+1 .. k+depth are already running; when the
+ * criterion is met their step loops are stopped early and their results
+ * dropped.  The library runs all of this on copies of the caller's handles
+ * (sharing their tables); kernel timing (rbc_profile) of the caller's handles
+ * covers the copies.  parareal_set_schedule and parareal_set_depth tune it.  */
 rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_iters,
                             int* k_done, double* defects, double* nus, cudaStream_t stream);
 
@@ -260,22 +267,29 @@ rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_i
  *                sweep U^0 has finished;
  *  first_group:  size of the first fine group (1 <= first_group <= group);
  *                sizes then double up to group (default ceil(group / 4));
- *  fine_streams: 1 to 4 streams (and fine handles) the groups alternate over
- *                (default 2);
- *  coarse_priority: 1 runs both coarse sweeps on high-priority streams
- *                (default 1);
- *  coarse_sms:   0 (default) shares all SMs; n > 0 gives the two coarse
- *                sweeps a partition of about n SMs of their own (a green
+ *  fine_streams: 1 to 4 streams (and fine handles) per iteration that the
+ *                groups alternate over (default 2);
+ *  coarse_priority: 1 runs the sweeps on the coarse grid on high-priority
+ *                streams (default 1);
+ *  coarse_sms:   0 (default) shares all SMs; n > 0 gives the sweeps on the
+ *                coarse grid a partition of about n SMs of their own (a green
  *                context; rounded up to the device's partition granularity)
  *                and the fine groups the other SMs, so that the latency-bound
  *                coarse kernels never wait for SMs held by fine batches.
- *                While parareal_iterate runs, the fine and coarse handles
- *                capture their step graphs in these partitions; they are
- *                released on return.  RBC_ECUDA if the driver cannot
+ *                The library's copies of the handles capture their step
+ *                graphs in these partitions.  RBC_ECUDA if the driver cannot
  *                partition the device (the schedule is then unchanged).
  * RBC_EINVAL outside these ranges.                                          */
 rbc_status parareal_set_schedule(parareal_t p, int group, int first_group, int fine_streams, int coarse_priority,
                                  int coarse_sms);
+
+/* Iterations parareal_iterate keeps enqueued beyond the one it evaluates
+ * next (0 to 6, default 2).  0 runs one iteration after another; with depth
+ * d, iteration k + 1 .. k + d run while the host waits for iteration k, and
+ * run for nothing (stopped early) when iteration k meets the criterion.
+ * Each extra level holds nslices + 1 and nslices fine states more.  Timing
+ * only; RBC_EINVAL outside [0, 6].                                          */
+rbc_status parareal_set_depth(parareal_t p, int depth);
 
 /* SMs of the coarse partition in use (0: none), -1 for a NULL handle.      */
 int parareal_coarse_sms(parareal_t p);

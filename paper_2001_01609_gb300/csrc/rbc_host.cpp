@@ -316,6 +316,7 @@ struct rbc_s {
   std::vector<int> up_ns;
   std::vector<double> up_ra;
   Prof prof;
+  Prof* profp = nullptr;   // the timing record in use: its own, or its template's (Parareal's copies)
   // Step loops: a graph whose one node is a device-side while loop over the
   // captured RK443 step (4 stages + counter), so a call of any length is one
   // launch.  A few bindings (states, B, nu) are kept, least recently used out.
@@ -343,43 +344,53 @@ struct rbc_s {
 };
 
 struct pr_s {
-  rbc_t fine = nullptr, coarse = nullptr;
+  rbc_t fine = nullptr, coarse = nullptr;   // the caller's handles: grids, time steps, options, tables
   double t0 = 0, t1 = 0;
   int N = 0, nf = 0, nc = 0, criterion = 0;
   double tol = 0;
-  double* d_F = nullptr;      // N fine states: F(U_n^k)
-  double* d_Uold = nullptr;   // N+1 fine states: previous iterate
-  double* d_Gold = nullptr;   // N coarse states: G_coarse(restrict(U_n^k))
-  double* d_C = nullptr;      // 1 coarse state
-  double* d_I = nullptr;      // N doubles: Nu_V integrals of the F sweep
-  double* d_norm = nullptr;   // 2N doubles
-  // Pipelined schedule: the coarse sweep U^0 (caller's stream, `coarse`), the
-  // fine sweep in groups of `group` slices (sF, `fine`) and the correction
-  // sweep (sG, `coarse2`, a second handle on the coarse grid) overlap; events
-  // carry the per-slice dependencies.
-  rbc_t coarse2 = nullptr;
-  double* d_C2 = nullptr;     // 1 coarse state of the correction sweep
+  // Schedule (timing only; the results are the same bit for bit).
   int group = 0;              // largest fine group
   int first_group = 0;        // first fine group
-  int fine_streams = 1;       // fine groups alternate over this many streams
-  int coarse_priority = 0;    // 1: the coarse sweeps run on high-priority streams
+  int fine_streams = 2;       // fine groups of an iteration alternate over this many streams
+  int coarse_priority = 1;    // 1: the sweeps on the coarse grid run on high-priority streams
+  int depth = 2;              // iterations enqueued beyond the one the host evaluates next
   static constexpr int kFineStreams = 4;
-  rbc_t fines[kFineStreams] = {};          // fines[0] = fine; the others are copies of it, made on demand
-  cudaStream_t sF[kFineStreams] = {};      // default priority
-  cudaStream_t sG0 = nullptr, sG = nullptr;        // coarse sweeps, default priority
-  cudaStream_t sG0_hi = nullptr, sG_hi = nullptr;  // the same, high priority
-  std::vector<cudaEvent_t> ev_g0;   // [N] U^0 sweep done with slice n
-  std::vector<cudaEvent_t> ev_f;    // [N] fine group j done
-  cudaEvent_t ev_begin = nullptr, ev_copy = nullptr, ev_gdone = nullptr, ev_g0done = nullptr;
-  cudaEvent_t ev_fdone[kFineStreams] = {};
-  // Optional SM partition: the coarse sweeps on `coarse_sms` SMs of their own
-  // (green context 0), the fine groups on the rest (green context 1), so the
-  // latency-bound coarse kernels never wait for SMs held by fine batches.
+  static constexpr int kMaxDepth = 6;
+  // One slot per iteration in flight: iteration k uses slot k % R, R = depth + 2.
+  // Its sweep on the coarse grid (k = 0: U^0; k >= 1: the correction of Eq. 20)
+  // runs on the slot's coarse handle and stream; its fine groups on the slot's
+  // fine handles and streams.  All handles are the library's own copies of the
+  // caller's (sharing their tables), so that their step loops can be cancelled.
+  struct Slot {
+    rbc_t coarse = nullptr;
+    rbc_t fines[kFineStreams] = {};
+    cudaStream_t sC = nullptr, sC_hi = nullptr;   // the sweep: default / high priority
+    cudaStream_t sF[kFineStreams] = {};
+    cudaStream_t pC = nullptr;                    // the same in the SM partition (gctx[0], gctx[1])
+    cudaStream_t pF[kFineStreams] = {};
+    double* U = nullptr;        // [N+1] fine states: U^k
+    double* Fin = nullptr;      // [N] fine states: inputs, then results, of the iteration's fine sweep
+    double* C = nullptr;        // 1 coarse state: the sweep's coarse state
+    double* I = nullptr;        // [N] Nu_V integrals of the fine sweep
+    double* norms = nullptr;    // [N][2]: ||T(U^k_{n+1} - U^{k-1}_{n+1})||^2, ||T(U^k_{n+1})||^2
+    double* partial = nullptr;  // block sums of the correction kernel
+    unsigned* counter = nullptr;
+    std::vector<cudaEvent_t> ev_step;    // [N] sweep step n done
+    std::vector<cudaEvent_t> ev_group;   // [N] fine group j done
+    std::vector<int> slice_group;        // fine group of each slice
+    cudaEvent_t ev_join[1 + kFineStreams] = {};
+    bool busy = false;                   // has work in the current call
+  };
+  std::vector<Slot> slots;
+  double* d_Gold = nullptr;   // [N] coarse states G(U_n), updated in place by each sweep
+  int* d_cancel = nullptr;    // read by the slots' step loops: set, they stop early
+  cudaStream_t sCancel = nullptr;
+  cudaEvent_t ev_begin = nullptr, ev_cancel = nullptr;
+  // Optional SM partition: the sweeps on the coarse grid on `coarse_sms` SMs of
+  // their own (green context 0), the fine groups on the rest (green context 1).
   int coarse_sms = 0;
   CUgreenCtx green[2] = {};
   CUcontext gctx[2] = {};
-  cudaStream_t pG0 = nullptr, pG = nullptr;   // in gctx[0]
-  cudaStream_t pF[kFineStreams] = {};         // in gctx[1]
 };
 
 static void release_context(rbc_t h, CUcontext ctx);
@@ -388,15 +399,18 @@ static void release_context(rbc_t h, CUcontext ctx);
 // its handles captured in it, and the green contexts.
 static void drop_partition(pr_s* p) {
   if (!p->gctx[0]) return;
-  for (cudaStream_t* st : {&p->pG0, &p->pG, &p->pF[0], &p->pF[1], &p->pF[2], &p->pF[3]})
-    if (*st) {
-      cudaStreamSynchronize(*st);
-      cudaStreamDestroy(*st);
-      *st = nullptr;
-    }
+  for (auto& S : p->slots)
+    for (cudaStream_t* st : {&S.pC, &S.pF[0], &S.pF[1], &S.pF[2], &S.pF[3]})
+      if (*st) {
+        cudaStreamSynchronize(*st);
+        cudaStreamDestroy(*st);
+        *st = nullptr;
+      }
   for (int i = 0; i < 2; ++i) {
-    for (rbc_t h : {p->coarse, p->coarse2}) release_context(h, p->gctx[i]);
-    for (rbc_t h : p->fines) release_context(h, p->gctx[i]);
+    for (auto& S : p->slots) {
+      release_context(S.coarse, p->gctx[i]);
+      for (rbc_t h : S.fines) release_context(h, p->gctx[i]);
+    }
     if (p->green[i]) driver_api().green_destroy(p->green[i]);
     p->green[i] = nullptr;
     p->gctx[i] = nullptr;
@@ -423,25 +437,6 @@ static rbc_status make_partition(pr_s* p, int coarse_sms) {
       drop_partition(p);
       return fail(RBC_ECUDA, "green context creation");
     }
-  bool ok = true;
-  {
-    CtxScope scope(p->gctx[0]);
-    int lo = 0, hi = 0;
-    ok = scope.ok() && cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
-         cudaStreamCreateWithPriority(&p->pG0, cudaStreamNonBlocking, hi) == cudaSuccess &&
-         cudaStreamCreateWithPriority(&p->pG, cudaStreamNonBlocking, hi) == cudaSuccess;
-  }
-  if (ok) {
-    CtxScope scope(p->gctx[1]);
-    ok = scope.ok();
-    for (int i = 0; ok && i < pr_s::kFineStreams; ++i)
-      ok = cudaStreamCreateWithFlags(&p->pF[i], cudaStreamNonBlocking) == cudaSuccess;
-  }
-  if (!ok) {
-    cudaGetLastError();
-    drop_partition(p);
-    return fail(RBC_ECUDA, "streams of the SM partition");
-  }
   p->coarse_sms = (int)grp.sm.smCount;
   return RBC_OK;
 }
@@ -748,6 +743,7 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   rbc_t h = new (std::nothrow) rbc_s();
   if (!h) return fail(RBC_ENOMEM, "host allocation");
   h->opts = o;
+  h->profp = &h->prof;
   h->use_graphs = (o.eager == 0);
   cudaGetDevice(&h->device);
   Grid& g = h->g;
@@ -853,7 +849,7 @@ extern "C" rbc_status rbc_reserve(rbc_t h, int B) {
     cudaGetLastError();
     return fail(RBC_ECUDA, "workspace counters");
   }
-  w.prof = &h->prof;
+  w.prof = h->profp;
   return RBC_OK;
 }
 
@@ -1099,12 +1095,13 @@ static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps
   // Steps launched one kernel at a time: all of them while profiling every
   // call; the first kProfileSampleSteps of a sampled call (the rest continue
   // on the graph loop from the same device step counter); none otherwise.
-  const int eager = !h->prof.on ? 0 : h->prof.once ? std::min(maxs, kProfileSampleSteps) : maxs;
+  Prof& pr = *h->profp;
+  const int eager = !pr.on ? 0 : pr.once ? std::min(maxs, kProfileSampleSteps) : maxs;
   for (int st = 0; st < eager; ++st) {
     for (int stage = 1; stage <= 4; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
     CK(launch_advance(w, stream));
   }
-  if (h->prof.once) h->prof.on = false;
+  if (pr.once) pr.on = false;
   const int rest = maxs - eager;
   if (rest >= 2 && h->use_graphs) {
     cudaGraphExec_t ex = nullptr;
@@ -1119,7 +1116,7 @@ static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps
     }
   }
   if (maxs > 0) CK(launch_nu_final(h->g, h->t, w, X, B, nu, stream));
-  if (h->prof.once) h->prof.on = h->prof.once = false;   // sampled profiling: this call only (its first steps)
+  if (pr.once) pr.on = pr.once = false;   // sampled profiling: this call only (its first steps)
   return RBC_OK;
 }
 
@@ -1265,46 +1262,124 @@ static bool whole_steps(double len, double dt, int* n) {
   return true;
 }
 
+// A handle of the library's own on the grid, time step and options of `src`,
+// sharing its device tables (src must outlive it), with a workspace of its own.
+static rbc_status clone_handle(rbc_t src, rbc_t* out) {
+  rbc_t h = new (std::nothrow) rbc_s();
+  if (!h) return fail(RBC_ENOMEM, "host allocation");
+  h->g = src->g;
+  h->opts = src->opts;
+  h->device = src->device;
+  h->max_residual = src->max_residual;
+  h->t = src->t;                  // d_tables stays null: the tables are src's
+  h->profp = src->profp;          // kernel timing goes to the template's record
+  h->use_graphs = src->use_graphs;
+  *out = h;
+  return RBC_OK;
+}
+
+static void destroy_slot(pr_s::Slot& S) {
+  for (cudaStream_t st : {S.sC, S.sC_hi, S.sF[0], S.sF[1], S.sF[2], S.sF[3], S.pC, S.pF[0], S.pF[1], S.pF[2], S.pF[3]})
+    if (st) cudaStreamSynchronize(st);
+  for (cudaEvent_t e : S.ev_step)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : S.ev_group)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : S.ev_join)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t st : {S.sC, S.sC_hi, S.sF[0], S.sF[1], S.sF[2], S.sF[3], S.pC, S.pF[0], S.pF[1], S.pF[2], S.pF[3]})
+    if (st) cudaStreamDestroy(st);
+  rbc_destroy(S.coarse);
+  for (rbc_t h : S.fines) rbc_destroy(h);
+  for (void* b : {(void*)S.U, (void*)S.Fin, (void*)S.C, (void*)S.I, (void*)S.norms, (void*)S.partial, (void*)S.counter})
+    cudaFree(b);
+  S = pr_s::Slot{};
+}
+
 extern "C" void parareal_destroy(parareal_t p) {
   if (!p) return;
   drop_partition(p);
-  for (cudaStream_t st : {p->sF[0], p->sF[1], p->sF[2], p->sF[3], p->sG0, p->sG, p->sG0_hi, p->sG_hi})
-    if (st) cudaStreamSynchronize(st);
-  for (cudaEvent_t e : p->ev_g0) cudaEventDestroy(e);
-  for (cudaEvent_t e : p->ev_f) cudaEventDestroy(e);
-  for (cudaEvent_t e : {p->ev_begin, p->ev_copy, p->ev_gdone, p->ev_g0done})
+  if (p->sCancel) cudaStreamSynchronize(p->sCancel);
+  for (auto& S : p->slots) destroy_slot(S);
+  for (cudaEvent_t e : {p->ev_begin, p->ev_cancel})
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : p->ev_fdone)
-    if (e) cudaEventDestroy(e);
-  for (cudaStream_t st : {p->sF[0], p->sF[1], p->sF[2], p->sF[3], p->sG0, p->sG, p->sG0_hi, p->sG_hi})
-    if (st) cudaStreamDestroy(st);
-  for (int i = 1; i < pr_s::kFineStreams; ++i) rbc_destroy(p->fines[i]);
-  rbc_destroy(p->coarse2);
-  cudaFree(p->d_C2);
-  cudaFree(p->d_F);
-  cudaFree(p->d_Uold);
+  if (p->sCancel) cudaStreamDestroy(p->sCancel);
   cudaFree(p->d_Gold);
-  cudaFree(p->d_C);
-  cudaFree(p->d_I);
-  cudaFree(p->d_norm);
+  cudaFree(p->d_cancel);
   delete p;
 }
 
-// Fine handles 1 .. n-1 (copies of the caller's fine handle, for concurrent fine groups).
-static rbc_status ensure_fines(pr_s* p, int n) {
-  const Grid& gf = p->fine->g;
-  for (int i = 1; i < n; ++i) {
-    if (p->fines[i]) continue;
-    rbc_status s = rbc_create(gf.Ra, gf.Pr, gf.Lx, gf.Nx, gf.Nz, gf.dt, &p->fine->opts, &p->fines[i]);
-    if (s == RBC_OK) s = rbc_reserve(p->fines[i], p->N);
-    if (s != RBC_OK) {
-      rbc_destroy(p->fines[i]);
-      p->fines[i] = nullptr;
-      return s;
+// Buffers, handles, streams and events of slot i, for `fine_streams` fine
+// streams and the current partition (made on first use).
+static rbc_status ensure_slot(pr_s* p, int i) {
+  if ((int)p->slots.size() <= i) p->slots.resize(i + 1);
+  pr_s::Slot& S = p->slots[i];
+  const Grid &gf = p->fine->g, &gc = p->coarse->g;
+  const int N = p->N;
+  const size_t Bf = state_doubles(gf) * sizeof(double), Bc = state_doubles(gc) * sizeof(double);
+  if (!S.U) {
+    bool ok = cudaMalloc(&S.U, (N + 1) * Bf) == cudaSuccess && cudaMalloc(&S.Fin, N * Bf) == cudaSuccess &&
+              cudaMalloc(&S.C, Bc) == cudaSuccess && cudaMalloc(&S.I, N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&S.norms, 2 * N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&S.partial, 2 * correct_norm_blocks(gf) * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&S.counter, sizeof(unsigned)) == cudaSuccess &&
+              cudaMemset(S.counter, 0, sizeof(unsigned)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      destroy_slot(S);
+      return fail(RBC_ENOMEM, "Parareal buffers of an iteration");
     }
+    S.ev_step.assign(N, nullptr);
+    S.ev_group.assign(N, nullptr);
+    S.slice_group.assign(N, 0);
+    for (auto* v : {&S.ev_step, &S.ev_group})
+      for (cudaEvent_t& e : *v) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (cudaEvent_t& e : S.ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  if (!S.coarse) {
+    rbc_status s = clone_handle(p->coarse, &S.coarse);
+    if (s == RBC_OK) s = rbc_reserve(S.coarse, 1);
+    if (s != RBC_OK) return s;
+    S.coarse->w.cancel = p->d_cancel;
+  }
+  for (int j = 0; j < p->fine_streams; ++j)
+    if (!S.fines[j]) {
+      rbc_status s = clone_handle(p->fine, &S.fines[j]);
+      if (s == RBC_OK) s = rbc_reserve(S.fines[j], std::min(p->N, p->group));
+      if (s != RBC_OK) return s;
+      S.fines[j]->w.cancel = p->d_cancel;
+    }
+  int lo = 0, hi = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  if (!S.sC) CK(cudaStreamCreateWithFlags(&S.sC, cudaStreamNonBlocking));
+  if (!S.sC_hi) CK(cudaStreamCreateWithPriority(&S.sC_hi, cudaStreamNonBlocking, hi));
+  for (int j = 0; j < p->fine_streams; ++j)
+    if (!S.sF[j]) CK(cudaStreamCreateWithFlags(&S.sF[j], cudaStreamNonBlocking));
+  if (p->gctx[0]) {
+    {
+      CtxScope scope(p->gctx[0]);
+      if (!scope.ok()) return fail(RBC_ECUDA, "cannot enter the SM partition's context");
+      int l2 = 0, h2 = 0;
+      if (!S.pC)
+        CK(cudaDeviceGetStreamPriorityRange(&l2, &h2) == cudaSuccess
+               ? cudaStreamCreateWithPriority(&S.pC, cudaStreamNonBlocking, h2)
+               : cudaErrorUnknown);
+    }
+    CtxScope scope(p->gctx[1]);
+    if (!scope.ok()) return fail(RBC_ECUDA, "cannot enter the SM partition's context");
+    for (int j = 0; j < p->fine_streams; ++j)
+      if (!S.pF[j]) CK(cudaStreamCreateWithFlags(&S.pF[j], cudaStreamNonBlocking));
+  }
+  // handles capture their step graphs in the partition they run in
+  S.coarse->bind_ctx = p->gctx[0];
+  for (int j = 0; j < p->fine_streams; ++j) S.fines[j]->bind_ctx = p->gctx[1];
   return RBC_OK;
 }
+
+static cudaStream_t sweep_stream(const pr_s* p, const pr_s::Slot& S) {
+  return p->gctx[0] ? S.pC : p->coarse_priority ? S.sC_hi : S.sC;
+}
+static cudaStream_t fine_stream(const pr_s* p, const pr_s::Slot& S, int j) { return p->gctx[0] ? S.pF[j] : S.sF[j]; }
 
 extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, double t1, int nslices, int criterion,
                                       double tol, parareal_t* out) {
@@ -1331,56 +1406,28 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
   p->nc = nc;
   p->criterion = criterion;
   p->tol = tol;
-  const size_t Sf = state_doubles(gf) * sizeof(double), Sc = state_doubles(gc) * sizeof(double);
-  const int N = nslices;
-  bool ok = cudaMalloc(&p->d_F, N * Sf) == cudaSuccess && cudaMalloc(&p->d_Uold, (N + 1) * Sf) == cudaSuccess &&
-            cudaMalloc(&p->d_Gold, N * Sc) == cudaSuccess && cudaMalloc(&p->d_C, Sc) == cudaSuccess &&
-            cudaMalloc(&p->d_I, N * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&p->d_norm, 2 * (N + 1) * sizeof(double)) == cudaSuccess;
+  // default schedule: largest fine group N/4, first group a quarter of that,
+  // groups alternating over two fine streams, sweeps on the coarse grid at high
+  // priority, two iterations enqueued ahead of the one being evaluated
+  p->group = std::max(1, (nslices + 3) / 4);
+  p->first_group = std::max(1, (p->group + 3) / 4);
+  const size_t Bc = state_doubles(gc) * sizeof(double);
+  bool ok = cudaMalloc(&p->d_Gold, nslices * Bc) == cudaSuccess && cudaMalloc(&p->d_cancel, sizeof(int)) == cudaSuccess &&
+            cudaMemset(p->d_cancel, 0, sizeof(int)) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&p->sCancel, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&p->ev_begin, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&p->ev_cancel, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     parareal_destroy(p);
     return fail(RBC_ENOMEM, "Parareal buffers");
   }
-  rbc_status s = rbc_reserve(fine, N);
-  if (s == RBC_OK) s = rbc_reserve(coarse, 1);
-  if (s == RBC_OK)
-    s = rbc_create(gc.Ra, gc.Pr, gc.Lx, gc.Nx, gc.Nz, gc.dt, &coarse->opts, &p->coarse2);
-  if (s == RBC_OK) s = rbc_reserve(p->coarse2, 1);
-  p->fines[0] = fine;
-  if (s == RBC_OK) s = ensure_fines(p, 2);
+  rbc_status s = ensure_slot(p, 0);   // the coarse sweep U^0 and the first iteration
+  if (s == RBC_OK) s = ensure_slot(p, 1);
   if (s != RBC_OK) {
     parareal_destroy(p);
     return s;
   }
-  int prio_lo = 0, prio_hi = 0;
-  bool ok2 = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) == cudaSuccess &&
-             cudaMalloc(&p->d_C2, Sc) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&p->sG0, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&p->sG, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithPriority(&p->sG0_hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
-             cudaStreamCreateWithPriority(&p->sG_hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess;
-  for (int i = 0; ok2 && i < pr_s::kFineStreams; ++i)
-    ok2 = cudaStreamCreateWithFlags(&p->sF[i], cudaStreamNonBlocking) == cudaSuccess &&
-          cudaEventCreateWithFlags(&p->ev_fdone[i], cudaEventDisableTiming) == cudaSuccess;
-  p->ev_g0.assign(N, nullptr);
-  p->ev_f.assign(N, nullptr);
-  for (int n = 0; ok2 && n < N; ++n)
-    ok2 = cudaEventCreateWithFlags(&p->ev_g0[n], cudaEventDisableTiming) == cudaSuccess &&
-          cudaEventCreateWithFlags(&p->ev_f[n], cudaEventDisableTiming) == cudaSuccess;
-  for (cudaEvent_t* e : {&p->ev_begin, &p->ev_copy, &p->ev_gdone, &p->ev_g0done})
-    ok2 = ok2 && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
-  if (!ok2) {
-    cudaGetLastError();
-    parareal_destroy(p);
-    return fail(RBC_ENOMEM, "Parareal streams and events");
-  }
-  // default schedule: largest fine group N/4, first group a quarter of that,
-  // groups alternating over two fine streams, coarse sweeps at high priority
-  p->group = std::max(1, (N + 3) / 4);
-  p->first_group = std::max(1, (p->group + 3) / 4);
-  p->fine_streams = 2;
-  p->coarse_priority = 1;
   *out = p;
   return RBC_OK;
 }
@@ -1390,8 +1437,6 @@ extern "C" rbc_status parareal_set_schedule(parareal_t p, int group, int first_g
   if (!p || group < 1 || first_group < 1 || first_group > group || fine_streams < 1 ||
       fine_streams > pr_s::kFineStreams || coarse_priority < 0 || coarse_priority > 1 || coarse_sms < 0)
     return fail(RBC_EINVAL, "bad schedule");
-  rbc_status fs = ensure_fines(p, fine_streams);
-  if (fs != RBC_OK) return fs;
   if (coarse_sms != p->coarse_sms) {
     drop_partition(p);
     if (coarse_sms > 0) {
@@ -1403,6 +1448,16 @@ extern "C" rbc_status parareal_set_schedule(parareal_t p, int group, int first_g
   p->first_group = std::min(first_group, p->group);
   p->fine_streams = fine_streams;
   p->coarse_priority = coarse_priority;
+  for (int i = 0; i < (int)p->slots.size(); ++i) {
+    rbc_status s = ensure_slot(p, i);
+    if (s != RBC_OK) return s;
+  }
+  return RBC_OK;
+}
+
+extern "C" rbc_status parareal_set_depth(parareal_t p, int depth) {
+  if (!p || depth < 0 || depth > pr_s::kMaxDepth) return fail(RBC_EINVAL, "depth must be in [0, %d]", pr_s::kMaxDepth);
+  p->depth = depth;
   return RBC_OK;
 }
 
@@ -1426,158 +1481,190 @@ static std::vector<int> fine_group_starts(const pr_s* p, int n0) {
   return a;
 }
 
-// Launch the fine groups, group j on stream/handle j % kFineStreams after
-// `wait_for(a, cnt)` (an event of the stream that writes its inputs); group j
-// records ev_f[j], and slice_group[n] receives the group of slice n.
-template <class WaitFor>
-static rbc_status fine_groups(parareal_t p, const cudaStream_t* sF, int n0, const std::vector<int>& nfv,
-                              std::vector<int>& slice_group, WaitFor wait_for) {
-  const size_t Sf = state_doubles(p->fine->g);
+// Enqueue iteration k: for k = 0 the coarse sweep U^0_{n+1} = prolong(G(U^0_n));
+// for k >= 1 the fine groups F(U^{k-1}_n), n >= k - 1, and the correction sweep
+// U^k_{n+1} = F(U^{k-1}_n) + (G(U^k_n) - G(U^{k-1}_n)) with its norms.  Slices
+// n < k - 1 are exact already: U^k_{n+1} = U^{k-1}_{n+1}.  Every step waits only
+// for the data it reads: the previous iteration's step n (which wrote
+// G(U^{k-1}_n) and U^{k-1}_{n+1}) and the fine group of slice n.  `last`: the
+// final iteration that will be enqueued (it writes no fine inputs for k + 1).
+static rbc_status enqueue_iteration(pr_s* p, int k, int last, const double* d_U0) {
+  const int R = p->depth + 2, N = p->N;
+  const Grid &gf = p->fine->g, &gc = p->coarse->g;
+  const size_t Sf = state_doubles(gf), Sc = state_doubles(gc), Bf = Sf * sizeof(double);
+  pr_s::Slot& S = p->slots[k % R];
+  pr_s::Slot& X = p->slots[(k + 1) % R];
+  const cudaStream_t sC = sweep_stream(p, S);
+  S.busy = true;
+  std::vector<int> ncv(1, p->nc);
+  CK(cudaMemsetAsync(S.coarse->w.err, 0, sizeof(int), sC));   // this iteration's error bits
+  if (k == 0) {
+    CK(launch_restrict(gf, gc, static_cast<const double*>(d_U0), S.C, 1, sC));
+    for (int n = 0; n < N; ++n) {
+      rbc_status s = rbc_step_batch(S.coarse, S.C, 1, ncv.data(), nullptr, sC);
+      if (s != RBC_OK) return s;
+      double* Fnext = (n + 1 < N && last >= 1) ? X.Fin + (n + 1) * Sf : nullptr;
+      CK(launch_correct_norm(gf, gc, p->fine->t, 0, nullptr, S.C, p->d_Gold + n * Sc, S.C, nullptr,
+                             S.U + (n + 1) * Sf, Fnext, S.partial, S.counter, nullptr, sC));
+      CK(cudaEventRecord(S.ev_step[n], sC));
+    }
+    return RBC_OK;
+  }
+  pr_s::Slot& P = p->slots[(k - 1) % R];
+  const int n0 = k - 1;
+  // the converged slices U^k_0 .. U^k_{k-1}
+  if (k >= 2) CK(cudaStreamWaitEvent(sC, P.ev_step[k - 2], 0));
+  CK(cudaMemcpyAsync(S.U, P.U, (size_t)k * Bf, cudaMemcpyDeviceToDevice, sC));
+  // the fine groups: inputs S.Fin[n] written by the previous sweep at its step n - 1
+  std::vector<int> nfv(N, p->nf);
   const std::vector<int> a = fine_group_starts(p, n0);
+  for (int i = 0; i < p->fine_streams; ++i)
+    CK(cudaMemsetAsync(S.fines[i]->w.err, 0, sizeof(int), fine_stream(p, S, i)));
   for (int j = 0; j + 1 < (int)a.size(); ++j) {
     const int cnt = a[j + 1] - a[j];
     const int i = j % p->fine_streams;
-    CK(cudaStreamWaitEvent(sF[i], wait_for(a[j], cnt), 0));
-    rbc_status s = rbc_step_batch(p->fines[i], p->d_F + (size_t)a[j] * Sf, cnt, nfv.data(), p->d_I + a[j], sF[i]);
+    const cudaStream_t st = fine_stream(p, S, i);
+    const int last_in = a[j] + cnt - 2;
+    if (last_in >= std::max(0, k - 2)) CK(cudaStreamWaitEvent(st, P.ev_step[last_in], 0));
+    rbc_status s = rbc_step_batch(S.fines[i], S.Fin + (size_t)a[j] * Sf, cnt, nfv.data(), S.I + a[j], st);
     if (s != RBC_OK) return s;
-    CK(cudaEventRecord(p->ev_f[j], sF[i]));
-    for (int n = a[j]; n < a[j + 1]; ++n) slice_group[n] = j;
+    CK(cudaEventRecord(S.ev_group[j], st));
+    for (int n = a[j]; n < a[j + 1]; ++n) S.slice_group[n] = j;
   }
+  // the correction sweep
+  for (int n = n0; n < N; ++n) {
+    if (n >= k) {   // G(U^k_n); S.C holds the coarse modes of U^k_n
+      rbc_status s = rbc_step_batch(S.coarse, S.C, 1, ncv.data(), nullptr, sC);
+      if (s != RBC_OK) return s;
+    }
+    CK(cudaStreamWaitEvent(sC, P.ev_step[n], 0));
+    CK(cudaStreamWaitEvent(sC, S.ev_group[S.slice_group[n]], 0));
+    double* Gold = p->d_Gold + n * Sc;
+    const double* Gnew = n >= k ? S.C : Gold;   // U^k_{k-1} = U^{k-1}_{k-1}: G of it is Gold exactly
+    double* Fnext = (n + 1 < N && k < last) ? X.Fin + (n + 1) * Sf : nullptr;
+    CK(launch_correct_norm(gf, gc, p->fine->t, 1, S.Fin + n * Sf, Gnew, Gold, S.C, P.U + (n + 1) * Sf,
+                           S.U + (n + 1) * Sf, Fnext, S.partial, S.counter, S.norms + 2 * n, sC));
+    CK(cudaEventRecord(S.ev_step[n], sC));
+  }
+  return RBC_OK;
+}
+
+// Stop the step loops still running (speculative iterations past the one
+// that met the criterion), copy U^k_final to the caller and join every stream
+// of the call into `stream`, then clear the cancel word for the next call.
+static rbc_status finish_iterations(pr_s* p, int final_k, void* d_U, cudaStream_t stream) {
+  const int R = p->depth + 2;
+  CK(cudaMemsetAsync(p->d_cancel, 1, sizeof(int), p->sCancel));
+  CK(cudaEventRecord(p->ev_cancel, p->sCancel));
+  if (final_k >= 0) {
+    pr_s::Slot& F = p->slots[final_k % R];
+    CK(cudaStreamWaitEvent(stream, F.ev_step[p->N - 1], 0));
+    CK(cudaMemcpyAsync(d_U, F.U, (size_t)(p->N + 1) * state_doubles(p->fine->g) * sizeof(double),
+                       cudaMemcpyDeviceToDevice, stream));
+  }
+  for (auto& S : p->slots) {
+    if (!S.busy) continue;
+    S.busy = false;
+    CK(cudaEventRecord(S.ev_join[0], sweep_stream(p, S)));
+    CK(cudaStreamWaitEvent(stream, S.ev_join[0], 0));
+    for (int j = 0; j < p->fine_streams; ++j) {
+      CK(cudaEventRecord(S.ev_join[1 + j], fine_stream(p, S, j)));
+      CK(cudaStreamWaitEvent(stream, S.ev_join[1 + j], 0));
+    }
+  }
+  CK(cudaStreamWaitEvent(stream, p->ev_cancel, 0));
+  CK(cudaMemsetAsync(p->d_cancel, 0, sizeof(int), stream));
   return RBC_OK;
 }
 
 extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_iters, int* k_done,
                                        double* defects, double* nus, cudaStream_t stream) {
   if (!p || !d_U0 || !d_U || max_iters < 1) return fail(RBC_EINVAL, "bad arguments");
-  rbc_t F = p->fine, G = p->coarse, G2 = p->coarse2;
-  const Grid &gf = F->g, &gc = G->g;
-  const size_t Sf = state_doubles(gf), Sc = state_doubles(gc);
-  const size_t Bf = Sf * sizeof(double), Bc = Sc * sizeof(double);
-  const int N = p->N;
-  double* U = static_cast<double*>(d_U);
-  std::vector<int> ncv(1, p->nc), nfv(N, p->nf);
+  const Grid& gf = p->fine->g;
+  const size_t Sf = state_doubles(gf), Bf = Sf * sizeof(double);
+  const int N = p->N, R = p->depth + 2;
+  const int K = std::min(max_iters, N);   // U^N is the serial fine solution
   if (k_done) *k_done = 0;
-  CK(cudaMemcpyAsync(U, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
-  CK(cudaMemcpyAsync(p->d_Uold, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
-  CK(cudaMemcpyAsync(p->d_F, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
-  const bool part = p->gctx[0] != nullptr;
-  cudaStream_t s0 = part ? p->pG0 : p->coarse_priority ? p->sG0_hi : p->sG0;
-  cudaStream_t sg = part ? p->pG : p->coarse_priority ? p->sG_hi : p->sG;
-  cudaStream_t sF[pr_s::kFineStreams];
-  for (int i = 0; i < pr_s::kFineStreams; ++i) sF[i] = part ? p->pF[i] : p->sF[i];
-  // with an SM partition the handles capture their step graphs in it; the
-  // caller's handles are unbound again on every return
-  struct Bind {
-    pr_s* p;
-    Bind(pr_s* q, bool part) : p(q) {
-      for (rbc_t h : {p->coarse, p->coarse2}) h->bind_ctx = part ? p->gctx[0] : nullptr;
-      for (rbc_t h : p->fines)
-        if (h) h->bind_ctx = part ? p->gctx[1] : nullptr;
-    }
-    ~Bind() {
-      for (rbc_t h : {p->fine, p->coarse}) h->bind_ctx = nullptr;
-    }
-  } bind(p, part);
-  // sticky error bits of every handle in use, read after each iteration
-  std::vector<rbc_t> used{G, G2};
-  for (rbc_t h : p->fines)
-    if (h) used.push_back(h);
-  for (rbc_t h : used)
-    if (h->cap > 0) CK(cudaMemsetAsync(h->w.err, 0, sizeof(int), stream));
-  CK(cudaEventRecord(p->ev_begin, stream));   // the side streams start after the caller's work and these copies
-  for (cudaStream_t st : sF) CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
-  for (cudaStream_t st : {s0, sg}) CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
-  // k = 0: serial coarse sweep U_{n+1}^0 = G(U_n^0), on s0.  The coarse chain
-  // carries its own state (restricting the prolonged state gives it back
-  // exactly), so nothing here reads U while the correction sweep rewrites it.
-  CK(launch_restrict(gf, gc, U, p->d_C, 1, s0));
-  for (int n = 0; n < N; ++n) {
-    rbc_status s = rbc_step_batch(G, p->d_C, 1, ncv.data(), nullptr, s0);
+  for (int i = 0; i < std::min(R, K + 1); ++i) {
+    rbc_status s = ensure_slot(p, i);
     if (s != RBC_OK) return s;
-    CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C, Bc, cudaMemcpyDeviceToDevice, s0));
-    CK(launch_prolong(gf, gc, p->d_C, U + (n + 1) * Sf, 1, s0));
-    CK(cudaMemcpyAsync(p->d_Uold + (n + 1) * Sf, U + (n + 1) * Sf, Bf, cudaMemcpyDeviceToDevice, s0));
-    if (n + 1 < N) CK(cudaMemcpyAsync(p->d_F + (n + 1) * Sf, U + (n + 1) * Sf, Bf, cudaMemcpyDeviceToDevice, s0));
-    CK(cudaEventRecord(p->ev_g0[n], s0));
   }
-  CK(cudaEventRecord(p->ev_g0done, s0));
-  CK(cudaStreamWaitEvent(stream, p->ev_g0done, 0));
-  std::vector<int> slice_group(N, 0);
-  std::vector<double> I(N), nrm(2 * (N + 1));
+  // U^0_0 = U0 (slot 0), and the first fine input of iteration 1
+  CK(cudaMemcpyAsync(p->slots[0].U, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
+  CK(cudaMemcpyAsync(p->slots[1].Fin, d_U0, Bf, cudaMemcpyDeviceToDevice, stream));
+  CK(cudaEventRecord(p->ev_begin, stream));   // every stream of the call starts after the caller's work
+  for (int i = 0; i < std::min(R, K + 1); ++i) {
+    pr_s::Slot& S = p->slots[i];
+    CK(cudaStreamWaitEvent(sweep_stream(p, S), p->ev_begin, 0));
+    for (int j = 0; j < p->fine_streams; ++j) CK(cudaStreamWaitEvent(fine_stream(p, S, j), p->ev_begin, 0));
+  }
+  int final_k = 0;
+  rbc_status result = (p->criterion == RBC_CRIT_FIXED) ? RBC_OK : RBC_ENOTCONVERGED;
+  int enqueued = -1;
+  auto enqueue_upto = [&](int kmax) -> rbc_status {
+    for (int k = enqueued + 1; k <= std::min(kmax, K); ++k) {
+      rbc_status s = enqueue_iteration(p, k, K, static_cast<const double*>(d_U0));
+      if (s != RBC_OK) return s;
+      enqueued = k;
+    }
+    return RBC_OK;
+  };
+  auto bail = [&](rbc_status s) {
+    const std::string why = g_err;
+    finish_iterations(p, final_k, d_U, stream);
+    snprintf(g_err, sizeof(g_err), "%s", why.c_str());
+    return s;
+  };
+  rbc_status s = enqueue_upto(1 + p->depth);
+  if (s != RBC_OK) return bail(s);
+  std::vector<double> Ih(N, 0.0), nrm(2 * N), In(N);
   double nu_prev = 0.0;
   const int n_half = N / 2;
   const double win = (p->t1 - p->t0) * (double)(N - n_half) / N;
-  rbc_status result = (p->criterion == RBC_CRIT_FIXED) ? RBC_OK : RBC_ENOTCONVERGED;
-  for (int k = 1; k <= max_iters; ++k) {
+  for (int k = 1; k <= K; ++k) {
+    pr_s::Slot& S = p->slots[k % R];
     const int n0 = k - 1;
-    rbc_status s;
-    if (k == 1) {
-      // group inputs U_a .. U_{a+cnt-1} come from the U^0 sweep, up to its step a+cnt-2
-      s = fine_groups(p, sF, 0, nfv, slice_group,
-                      [&](int a, int cnt) { return a + cnt >= 2 ? p->ev_g0[a + cnt - 2] : p->ev_begin; });
-    } else {
-      // U^{k-1} is final: keep it for the defect and as the fine inputs
-      CK(cudaMemcpyAsync(p->d_Uold, U, (size_t)(N + 1) * Bf, cudaMemcpyDeviceToDevice, stream));
-      CK(cudaMemcpyAsync(p->d_F + n0 * Sf, U + n0 * Sf, (size_t)(N - n0) * Bf, cudaMemcpyDeviceToDevice, stream));
-      CK(cudaEventRecord(p->ev_copy, stream));
-      CK(cudaStreamWaitEvent(sg, p->ev_copy, 0));
-      s = fine_groups(p, sF, n0, nfv, slice_group, [&](int, int) { return p->ev_copy; });
-    }
-    if (s != RBC_OK) return s;
-    // serial correction sweep on sG
-    for (int n = 0; n < N; ++n) {
-      if (k == 1) CK(cudaStreamWaitEvent(sg, p->ev_g0[n], 0));   // Gold_n, and U^0_{n+1} written
-      if (n >= n0) CK(cudaStreamWaitEvent(sg, p->ev_f[slice_group[n]], 0));
-      if (n <= k - 1) {
-        // U_n unchanged since the last iteration: G(U_n) = Gold_n exactly
-        CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_Gold + n * Sc, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1,
-                          sg));
-        continue;
-      }
-      CK(launch_restrict(gf, gc, U + n * Sf, p->d_C2, 1, sg));
-      s = rbc_step_batch(G2, p->d_C2, 1, ncv.data(), nullptr, sg);
-      if (s != RBC_OK) return s;
-      CK(launch_correct(gf, gc, p->d_F + n * Sf, p->d_C2, p->d_Gold + n * Sc, U + (n + 1) * Sf, 1, sg));
-      CK(cudaMemcpyAsync(p->d_Gold + n * Sc, p->d_C2, Bc, cudaMemcpyDeviceToDevice, sg));
-    }
-    CK(cudaEventRecord(p->ev_gdone, sg));
-    CK(cudaStreamWaitEvent(stream, p->ev_gdone, 0));
-    for (int i = 0; i < pr_s::kFineStreams; ++i) {
-      CK(cudaEventRecord(p->ev_fdone[i], sF[i]));
-      CK(cudaStreamWaitEvent(stream, p->ev_fdone[i], 0));
-    }
-    // Defect_k = max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k||  (L2 of T); a non-finite
-    // fine or coarse result reaches U through the correction and shows here
-    CK(launch_l2_diff(gf, F->t, U, p->d_Uold, N + 1, p->d_norm, stream));
-    CK(launch_l2_diff(gf, F->t, U, nullptr, N + 1, p->d_norm + N + 1, stream));
-    CK(cudaMemcpyAsync(nrm.data(), p->d_norm, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
-    CK(cudaMemcpyAsync(I.data(), p->d_I, N * sizeof(double), cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
+    CK(cudaEventSynchronize(S.ev_step[N - 1]));   // the sweep waited for every fine group of the iteration
+    final_k = k;
     int bits = 0;
-    for (rbc_t h : used) {
+    for (rbc_t h : {S.coarse, S.fines[0], S.fines[1], S.fines[2], S.fines[3]}) {
       int b = 0;
-      if (h->cap > 0) CK(cudaMemcpy(&b, h->w.err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (h && h->cap > 0) CK(cudaMemcpy(&b, h->w.err, sizeof(int), cudaMemcpyDeviceToHost));
       bits |= b;
     }
-    if (bits & kFlagTimeout) return status_of_bits(bits);
+    if (bits & kFlagTimeout) return bail(status_of_bits(bits));
+    CK(cudaMemcpy(nrm.data() + 2 * n0, S.norms + 2 * n0, 2 * (N - n0) * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(In.data() + n0, S.I + n0, (N - n0) * sizeof(double), cudaMemcpyDeviceToHost));
+    // Defect_k = max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k|| (L2 of T); the slices
+    // n <= k - 1 are unchanged.  A non-finite fine or coarse result reaches U
+    // through the correction and shows here.
     double defect = 0.0;
-    for (int n = 1; n <= N; ++n) {
-      if (!std::isfinite(nrm[n]) || !std::isfinite(nrm[N + 1 + n])) return fail(RBC_EDIVERGED, "non-finite iterate");
-      if (nrm[N + 1 + n] > 0) defect = std::max(defect, std::sqrt(nrm[n] / nrm[N + 1 + n]));
+    for (int n = n0; n < N; ++n) {
+      const double d2 = nrm[2 * n], u2 = nrm[2 * n + 1];
+      if (!std::isfinite(d2) || !std::isfinite(u2)) return bail(fail(RBC_EDIVERGED, "non-finite iterate"));
+      if (u2 > 0) defect = std::max(defect, std::sqrt(d2 / u2));
+      if (!std::isfinite(In[n])) return bail(fail(RBC_EDIVERGED, "non-finite Nu integral"));
+      Ih[n] = In[n];
     }
     double nu = 0.0;
-    for (int n = n_half; n < N; ++n) {
-      if (!std::isfinite(I[n])) return fail(RBC_EDIVERGED, "non-finite Nu integral");
-      nu += I[n];
-    }
+    for (int n = n_half; n < N; ++n) nu += Ih[n];
     nu /= win;
     if (defects) defects[k - 1] = defect;
     if (nus) nus[k - 1] = nu;
     if (k_done) *k_done = k;
-    if (p->criterion == RBC_CRIT_DEFECT && defect <= p->tol) return RBC_OK;
-    if (p->criterion == RBC_CRIT_NU && k >= 2 && std::fabs(nu - nu_prev) <= p->tol * std::fabs(nu)) return RBC_OK;
+    bool stop = false;
+    if (p->criterion == RBC_CRIT_DEFECT && defect <= p->tol) stop = true;
+    if (p->criterion == RBC_CRIT_NU && k >= 2 && std::fabs(nu - nu_prev) <= p->tol * std::fabs(nu)) stop = true;
     nu_prev = nu;
-    if (k >= N) break;   // U^N is the serial fine solution
+    if (stop) {
+      result = RBC_OK;
+      break;
+    }
+    s = enqueue_upto(k + 1 + p->depth);
+    if (s != RBC_OK) return bail(s);
   }
+  s = finish_iterations(p, final_k, d_U, stream);
+  if (s != RBC_OK) return s;
+  CK(cudaStreamSynchronize(stream));
   return result;
 }

@@ -118,6 +118,7 @@ struct Work {
   double* nu;      // [B] internal Nu integral when the caller passes none
   double* small;   // [16] scalars
   double* ra;      // [B] Rayleigh number of each state
+  const int* cancel;   // device word that ends the step loops early when set, or nullptr
   Prof* prof;      // timing, or nullptr
 };
 
@@ -156,6 +157,14 @@ cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const double* Xf, do
 cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, const double* Gnew,
                            const double* Gold, double* Uout, int B, cudaStream_t s);
 cudaError_t launch_prolong(const Grid& gf, const Grid& gc, const double* Xc, double* Xf, int B, cudaStream_t s);
+// One slice of a Parareal sweep fused with its norms (mode 0: U^0 = prolong(Gnew);
+// mode 1: the correction of Eq. 20); see k_correct_norm.  partial: 2 doubles
+// per block (correct_norm_blocks), counter: one zeroed unsigned; launches on
+// the same (partial, counter) must be ordered (one stream).
+int correct_norm_blocks(const Grid& gf);
+cudaError_t launch_correct_norm(const Grid& gf, const Grid& gc, const Tables& tf, int mode, const double* Ff,
+                                const double* Gnew, double* Gold, double* C, const double* Uprev, double* U,
+                                double* Fnext, double* partial, unsigned* counter, double* norms, cudaStream_t s);
 size_t rows_smem_bytes(const Grid& g);
 size_t static_scratch_doubles_needed(const Grid& g);
 constexpr size_t kStaticScratchCapacity = (size_t)3 << 17;   // doubles in the static scratch array (3 MiB)

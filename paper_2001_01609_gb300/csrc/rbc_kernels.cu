@@ -1084,10 +1084,13 @@ __global__ void k_advance(int* step) { *step += 1; }
 
 // Body end of the device-side step loop: the loop ends once every state of the
 // batch has taken its steps (maxs is written by the host before each launch).
-__global__ void k_advance_loop(int* step, const int* maxs, cudaGraphConditionalHandle loop) {
+// cancel (may be null): a word another stream sets to stop the loop early
+// (work whose result is no longer wanted, e.g. a speculative Parareal iteration)
+__global__ void k_advance_loop(int* step, const int* maxs, const int* cancel, cudaGraphConditionalHandle loop) {
   const int s = *step + 1;
   *step = s;
-  cudaGraphSetConditional(loop, s < *maxs ? 1u : 0u);
+  const bool stop = cancel != nullptr && *(const volatile int*)cancel != 0;
+  cudaGraphSetConditional(loop, (s < *maxs && !stop) ? 1u : 0u);
 }
 
 static inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -1268,7 +1271,7 @@ cudaError_t launch_advance(const Work& w, cudaStream_t s) {
 }
 
 cudaError_t launch_advance_loop(const Work& w, cudaGraphConditionalHandle loop, cudaStream_t s) {
-  k_advance_loop<<<1, 1, 0, s>>>(w.step, w.maxs, loop);
+  k_advance_loop<<<1, 1, 0, s>>>(w.step, w.maxs, w.cancel, loop);
   count();
   return cudaGetLastError();
 }
@@ -1417,38 +1420,58 @@ cudaError_t launch_diagnostics(const Grid& g, const Tables& t, const Work& w, co
   return cudaGetLastError();
 }
 
+// Squared L2(Omega) norms of temperature fields (the defect norm of Sec. 3.7):
+// ||T||^2 = (Lx / 2) sum_m w_m Re(conj(c_m) . Gram c_m), w = 1 for m = 0, 2
+// otherwise (Parseval in x), Gram the exact Chebyshev Gram matrix (z in
+// [-1/2, 1/2]).  The sum runs over tiles of kCorrTile Fourier modes in tile
+// order, each tile's terms summed by the block in a fixed order, with explicit
+// roundings; rbc_l2_diff and the fused Parareal correction share this order,
+// so both give the same bits.
+constexpr int kCorrTile = 8;
+constexpr int kCorrThreads = 256;
+
+// w Re(conj(di) . s) added to acc, s = sum_j gram_ij d_j
+__device__ __forceinline__ double l2_term(double acc, double w, double2 di, double2 s) {
+  return fma(w, fma(di.x, s.x, __dmul_rn(di.y, s.y)), acc);
+}
+__device__ __forceinline__ double2 gram_acc(double2 s, double gij, double2 dj) {
+  return make_double2(fma(gij, dj.x, s.x), fma(gij, dj.y, s.y));
+}
+
 // ||A_b - B_b||^2 (or ||A_b||^2 when Bm is null) of the temperature field of nst
-// states: Parseval in x (weights 1 for m = 0, 2 otherwise), exact Chebyshev
-// Gram matrix in z, times Lx / 2 (z in [-1/2, 1/2]).  Block per state,
-// deterministic reduction.
-__global__ void __launch_bounds__(256) k_l2_diff(Grid g, const double* gram, const double* A, const double* Bm,
-                                                 double* out) {
-  __shared__ double red[256];
+// states, block (kCorrThreads threads) per state.
+__global__ void __launch_bounds__(kCorrThreads) k_l2_diff(Grid g, const double* gram, const double* A, const double* Bm,
+                                                          double* out) {
+  __shared__ double red[kCorrThreads];
   const int b = blockIdx.x;
   const size_t S = state_doubles(g);
   const double* a = A + (size_t)b * S;
   const double* bb = Bm ? Bm + (size_t)b * S : nullptr;
-  double acc = 0.0;
-  for (int it = threadIdx.x; it < g.nm * g.Nz; it += blockDim.x) {
-    const int m = it % g.nm, i = it / g.nm;
-    double2 di = ld2(a + soff(g, 0, i, m));
-    if (bb) di = di - ld2(bb + soff(g, 0, i, m));
-    double2 s = {0.0, 0.0};
-    for (int jn = (i & 1); jn < g.Nz; jn += 2) {
-      double2 dj = ld2(a + soff(g, 0, jn, m));
-      if (bb) dj = dj - ld2(bb + soff(g, 0, jn, m));
-      s = s + __ldg(gram + (size_t)i * g.Nz + jn) * dj;
+  double tot = 0.0;
+  for (int m0 = 0; m0 < g.nm; m0 += kCorrTile) {
+    const int tm = min(kCorrTile, g.nm - m0);
+    double acc = 0.0;
+    for (int it = threadIdx.x; it < tm * g.Nz; it += blockDim.x) {
+      const int dm = it % tm, i = it / tm, m = m0 + dm;
+      double2 di = ld2(a + soff(g, 0, i, m));
+      if (bb) di = di - ld2(bb + soff(g, 0, i, m));
+      double2 s = {0.0, 0.0};
+      for (int jn = (i & 1); jn < g.Nz; jn += 2) {
+        double2 dj = ld2(a + soff(g, 0, jn, m));
+        if (bb) dj = dj - ld2(bb + soff(g, 0, jn, m));
+        s = gram_acc(s, __ldg(gram + (size_t)i * g.Nz + jn), dj);
+      }
+      acc = l2_term(acc, m == 0 ? 1.0 : 2.0, di, s);
     }
-    acc += (m == 0 ? 1.0 : 2.0) * (di.x * s.x + di.y * s.y);
+    tot += block_sum(acc, red);
   }
-  const double tot = block_sum(acc, red);
   if (threadIdx.x == 0) out[b] = 0.5 * g.Lx * tot;
 }
 
 cudaError_t launch_l2_diff(const Grid& g, const Tables& t, const double* A, const double* Bm, int nst, double* out,
                            cudaStream_t s) {
   if (nst <= 0) return cudaSuccess;
-  k_l2_diff<<<nst, 256, 0, s>>>(g, t.gram, A, Bm, out);
+  k_l2_diff<<<nst, kCorrThreads, 0, s>>>(g, t.gram, A, Bm, out);
   count();
   return cudaGetLastError();
 }
@@ -1635,6 +1658,107 @@ cudaError_t launch_correct(const Grid& gf, const Grid& gc, const double* Ff, con
                            double* Uout, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   k_correct<<<nblk(2L * gf.Nz * gf.nm * B, 128), 128, 0, s>>>(gf, gc, Ff, Gnew, Gold, Uout, B);
+  count();
+  return cudaGetLastError();
+}
+
+// One slice of a Parareal sweep (Sec. 3.1, Eq. 20) fused with its norms (Sec. 3.7).
+// mode 0 (the coarse sweep U^0):  U = prolong(Gnew).
+// mode 1 (a correction):          U = F + (prolong(Gnew) - prolong(Gold)), elementwise in that order.
+// Both: Gold <- Gnew (the coarse value of this iterate, which the next
+// iteration subtracts); C <- restrict(U) (the next coarse step's input: the
+// coarse modes of U; C may be the Gnew buffer, each element is read before
+// it is written); Fnext <- U when not null (the next iteration's fine input);
+// mode 1 with Uprev: norms[0] = ||T(U) - T(Uprev)||^2, norms[1] = ||T(U)||^2
+// (L2 over the domain, in the order of k_l2_diff: the same bits).
+// Block per tile of kCorrTile Fourier modes, all Chebyshev indices of both
+// fields; the blocks' partial sums are added in block order by the last block
+// to finish (partial[2 * gridDim.x], counter: left at zero).
+__global__ void __launch_bounds__(kCorrThreads) k_correct_norm(
+    Grid gf, Grid gc, const double* __restrict__ gram, int mode, const double* Ff, const double* Gnew, double* Gold,
+    double* C, const double* __restrict__ Uprev, double* __restrict__ U, double* __restrict__ Fnext,
+    double* partial, unsigned* counter, double* norms) {
+  __shared__ double red[kCorrThreads];
+  extern __shared__ double2 sd[];             // [kCorrTile][Nz]: T(U) - T(Uprev) of the tile's modes
+  __shared__ bool last;
+  const int m0 = blockIdx.x * kCorrTile;
+  const int tm = min(kCorrTile, gf.nm - m0);
+  const int per = 2 * gf.Nz * tm;
+  const bool with_norms = mode == 1 && Uprev != nullptr;
+  for (int it = threadIdx.x; it < per; it += blockDim.x) {
+    const int dm = it % tm, n = (it / tm) % gf.Nz, f = it / (tm * gf.Nz);
+    const int m = m0 + dm;
+    const size_t o = soff(gf, f, n, m);
+    const bool coarse = m < gc.nm && n < gc.Nz;
+    const size_t oc = coarse ? soff(gc, f, n, m) : 0;
+    double2 u;
+    if (mode == 0) {
+      u = coarse ? ld2(Gnew + oc) : make_double2(0.0, 0.0);
+      if (coarse) st2(Gold + oc, u);
+    } else {
+      double2 d = {0.0, 0.0};
+      if (coarse) {
+        const double2 gn = ld2(Gnew + oc);
+        d = gn - ld2(Gold + oc);
+        st2(Gold + oc, gn);
+      }
+      u = ld2(Ff + o) + d;
+      if (coarse) st2(C + oc, u);
+    }
+    st2(U + o, u);
+    if (Fnext) st2(Fnext + o, u);
+    if (with_norms && f == 0) sd[dm * gf.Nz + n] = u - ld2(Uprev + o);
+  }
+  if (!with_norms) return;
+  __syncthreads();
+  // sum_m w_m Re(conj(d_i) sum_j gram_ij d_j), i, j of equal parity; the same for U
+  double acc_d = 0.0, acc_u = 0.0;
+  for (int it = threadIdx.x; it < tm * gf.Nz; it += blockDim.x) {
+    const int dm = it % tm, i = it / tm, m = m0 + dm;
+    const double2 di = sd[dm * gf.Nz + i];
+    const double2 ui = ld2(U + soff(gf, 0, i, m));
+    double2 s = {0.0, 0.0}, t = {0.0, 0.0};
+    for (int j = (i & 1); j < gf.Nz; j += 2) {
+      const double gij = __ldg(gram + (size_t)i * gf.Nz + j);
+      s = gram_acc(s, gij, sd[dm * gf.Nz + j]);
+      t = gram_acc(t, gij, ld2(U + soff(gf, 0, j, m)));
+    }
+    const double w = m == 0 ? 1.0 : 2.0;
+    acc_d = l2_term(acc_d, w, di, s);
+    acc_u = l2_term(acc_u, w, ui, t);
+  }
+  acc_d = block_sum(acc_d, red);
+  acc_u = block_sum(acc_u, red);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = acc_d;
+    partial[2 * blockIdx.x + 1] = acc_u;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double sdiff = 0.0, su = 0.0;
+  for (unsigned bidx = 0; bidx < gridDim.x; ++bidx) {
+    sdiff += *((volatile double*)partial + 2 * bidx);
+    su += *((volatile double*)partial + 2 * bidx + 1);
+  }
+  norms[0] = 0.5 * gf.Lx * sdiff;
+  norms[1] = 0.5 * gf.Lx * su;
+  *counter = 0u;
+}
+
+int correct_norm_blocks(const Grid& gf) { return (gf.nm + kCorrTile - 1) / kCorrTile; }
+
+cudaError_t launch_correct_norm(const Grid& gf, const Grid& gc, const Tables& tf, int mode, const double* Ff,
+                                const double* Gnew, double* Gold, double* C, const double* Uprev, double* U,
+                                double* Fnext, double* partial, unsigned* counter, double* norms, cudaStream_t s) {
+  static int allowed = 48 * 1024;
+  const size_t smem = (size_t)kCorrTile * gf.Nz * sizeof(double2);
+  cudaError_t e = allow_smem(k_correct_norm, (int)smem, allowed);
+  if (e != cudaSuccess) return e;
+  k_correct_norm<<<correct_norm_blocks(gf), kCorrThreads, smem, s>>>(gf, gc, tf.gram, mode, Ff, Gnew, Gold, C, Uprev,
+                                                                     U, Fnext, partial, counter, norms);
   count();
   return cudaGetLastError();
 }

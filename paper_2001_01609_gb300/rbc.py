@@ -23,7 +23,7 @@ EXPORTS = [
     "rbc_l2_temperature", "parareal_create", "parareal_destroy", "parareal_iterate", "rbc_profile",
     "rbc_profile_read", "rbc_launch_count", "rbc_nusselt_static", "rbc_step_batch_ra", "rbc_restrict",
     "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff", "parareal_set_schedule", "parareal_coarse_sms",
-    "rbc_diag_size", "rbc_diagnostics", "rbc_set_wait_limit",
+    "rbc_diag_size", "rbc_diagnostics", "rbc_set_wait_limit", "parareal_set_depth",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -81,6 +81,7 @@ def load():
         "rbc_diag_size": (S, [P]),
         "rbc_diagnostics": (I, [P, P, I, P, P]),
         "rbc_set_wait_limit": (I, [ctypes.c_longlong]),
+        "parareal_set_depth": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -294,6 +295,10 @@ class Parareal:
         partition for the coarse sweeps, of the overlapped schedule (timing only)."""
         fg = group if first_group is None else first_group
         _check(load().parareal_set_schedule(self.h, group, fg, fine_streams, coarse_priority, coarse_sms))
+
+    def set_depth(self, depth):
+        """Iterations kept enqueued beyond the one being evaluated (0..6, timing only)."""
+        _check(load().parareal_set_depth(self.h, depth))
 
     @property
     def coarse_sms(self):

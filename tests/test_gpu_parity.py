@@ -322,6 +322,33 @@ def test_parareal_schedule_does_not_change_results(rbc, precision):
         assert torch.equal(U, out[0][0])
         np.testing.assert_array_equal(d, out[0][1])
         np.testing.assert_array_equal(nus, out[0][2])
+    # iterations enqueued ahead of the one being evaluated: timing only
+    for depth in (0, 1, 3, 6):
+        P = rbc.Parareal(F, G, 0.0, T, N)
+        P.set_depth(depth)
+        U = F.new_states(N + 1)
+        st, k, d, nus = P.iterate(u0[0], U, 3)
+        assert st == rbc.RBC_OK and k == 3
+        assert torch.equal(U, out[0][0])
+        np.testing.assert_array_equal(d, out[0][1])
+        np.testing.assert_array_equal(nus, out[0][2])
+    # a criterion met while later iterations run ahead: they are stopped and
+    # dropped, the result is iterate k, and the next call starts clean
+    d3 = out[0][1]
+    tol = d3[1] * 1.0001
+    expect = 1 + min(i for i in range(len(d3)) if d3[i] <= tol)
+    Pd = rbc.Parareal(F, G, 0.0, T, N, rbc.CRIT_DEFECT, tol)
+    Pd.set_depth(3)
+    Ud = F.new_states(N + 1)
+    P2 = rbc.Parareal(F, G, 0.0, T, N)
+    U2 = F.new_states(N + 1)
+    P2.iterate(u0[0], U2, expect)
+    for _ in range(2):
+        st, k, d, _ = Pd.iterate(u0[0], Ud, N)
+        assert st == rbc.RBC_OK and k == expect
+        assert torch.equal(Ud, U2)
+    with pytest.raises(rbc.RBCError):
+        Pd.set_depth(7)
     # more iterations than slices: stops at k = N with the serial fine solution
     P = rbc.Parareal(F, G, 0.0, T, N)
     U = F.new_states(N + 1)
