@@ -182,6 +182,72 @@ def fine_group_starts(N, group, first, n0=0):
     return a
 
 
+def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=2):
+    """Parareal to a stated tolerance against the serial all-FP64 fine propagator
+    on the same GPU (Sec. 3.7: iterate until Nu_k is within tol of Nu_{k-1}).
+
+    Serial fine: one trajectory, B = 1, all FP64, every slice in turn over
+    [0, t_end] (the same kernels), with the Nu_V integral of each slice.
+    Parareal arms: mixed precision (fine and coarse propagators: FP32
+    transforms and products, FP64 solves, correction and norms) and all FP64;
+    RBC_CRIT_NU with tol, iterations enqueued `depth` ahead.  "Equal
+    Nu accuracy": each arm's Nu (time mean over the second half of the slices)
+    is compared with the serial FP64 one.  Device time with CUDA events on the
+    caller's stream, after one untimed warm-up iteration per arm."""
+    import torch
+    N, nf = w["slices"], w["steps_per_slice"]
+    n_half = N // 2
+    win = dv["t_end"] * (N - n_half) / N
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, r
+
+    F64 = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"])
+    warm = F64.new_states(1)
+    warm.copy_(U0[0:1])
+    F64.step_batch(warm, 20, stream=stream)
+    ser = F64.new_states(1)
+    ser.copy_(U0[0:1])
+    nu_ser = torch.zeros(N, dtype=torch.float64, device="cuda")
+
+    def serial():
+        for n in range(N):
+            F64.step_batch(ser, nf, nu_ser[n:n + 1], stream=stream)
+    serial_s, _ = timed(serial)
+    if F64.check_diverged(stream) != rbc.RBC_OK:
+        raise RuntimeError("serial fine run diverged")
+    nu_serial = float(nu_ser[n_half:].sum().item()) / win
+    out = dict(criterion=f"Nu: |Nu_k - Nu_(k-1)| <= {tol} |Nu_k| (Sec. 3.7, the paper's 1%)",
+               serial_fine=dict(precision="fp64", s=serial_s, nu=nu_serial,
+                                run=f"B = 1, {N} slices x {nf} steps in turn, same kernels"),
+               arms={})
+    for name, pf, pg in (("mixed", rbc.RBC_MIXED, rbc.RBC_MIXED), ("fp64", rbc.RBC_FP64, rbc.RBC_FP64)):
+        F = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"], precision=pf)
+        G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dv["dtc"], precision=pg)
+        P = rbc.Parareal(F, G, 0.0, dv["t_end"], N, rbc.CRIT_NU, tol)
+        P.set_depth(depth)
+        U = F.new_states(N + 1)
+        P.iterate(U0[0], U, 1, stream=stream)                      # warm-up: graphs, workspaces
+        el, (st, k, de, nus) = timed(lambda: P.iterate(U0[0], U, max_iters, stream=stream))
+        nu = float(nus[-1]) if len(nus) else float("nan")
+        out["arms"][name] = dict(
+            fine_precision="mixed" if pf == rbc.RBC_MIXED else "fp64",
+            coarse_precision="mixed" if pg == rbc.RBC_MIXED else "fp64",
+            status={rbc.RBC_OK: "tolerance met", rbc.RBC_ENOTCONVERGED: "not converged",
+                    rbc.RBC_EDIVERGED: "diverged"}.get(st, str(st)),
+            iterations=int(k), s=el, speedup_vs_serial_fp64=serial_s / el, defects=[float(x) for x in de],
+            nus=[float(x) for x in nus], nu=nu, nu_rel_err_vs_serial_fp64=abs(nu - nu_serial) / abs(nu_serial),
+            equal_nu_accuracy=bool(abs(nu - nu_serial) <= tol * abs(nu_serial)), depth=depth)
+        del P, F, G, U
+    return out
+
+
 def run_gb300(args, w):
     import torch
     import torch.distributed as dist
@@ -268,17 +334,9 @@ def run_gb300(args, w):
     G.profile(False)
     ck = clocks.stop()
     gpu_launches = rbc.launch_count() - launches0
-    # Serial fine reference (after the timed region): one slice of the fine
-    # propagator alone (B = 1, all its steps, same kernels), times the slice count.
-    ser = F.new_states(1)
-    ser.copy_(U0[0:1])
-    F.step_batch(ser, 50, stream=stream)
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    F.step_batch(ser, w["steps_per_slice"], stream=stream)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    serial_fine_s = N * s0.elapsed_time(s1) / 1e3
+    # Time to tolerance (after the timed region): Parareal iterated until the
+    # Nu criterion holds, against the serial all-FP64 fine run on this GPU.
+    ttt = None if args.no_time_to_tol else time_to_tolerance(rbc, w, dv, U0, stream)
     # Sec. 2.2 diagnostics of all fine states (one rbc_diagnostics call), after the timed region
     dout = F.diagnostics(U[:N])
     for _ in range(3):
@@ -363,11 +421,7 @@ def run_gb300(args, w):
                                      frac_fp64=diag_flops / diag_s / 1e12 / peak_fp64,
                                      note="rbc_diagnostics (Sec. 2.2 averages) of all slices' fine states, "
                                           "FP64 z inverse plus Parseval and Clenshaw-Curtis reductions"),
-                    time_to_tol=dict(parareal_iterations=1, parareal_s=t_total / args.steps,
-                                     serial_fine_s=serial_fine_s, speedup=serial_fine_s / (t_total / args.steps),
-                                     defect_after=float(de[-1]) if len(de) else None,
-                                     serial_fine_sample="one slice of the fine propagator alone (B = 1, "
-                                                        f"{w['steps_per_slice']} steps) times {N} slices"))
+                    time_to_tol=ttt)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -598,14 +652,14 @@ def run_coarsening_study(coarse=None, slices=None):
 
 
 def run_statistics_study():
-    """StatisticalParareal (Sec. 2.2 statistics sampled along every fine sweep,
-    statistical stopping) against the library's parareal_iterate on the study's
-    fine grid: 16 slices of 600 fine steps, CF 2 coarse propagator."""
+    """Parareal with the Sec. 2.2 statistics sampled along every fine sweep and
+    the statistical stopping rule (RBC_CRIT_STAT), against the same Parareal
+    without sampling, on the study's fine grid: 16 slices of 600 fine steps,
+    CF 2 coarse propagator."""
     import torch
     from paper_2001_01609_gb300 import build
     build.build()
     from paper_2001_01609_gb300 import rbc
-    from paper_2001_01609_gb300 import statistics as pst
     from paper_2001_01609_gb300.inputs import initial_temperature
     s = STUDY
     N, every, K = 16, 50, 3
@@ -615,28 +669,30 @@ def run_statistics_study():
     U0 = F.new_states(1)
     F.set_state(U0[0], initial_temperature(s["Nx"], s["Nz"], seed=s["seed"], Lx=s["Lx"]))
     T = s["total_steps"] * s["dt"]
-    P = pst.StatisticalParareal(F, G, 0.0, T, N, every=every, tol=1e-2)
+    P = rbc.Parareal(F, G, 0.0, T, N, rbc.CRIT_STAT, 1e-2)
+    P.set_sampling(every)
     U = F.new_states(N + 1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = P.iterate(U0[0], U, K)
+    st_s, k_s, de_s, _ = P.iterate(U0[0], U, K)
     torch.cuda.synchronize()
     t_stat = time.perf_counter() - t0
+    summary = rbc.stat_summary(s["Nz"], s["Ra"], s["Pr"], P.stat_means())
     L = rbc.Parareal(F, G, 0.0, T, N)
     U2 = F.new_states(N + 1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    st, k, de, nus = L.iterate(U0[0], U2, res["k"])
+    st, k, de, nus = L.iterate(U0[0], U2, k_s)
     torch.cuda.synchronize()
     t_lib = time.perf_counter() - t0
     keep = ("NuV", "Nub", "Nut", "Re", "P", "eps_U", "Nu_int", "balance", "delta_T", "N_BL", "delta_t")
-    stats = [{q: (float(a[q]) if q != "N_BL" else int(a[q])) for q in keep} for a in res["stats"]]
     print(json.dumps(dict(study="statistical_parareal", grid=f"{s['Nx']}x{s['Nz']}", coarse_grid=f"{Nxc}x{Nzc}",
                           Ra=s["Ra"], slices=N, fine_steps_per_slice=s["total_steps"] // N, sample_every=every,
-                          criterion="stat", tol=1e-2, status=res["status"], iterations=res["k"],
-                          defects=res["defects"], stats=stats, seconds=t_stat,
-                          library_parareal=dict(iterations=k, seconds=t_lib, defects=list(map(float, de))),
-                          same_iterates_as_library=bool(torch.equal(U, U2)))), flush=True)
+                          criterion="stat", tol=1e-2, status=st_s, iterations=k_s,
+                          defects=list(map(float, de_s)), stats_at_stop={q: summary[q] for q in keep},
+                          seconds=t_stat,
+                          unsampled_parareal=dict(iterations=k, seconds=t_lib, defects=list(map(float, de))),
+                          same_iterates_as_unsampled=bool(torch.equal(U, U2)))), flush=True)
 
 
 def run_ncu_case(name):
@@ -692,6 +748,7 @@ def main():
     ap.add_argument("--coarse-priority", type=int, default=1, choices=[0, 1])
     ap.add_argument("--coarse-sms", type=int, default=0, help="SMs of the coarse sweeps' own partition (0: shared)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-tol", action="store_true", help="skip the Parareal-to-tolerance runs")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
     ap.add_argument("--study", choices=["coarsening", "statistics"],
                     help="the coarsening and slice-count study, or the statistical Parareal run (not bench lines)")

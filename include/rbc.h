@@ -63,7 +63,7 @@ typedef enum {
 
 enum { RBC_FP64 = 0, RBC_MIXED = 1 };         /* rbc_opts.precision */
 enum { RBC_FIXED_T = 0, RBC_FIXED_FLUX = 1 }; /* rbc_opts.bc (Eqs. 6, 7) */
-enum { RBC_CRIT_FIXED = 0, RBC_CRIT_DEFECT = 1, RBC_CRIT_NU = 2 };
+enum { RBC_CRIT_FIXED = 0, RBC_CRIT_DEFECT = 1, RBC_CRIT_NU = 2, RBC_CRIT_STAT = 3 };
 
 typedef struct {
   int precision;   /* RBC_FP64: every step in FP64.  RBC_MIXED: transforms and
@@ -203,6 +203,40 @@ rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStr
 size_t     rbc_diag_size(rbc_t h);
 rbc_status rbc_diagnostics(rbc_t h, const void* d_states, int B, double* d_out, cudaStream_t stream);
 
+/* Time statistics of Sec. 2.2 along a run.
+ * rbc_step_batch_sampled: rbc_step_batch of B states by nsteps steps each,
+ * with the averages of rbc_diagnostics taken at steps 0, every, 2 every, ...
+ * and nsteps, and their trapezoid-rule time integrals written to the
+ * caller-owned device array d_stat[B][rbc_diag_size(h)] (FP64) in the order
+ *   [0] <u^2 + w^2>_V^(1/2)   [1] <u . lap u>_V   [2] <w T>_V
+ *   [3] Nu_V  [4] Nu_b  [5] Nu_t
+ *   [6, 6 + Mz)          <T>_x at the padded points (as rbc_diagnostics)
+ *   [6 + Mz, 6 + 2 Mz)   <T^2>_x = <(T - <T>_x)^2>_x + <T>_x^2
+ * (divided by the sampled duration they give the time means; reading: the
+ * paper gives no sampling rule).  d_nu_integral (device double[B], may be
+ * NULL) receives the Nu_V integral as rbc_step_batch would (summed over the
+ * sampling intervals, so its last bits can differ from one unsampled call).
+ * Asynchronous on `stream`; grows the handle's buffers on demand.  RBC_EINVAL
+ * for every < 1, nsteps < 0 or a null pointer.                              */
+rbc_status rbc_step_batch_sampled(rbc_t h, void* d_states, int B, int nsteps, int every,
+                                  double* d_nu_integral, double* d_stat, cudaStream_t stream);
+
+/* rbc_stat_summary: the quantities of Sec. 2.2 from time means (d_stat rows
+ * divided by the duration, summed over slices first when there are several)
+ * of a grid with Nz Chebyshev points, Rayleigh number Ra and Prandtl number
+ * Pr, into host out[12 + 3 Nz / 2]:
+ *   [0] U (characteristic speed)  [1] Re = U / Pr  [2] Nu_V  [3] Nu_b  [4] Nu_t
+ *   [5] Nu_int = max pairwise |difference| / Nu_V (Eq. 13)
+ *   [6] P = Ra <w T> (Eq. 14)  [7] eps_U = |<u . lap u>|  [8] |P - eps_U| / P (Eq. 15)
+ *   [9] delta_t = 1 / (2 Nu_V) (Eq. 17)
+ *   [10] delta_T: height above the bottom wall of the largest T_rms over the
+ *        padded points of the lower half (the first from the wall on a tie)
+ *   [11] N_BL: interior native Lobatto points within delta_T of the wall
+ *   [12, 12 + Mz) T_rms (Eq. 16, read as the RMS about the time-mean plane
+ *        average) at the padded points.
+ * Host arithmetic only (no device, no handle).                              */
+rbc_status rbc_stat_summary(int Nz, double Ra, double Pr, const double* means, double* out);
+
 /* Building blocks of Eq. 20 for callers that drive Parareal themselves (the
  * serving engine interleaves many runs).  All act on B contiguous states on
  * `stream`, asynchronously; the coarse grid must be no finer than the fine.
@@ -228,7 +262,12 @@ rbc_status rbc_l2_diff(rbc_t h, const void* d_A, const void* d_B, int B, double*
  * paper's practice, Sec. 3.7), RBC_CRIT_DEFECT (stop when
  * max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k|| <= tol, L2 norm of T), RBC_CRIT_NU
  * (stop when |Nu_k - Nu_{k-1}| / |Nu_k| <= tol, Nu_k = time average of Nu_V
- * over the second half of the slices along the fine trajectories from U^k).
+ * over the second half of the slices along the fine trajectories from U^k),
+ * RBC_CRIT_STAT (the statistical rule the paper leaves open, Sec. 3.7 and
+ * Sec. 5.2, read as: stop at the first k >= 2 whose time means of Nu_V, Nu_b,
+ * Nu_t, Re, P and eps_U over the averaging window all changed by at most tol
+ * relative to iteration k - 1; the fine sweeps are then sampled, see
+ * parareal_set_sampling).
  * The handles must outlive the Parareal handle.                            */
 rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, double t1, int nslices,
                            int criterion, double tol, parareal_t* out);
@@ -290,6 +329,18 @@ rbc_status parareal_set_schedule(parareal_t p, int group, int first_group, int f
  * Each extra level holds nslices + 1 and nslices fine states more.  Timing
  * only; RBC_EINVAL outside [0, 6].                                          */
 rbc_status parareal_set_depth(parareal_t p, int depth);
+
+/* Sampling of the Sec. 2.2 time statistics along parareal_iterate's fine
+ * sweeps (rbc_step_batch_sampled): every > 0 samples every `every` fine steps
+ * and at each slice end, 0 turns sampling off (not allowed with
+ * RBC_CRIT_STAT, whose default is one sample per slice end); the averaging
+ * window is the slices [window_first, nslices) (default nslices / 2).
+ * parareal_stat_means writes the window means of the last iteration that
+ * parareal_iterate evaluated (iteration k: the fine trajectories from
+ * U^{k-1}), 6 + 2 Mz doubles in rbc_step_batch_sampled's order, to host
+ * out; RBC_EINVAL before any sampled iteration.                             */
+rbc_status parareal_set_sampling(parareal_t p, int every, int window_first);
+rbc_status parareal_stat_means(parareal_t p, double* out);
 
 /* SMs of the coarse partition in use (0: none), -1 for a NULL handle.      */
 int parareal_coarse_sms(parareal_t p);

@@ -15,7 +15,6 @@ It is a slow, obviously-correct restatement of the method in NumPy/SciPy:
   Nusselt stopping norms (Sec. 3.7) and a statistical stopping rule.
 * ``statistics``     - sampled time means and the consistency checks of
   Sec. 2.2 (Re, Nu_int, the P / eps_U balance, T_rms, delta_T, N_BL).
-* ``survey_dt``      - a time-step stability survey of one propagator.
 
 ``rbc`` also takes fixed-flux walls (Eq. 7) and forms the instantaneous
 averages of Sec. 2.2 (``RBC.diagnostics``).

@@ -301,6 +301,8 @@ struct rbc_s {
   void* d_work = nullptr;
   Work w{};
   double* d_scratch = nullptr;   // set/get state and diagnostics, independent of B
+  double* d_sbuf = nullptr;      // sampled runs: two rows of diagnostics per state and a Nu slot
+  int sbuf_cap = 0;              // states d_sbuf holds
   int last_B = 0;
   // Pinned staging of each call's host arrays (Ra, step counts): a ring of
   // slots, each reused only after the copy that last read it has run, so the
@@ -354,6 +356,11 @@ struct pr_s {
   int fine_streams = 2;       // fine groups of an iteration alternate over this many streams
   int coarse_priority = 1;    // 1: the sweeps on the coarse grid run on high-priority streams
   int depth = 2;              // iterations enqueued beyond the one the host evaluates next
+  // Sampled time statistics of Sec. 2.2 along the fine sweeps (every > 0):
+  // diagnostics every `every` fine steps and at each slice end, trapezoid
+  // integrals per slice; window = slices [window_first, N).
+  int every = 0, window_first = 0;
+  std::vector<double> stat_means;   // window means of the last evaluated iteration
   static constexpr int kFineStreams = 4;
   static constexpr int kMaxDepth = 6;
   // One slot per iteration in flight: iteration k uses slot k % R, R = depth + 2.
@@ -373,6 +380,7 @@ struct pr_s {
     double* C = nullptr;        // 1 coarse state: the sweep's coarse state
     double* I = nullptr;        // [N] Nu_V integrals of the fine sweep
     double* norms = nullptr;    // [N][2]: ||T(U^k_{n+1} - U^{k-1}_{n+1})||^2, ||T(U^k_{n+1})||^2
+    double* stat = nullptr;     // [N][6 + 2 Mz]: sampled time integrals of the fine sweep (every > 0)
     double* partial = nullptr;  // block sums of the correction kernel
     unsigned* counter = nullptr;
     std::vector<cudaEvent_t> ev_step;    // [N] sweep step n done
@@ -792,6 +800,7 @@ extern "C" void rbc_destroy(rbc_t h) {
   cudaFree(h->d_tables);
   cudaFree(h->d_work);
   cudaFree(h->d_scratch);
+  cudaFree(h->d_sbuf);
   delete h;
 }
 
@@ -1239,6 +1248,96 @@ extern "C" rbc_status rbc_diagnostics(rbc_t h, const void* d_states, int B, doub
   return RBC_OK;
 }
 
+// Buffers of a sampled run of B states (grown on demand, as the workspace).
+static rbc_status reserve_sampling(rbc_t h, int B) {
+  if (B <= h->sbuf_cap) return RBC_OK;
+  const size_t D = 6 + 2 * (size_t)h->g.Mz;
+  void* p = nullptr;
+  if (cudaMalloc(&p, (size_t)B * (2 * D + 1) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RBC_ENOMEM, "sampling buffers for %d states", B);
+  }
+  cudaFree(h->d_sbuf);
+  h->d_sbuf = static_cast<double*>(p);
+  h->sbuf_cap = B;
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_step_batch_sampled(rbc_t h, void* d_states, int B, int nsteps, int every,
+                                             double* d_nu_integral, double* d_stat, cudaStream_t stream) {
+  if (!h || B < 0 || nsteps < 0 || every < 1 || (B > 0 && (!d_states || !d_stat)))
+    return fail(RBC_EINVAL, "null argument, B < 0, nsteps < 0 or every < 1");
+  if (B == 0) return RBC_OK;
+  rbc_status s = rbc_reserve(h, B);
+  if (s == RBC_OK) s = reserve_sampling(h, B);
+  if (s != RBC_OK) return s;
+  const Grid& g = h->g;
+  const long D = 6 + 2 * (long)g.Mz;
+  double* X = static_cast<double*>(d_states);
+  double* prev = h->d_sbuf;
+  double* cur = prev + (size_t)B * D;
+  double* nuc = cur + (size_t)B * D;
+  CK(cudaMemsetAsync(d_stat, 0, (size_t)B * D * sizeof(double), stream));
+  if (d_nu_integral) CK(cudaMemsetAsync(d_nu_integral, 0, (size_t)B * sizeof(double), stream));
+  CK(launch_diagnostics(g, h->t, h->w, X, B, prev, stream));
+  CK(launch_stat_sample(g, prev, B, stream));
+  std::vector<int> ns(B, 0);
+  for (int done = 0; done < nsteps;) {
+    const int c = std::min(every, nsteps - done);
+    std::fill(ns.begin(), ns.end(), c);
+    s = rbc_step_batch(h, X, B, ns.data(), nuc, stream);
+    if (s != RBC_OK) return s;
+    if (d_nu_integral) CK(launch_add(d_nu_integral, nuc, B, stream));
+    CK(launch_diagnostics(g, h->t, h->w, X, B, cur, stream));
+    CK(launch_stat_sample(g, cur, B, stream));
+    CK(launch_stat_accum(d_stat, prev, cur, 0.5 * (c * g.dt), (long)B * D, stream));
+    done += c;
+  }
+  return RBC_OK;
+}
+
+// Time means and the checks of Sec. 2.2 from window means of the sampled
+// quantities (see include/rbc.h for the layout of both arrays).
+extern "C" rbc_status rbc_stat_summary(int Nz, double Ra, double Pr, const double* means, double* out) {
+  if (!means || !out || Nz < 8 || (Nz & 1) || !(Pr > 0)) return fail(RBC_EINVAL, "bad arguments");
+  const int Mz = 3 * Nz / 2;
+  const double U = means[0], eps = means[1], wT = means[2], NuV = means[3], Nub = means[4], Nut = means[5];
+  const double* Tm = means + 6;
+  const double* T2 = means + 6 + Mz;
+  const double P = Ra * wT, epsU = std::fabs(eps);
+  out[0] = U;
+  out[1] = U / Pr;                                                               // Re
+  out[2] = NuV;
+  out[3] = Nub;
+  out[4] = Nut;
+  out[5] = std::max(std::fabs(Nub - NuV), std::max(std::fabs(Nub - Nut), std::fabs(NuV - Nut))) / NuV;   // Nu_int
+  out[6] = P;
+  out[7] = epsU;
+  out[8] = P != 0.0 ? std::fabs(P - epsU) / P : NAN;                            // |P - eps_U| / P
+  out[9] = 0.5 / NuV;                                                           // delta_t = 1 / (2 Nu)
+  // T_rms at the padded points z_j = cos(pi j / (Mz - 1)) / 2 (descending), its
+  // peak over the lower half from the bottom wall up (the first maximum), and
+  // the interior native Lobatto points no farther from the wall than it
+  double* Trms = out + 12;
+  for (int j = 0; j < Mz; ++j) Trms[j] = std::sqrt(std::max(T2[j] - Tm[j] * Tm[j], 0.0));
+  double best = 0.0, delta = NAN;
+  for (int j = Mz - 1; j >= 0; --j) {
+    const double z = 0.5 * std::cos(M_PI * j / (Mz - 1));
+    if (!(z < 0.0)) continue;
+    if (Trms[j] > best) {
+      best = Trms[j];
+      delta = z + 0.5;
+    }
+  }
+  int nbl = 0;
+  if (best > 0.0)
+    for (int j = 1; j < Nz - 1; ++j)
+      if (0.5 - 0.5 * std::cos(M_PI * j / (Nz - 1)) <= delta) ++nbl;
+  out[10] = best > 0.0 ? delta : NAN;                                           // delta_T
+  out[11] = nbl;                                                                // N_BL
+  return RBC_OK;
+}
+
 extern "C" rbc_status rbc_l2_temperature(rbc_t h, const void* d_state, double* out, cudaStream_t stream) {
   if (!h || !d_state || !out) return fail(RBC_EINVAL, "null argument");
   rbc_status s = rbc_reserve(h, 1);
@@ -1291,7 +1390,8 @@ static void destroy_slot(pr_s::Slot& S) {
     if (st) cudaStreamDestroy(st);
   rbc_destroy(S.coarse);
   for (rbc_t h : S.fines) rbc_destroy(h);
-  for (void* b : {(void*)S.U, (void*)S.Fin, (void*)S.C, (void*)S.I, (void*)S.norms, (void*)S.partial, (void*)S.counter})
+  for (void* b : {(void*)S.U, (void*)S.Fin, (void*)S.C, (void*)S.I, (void*)S.norms, (void*)S.partial, (void*)S.counter,
+                  (void*)S.stat})
     cudaFree(b);
   S = pr_s::Slot{};
 }
@@ -1336,6 +1436,12 @@ static rbc_status ensure_slot(pr_s* p, int i) {
       for (cudaEvent_t& e : *v) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (cudaEvent_t& e : S.ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  if (p->every > 0 && !S.stat) {
+    if (cudaMalloc(&S.stat, (size_t)N * (6 + 2 * gf.Mz) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RBC_ENOMEM, "Parareal statistics of an iteration");
+    }
+  }
   if (!S.coarse) {
     rbc_status s = clone_handle(p->coarse, &S.coarse);
     if (s == RBC_OK) s = rbc_reserve(S.coarse, 1);
@@ -1349,6 +1455,10 @@ static rbc_status ensure_slot(pr_s* p, int i) {
       if (s != RBC_OK) return s;
       S.fines[j]->w.cancel = p->d_cancel;
     }
+  for (int j = 0; p->every > 0 && j < p->fine_streams; ++j) {
+    rbc_status s = reserve_sampling(S.fines[j], std::min(p->N, p->group));
+    if (s != RBC_OK) return s;
+  }
   int lo = 0, hi = 0;
   CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
   if (!S.sC) CK(cudaStreamCreateWithFlags(&S.sC, cudaStreamNonBlocking));
@@ -1386,7 +1496,7 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
   if (!out) return fail(RBC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!fine || !coarse || nslices < 1 || !(t1 > t0)) return fail(RBC_EINVAL, "bad handles, slices or interval");
-  if (criterion < RBC_CRIT_FIXED || criterion > RBC_CRIT_NU || !(tol >= 0)) return fail(RBC_EINVAL, "bad criterion");
+  if (criterion < RBC_CRIT_FIXED || criterion > RBC_CRIT_STAT || !(tol >= 0)) return fail(RBC_EINVAL, "bad criterion");
   const Grid &gf = fine->g, &gc = coarse->g;
   if (gc.Nx > gf.Nx || gc.Nz > gf.Nz) return fail(RBC_EINVAL, "coarse grid finer than fine grid");
   if (gc.Ra != gf.Ra || gc.Pr != gf.Pr || gc.Lx != gf.Lx || gc.bc != gf.bc)
@@ -1411,6 +1521,9 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
   // priority, two iterations enqueued ahead of the one being evaluated
   p->group = std::max(1, (nslices + 3) / 4);
   p->first_group = std::max(1, (p->group + 3) / 4);
+  // the statistical criterion samples at the slice ends unless told otherwise
+  p->every = criterion == RBC_CRIT_STAT ? nf : 0;
+  p->window_first = nslices / 2;
   const size_t Bc = state_doubles(gc) * sizeof(double);
   bool ok = cudaMalloc(&p->d_Gold, nslices * Bc) == cudaSuccess && cudaMalloc(&p->d_cancel, sizeof(int)) == cudaSuccess &&
             cudaMemset(p->d_cancel, 0, sizeof(int)) == cudaSuccess &&
@@ -1458,6 +1571,26 @@ extern "C" rbc_status parareal_set_schedule(parareal_t p, int group, int first_g
 extern "C" rbc_status parareal_set_depth(parareal_t p, int depth) {
   if (!p || depth < 0 || depth > pr_s::kMaxDepth) return fail(RBC_EINVAL, "depth must be in [0, %d]", pr_s::kMaxDepth);
   p->depth = depth;
+  return RBC_OK;
+}
+
+extern "C" rbc_status parareal_set_sampling(parareal_t p, int every, int window_first) {
+  if (!p || every < 0 || window_first < 0 || window_first >= p->N)
+    return fail(RBC_EINVAL, "every must be >= 0 and window_first in [0, nslices)");
+  if (every == 0 && p->criterion == RBC_CRIT_STAT) return fail(RBC_EINVAL, "the statistical criterion needs samples");
+  p->every = every;
+  p->window_first = window_first;
+  for (int i = 0; i < (int)p->slots.size(); ++i) {
+    rbc_status s = ensure_slot(p, i);
+    if (s != RBC_OK) return s;
+  }
+  return RBC_OK;
+}
+
+extern "C" rbc_status parareal_stat_means(parareal_t p, double* out) {
+  if (!p || !out) return fail(RBC_EINVAL, "null argument");
+  if (p->stat_means.empty()) return fail(RBC_EINVAL, "no sampled iteration yet");
+  std::copy(p->stat_means.begin(), p->stat_means.end(), out);
   return RBC_OK;
 }
 
@@ -1526,7 +1659,10 @@ static rbc_status enqueue_iteration(pr_s* p, int k, int last, const double* d_U0
     const cudaStream_t st = fine_stream(p, S, i);
     const int last_in = a[j] + cnt - 2;
     if (last_in >= std::max(0, k - 2)) CK(cudaStreamWaitEvent(st, P.ev_step[last_in], 0));
-    rbc_status s = rbc_step_batch(S.fines[i], S.Fin + (size_t)a[j] * Sf, cnt, nfv.data(), S.I + a[j], st);
+    double* Fj = S.Fin + (size_t)a[j] * Sf;
+    rbc_status s = p->every > 0 ? rbc_step_batch_sampled(S.fines[i], Fj, cnt, p->nf, p->every, S.I + a[j],
+                                                         S.stat + (size_t)a[j] * (6 + 2 * gf.Mz), st)
+                                : rbc_step_batch(S.fines[i], Fj, cnt, nfv.data(), S.I + a[j], st);
     if (s != RBC_OK) return s;
     CK(cudaEventRecord(S.ev_group[j], st));
     for (int n = a[j]; n < a[j + 1]; ++n) S.slice_group[n] = j;
@@ -1619,6 +1755,10 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
   if (s != RBC_OK) return bail(s);
   std::vector<double> Ih(N, 0.0), nrm(2 * N), In(N);
   double nu_prev = 0.0;
+  const size_t D = 6 + 2 * (size_t)gf.Mz;
+  std::vector<double> Sh(p->every > 0 ? (size_t)N * D : 0), means(D);
+  double stat_prev[6] = {};
+  p->stat_means.clear();
   const int n_half = N / 2;
   const double win = (p->t1 - p->t0) * (double)(N - n_half) / N;
   for (int k = 1; k <= K; ++k) {
@@ -1656,6 +1796,30 @@ extern "C" rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U
     if (p->criterion == RBC_CRIT_DEFECT && defect <= p->tol) stop = true;
     if (p->criterion == RBC_CRIT_NU && k >= 2 && std::fabs(nu - nu_prev) <= p->tol * std::fabs(nu)) stop = true;
     nu_prev = nu;
+    if (p->every > 0) {
+      // window means of the sampled quantities (Sec. 2.2) over the fine
+      // trajectories from U^{k-1}; slices n < k - 1 keep their last values
+      CK(cudaMemcpy(Sh.data() + (size_t)n0 * D, S.stat + (size_t)n0 * D, (size_t)(N - n0) * D * sizeof(double),
+                    cudaMemcpyDeviceToHost));
+      std::fill(means.begin(), means.end(), 0.0);
+      double dur = 0.0;
+      for (int n = p->window_first; n < N; ++n) {
+        for (size_t q = 0; q < D; ++q) means[q] += Sh[(size_t)n * D + q];
+        dur += p->nf * gf.dt;
+      }
+      for (size_t q = 0; q < D; ++q) means[q] /= dur;
+      p->stat_means = means;
+      // reading R22: stop at the first k >= 2 at which Nu_V, Nu_b, Nu_t, Re, P
+      // and eps_U all changed by at most tol relative to iteration k - 1
+      const double st[6] = {means[3], means[4], means[5], means[0] / gf.Pr, gf.Ra * means[2], std::fabs(means[1])};
+      double change = 0.0;
+      for (int q = 0; q < 6; ++q) {
+        if (!std::isfinite(st[q])) return bail(fail(RBC_EDIVERGED, "non-finite time statistics"));
+        change = std::max(change, std::fabs(st[q] - stat_prev[q]) / std::fabs(st[q]));
+      }
+      if (p->criterion == RBC_CRIT_STAT && k >= 2 && change <= p->tol) stop = true;
+      std::copy(st, st + 6, stat_prev);
+    }
     if (stop) {
       result = RBC_OK;
       break;

@@ -147,6 +147,11 @@ cudaError_t launch_nusselt(const Grid& g, const Tables& t, const Work& w, const 
 // Sec. 2.2 averages of B states into out[B][6 + 2 Mz] (layout as rbc_diagnostics)
 cudaError_t launch_diagnostics(const Grid& g, const Tables& t, const Work& w, const double* X, int B, double* out,
                                cudaStream_t s);
+// Time statistics of Sec. 2.2: sampled quantities from diagnostics rows (in
+// place), trapezoid accumulation (acc += h2 (prev + cur); prev = cur), a += b.
+cudaError_t launch_stat_sample(const Grid& g, double* d, int B, cudaStream_t s);
+cudaError_t launch_stat_accum(double* acc, double* prev, const double* cur, double h2, long n, cudaStream_t s);
+cudaError_t launch_add(double* a, const double* b, int n, cudaStream_t s);
 cudaError_t launch_l2_diff(const Grid& g, const Tables& t, const double* A, const double* Bm, int nst,
                            double* out, cudaStream_t s);
 cudaError_t launch_set_state(const Grid& g, const Tables& t, const double* gT, const double* gu,

@@ -1420,6 +1420,58 @@ cudaError_t launch_diagnostics(const Grid& g, const Tables& t, const Work& w, co
   return cudaGetLastError();
 }
 
+// Sampled quantities of the time statistics of Sec. 2.2, in place over B rows
+// of rbc_diagnostics (6 + 2 Mz each): the characteristic speed
+// <u^2 + w^2>_V^(1/2) replaces <u^2 + w^2>_V, and the plane mean of T^2,
+// <(T - <T>_x)^2>_x + <T>_x^2, replaces the plane variance.
+__global__ void k_stat_sample(Grid g, double* d, int B) {
+  const int D = 6 + 2 * g.Mz;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)B * D) return;
+  const int i = (int)(idx % D);
+  if (i == 0) {
+    d[idx] = sqrt(d[idx]);
+  } else if (i >= 6 + g.Mz) {
+    const double tm = d[idx - g.Mz];
+    d[idx] = __dadd_rn(d[idx], __dmul_rn(tm, tm));
+  }
+}
+
+// Trapezoid rule over one sampling interval: acc += h2 (prev + cur), h2 = half
+// the interval; then prev = cur (n values).
+__global__ void k_stat_accum(double* acc, double* prev, const double* cur, double h2, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double c = cur[i];
+  acc[i] = __dadd_rn(acc[i], __dmul_rn(h2, __dadd_rn(prev[i], c)));
+  prev[i] = c;
+}
+
+// a += b (n values)
+__global__ void k_add(double* a, const double* b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += b[i];
+}
+
+cudaError_t launch_stat_sample(const Grid& g, double* d, int B, cudaStream_t s) {
+  const long n = (long)B * (6 + 2 * g.Mz);
+  k_stat_sample<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, d, B);
+  count();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stat_accum(double* acc, double* prev, const double* cur, double h2, long n, cudaStream_t s) {
+  k_stat_accum<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(acc, prev, cur, h2, n);
+  count();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(double* a, const double* b, int n, cudaStream_t s) {
+  k_add<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a, b, n);
+  count();
+  return cudaGetLastError();
+}
+
 // Squared L2(Omega) norms of temperature fields (the defect norm of Sec. 3.7):
 // ||T||^2 = (Lx / 2) sum_m w_m Re(conj(c_m) . Gram c_m), w = 1 for m = 0, 2
 // otherwise (Parseval in x), Gram the exact Chebyshev Gram matrix (z in

@@ -11,16 +11,20 @@
 // which keeps about FP32 accuracy (the mixed mode computes the transforms and
 // products in FP32).
 //
-// CTA per (slice, field, tile of 64 columns).  The X tile (all K) is converted
-// from FP64 into hi/lo TF32 operands in shared memory once; for each 128-row
-// tile of A the K-chunks of A (pre-swizzled images built on the host) are
-// staged in shared memory, one thread issues the MMAs, and the four warps read
+// CTA per (slice, tile of 64 columns, 128-row tile of one field's operator
+// rows).  Thread 0 starts bulk (TMA) copies of the operator images' K-chunks
+// (pre-swizzled on the host, 16 KB each, hi and lo) into a ring of up to four
+// shared-memory stages, while all threads convert the X tile (all K) from FP64
+// into hi/lo TF32 operands; thread 0 then issues the MMAs of each chunk as it
+// lands and refills a stage once its MMAs are done, and the four warps read
 // the 128 x 64 FP32 accumulator from tensor memory and form the fields of the
 // z-inverse output with the ik factors (the epilogue of k_zinv).
 // Operands are K-major with the 128-byte swizzle; every mbarrier wait is bounded
-// and reports through the slice's error flag.
+// and reports through the slice's error flag, and nothing (MMA or copy) is in
+// flight when a kernel frees its tensor memory.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
@@ -71,6 +75,20 @@ __device__ __forceinline__ void commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar)));
 }
 
+// arrive on an mbarrier, announcing `bytes` of bulk-copy transactions for the phase
+__device__ __forceinline__ void arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(mbar)), "r"(bytes) : "memory");
+}
+
+// bulk (TMA) copy of `bytes` contiguous bytes, global -> shared, completing on mbar
+// (both addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(saddr(dst)),
+      "l"(src), "r"(bytes), "r"(saddr(mbar))
+      : "memory");
+}
+
 // bounded wait for the completion of phase `parity` of an mbarrier: at most
 // `limit` polls (limit 0: gives up at once)
 __device__ __forceinline__ bool wait_parity(uint64_t* mbar, uint32_t parity, long long limit) {
@@ -114,20 +132,6 @@ __device__ long long g_wait_limit = kWaitLimit;
 __device__ __forceinline__ void flag_timeout(int* flags, int* err, int b) {
   atomicOr(flags + b, kFlagTimeout);
   if (err) atomicOr(err, kFlagTimeout);
-}
-
-// Before tensor memory is freed, thread 0 waits (with the default limit, never
-// the lowered one) for the commits it issued on the two A buffers, so no MMA
-// is still in flight when the kernel releases its tensor memory and exits.
-// use[i] / issued[i]: completions observed / commits issued on mbarrier i
-// (0, 1: the A buffers; 2: the accumulator).  A wait that gave up observed
-// nothing, so the phases are drained in order.
-__device__ __forceinline__ void drain(uint64_t* mbar, uint32_t* use, const uint32_t* issued) {
-  for (int bb = 0; bb < 3; ++bb)
-    while (use[bb] < issued[bb]) {
-      if (!wait_parity(&mbar[bb], use[bb] & 1, kWaitLimit)) break;
-      use[bb]++;
-    }
 }
 
 }  // namespace
@@ -175,38 +179,82 @@ void tc_zinv_build_images(const Grid& g, const double* zinv, int nops, float* hi
     }
 }
 
-size_t tc_zinv_smem_bytes(const Grid& g) {
+// Operator-image stages (16 KB hi + 16 KB lo per K-chunk) of k_zinv_tc: up to
+// four, as many as fit beside the X tile in 200 KB of shared memory.
+static int tc_zinv_stages(const Grid& g) {
   const int kc = tc_zinv_kchunks(g);
-  // X tile hi/lo (all K), two buffers of the A chunk hi/lo, alignment slack
-  return (size_t)kc * kTileN * 128 * 2 + 2 * 2 * (size_t)kTileM * 128 + 1024;
+  for (int nb = std::min(kc, 4); nb > 1; --nb)
+    if ((size_t)kc * kTileN * 128 * 2 + (size_t)nb * 2 * kTileM * 128 + 1024 <= 200 * 1024) return nb;
+  return 1;
+}
+
+size_t tc_zinv_smem_bytes(const Grid& g) {
+  // X tile hi/lo (all K), the A-chunk stages hi/lo, alignment slack
+  return (size_t)tc_zinv_kchunks(g) * kTileN * 128 * 2 + (size_t)tc_zinv_stages(g) * 2 * kTileM * 128 + 1024;
 }
 
 // Output fields: psi (nops = 4): u, w, d_x omega, d_z omega, d_x u, d_z u (0..5);
 // T (nops = 2): T, d_x T, d_z T (6..8).
+// CTA per (slice, 64-column tile, 128-row tile of one field's operator rows):
+// thread 0 streams the K-chunks of the operator images into a ring of NB
+// stages with bulk (TMA) copies while all threads convert the X tile to hi/lo
+// TF32 operands; thread 0 then issues 3 x 4 MMAs per chunk as each lands,
+// refilling a stage once its MMAs completed; the four warps read the
+// accumulator and form the fields.
 __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict__ Ahi_psi,
                                                  const float* __restrict__ Alo_psi, const float* __restrict__ Ahi_T,
                                                  const float* __restrict__ Alo_T, const double* __restrict__ X,
                                                  size_t S, float* __restrict__ Z, int B, const int* nsteps,
-                                                 const int* step, int* flags, int* err) {
+                                                 const int* step, int* flags, int* err, int NB) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t mbar[3];   // 0, 1: A-chunk buffers free; 2: accumulator ready
+  __shared__ __align__(8) uint64_t full[4], empty[4], accb[1];
   __shared__ uint32_t tmem_base;
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
-  const int b = blockIdx.x / (2 * ntile);
-  const int rem = blockIdx.x - b * 2 * ntile;
-  const int fsel = rem / ntile;               // 0: psi (nops 4), 1: T (nops 2)
-  const int c0 = (rem - fsel * ntile) * kTileN;
+  const int mt4 = tc_zinv_mtiles(g, 4), mt2 = tc_zinv_mtiles(g, 2);
+  const int per_b = ntile * (mt4 + mt2);
+  const int b = blockIdx.x / per_b;
+  int rem = blockIdx.x - b * per_b;
+  const int ct = rem / (mt4 + mt2);
+  const int q = rem - ct * (mt4 + mt2);
+  const int fsel = q < mt4 ? 0 : 1;           // 0: psi (nops 4), 1: T (nops 2)
+  const int t = q < mt4 ? q : q - mt4;        // row tile of the field's operator rows
+  const int c0 = ct * kTileN;
   if (b >= B || !(nsteps == nullptr || *step < nsteps[b])) return;   // uniform per block
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nops = fsel == 0 ? 4 : 2;
   const int f = fsel == 0 ? 1 : 0;            // state field: psi slot 1, T slot 0
-  const float* Ahi = fsel == 0 ? Ahi_psi : Ahi_T;
-  const float* Alo = fsel == 0 ? Alo_psi : Alo_T;
-  const int kc = tc_zinv_kchunks(g), mtiles = tc_zinv_mtiles(g, nops);
+  const int kc = tc_zinv_kchunks(g);
+  const float* Ahi = (fsel == 0 ? Ahi_psi : Ahi_T) + (size_t)t * kc * kTileM * kChunkK;
+  const float* Alo = (fsel == 0 ? Alo_psi : Alo_T) + (size_t)t * kc * kTileM * kChunkK;
+  constexpr uint32_t kChunkBytes = kTileM * kChunkK * 4;   // one image chunk, 16 KB
   unsigned char* sXhi = base;
   unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
-  unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [buf][hi, lo][128 x 128 B]
+  unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [stage][hi, lo][128 x 128 B]
+  uint32_t seen_full[4] = {0, 0, 0, 0}, copies[4] = {0, 0, 0, 0};   // thread 0's bookkeeping
+  uint32_t seen_empty[4] = {0, 0, 0, 0}, commits[4] = {0, 0, 0, 0};
+  uint32_t acc_commits = 0, acc_seen = 0;
+  if (tid == 0) {
+    for (int i = 0; i < NB; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accb[0])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    // the first NB chunks of the operator images start streaming in at once
+    for (int c = 0; c < NB && c < kc; ++c) {
+      unsigned char* ah = sA + (size_t)c * 2 * kTileM * 128;
+      arrive_expect_tx(&full[c], 2 * kChunkBytes);
+      bulk_g2s(ah, Ahi + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
+      bulk_g2s(ah + kTileM * 128, Alo + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
+      copies[c]++;
+    }
+  }
+  if (warp == 0) {
+    __syncwarp();                             // the warp converged again after thread 0's set-up
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
   // X tile -> hi/lo TF32 operands, K-major (row = column of the tile, k = n)
   // (four consecutive columns, two modes, per item: 16-byte loads, several in flight)
   const double* Xb = X + (size_t)b * S;
@@ -236,14 +284,6 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
       *reinterpret_cast<uint32_t*>(sXlo + o) = l;
     }
   }
-  if (tid == 0) {
-    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[i])));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(saddr(&tmem_base)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
   asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -251,54 +291,54 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
   const long long limit = g_wait_limit;
-  uint32_t use[3] = {0, 0, 0};                // completions observed: A buffers 0, 1, accumulator
-  uint32_t issued[3] = {0, 0, 0};             // commits issued on them
-  bool ok = true;
-  float* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
-  const int rows_per_j = nops, jper = kTileM / nops;
-  for (int t = 0; t < mtiles && ok; ++t) {
-    for (int c = 0; c < kc && ok; ++c) {
-      const int gidx = t * kc + c, buf = gidx & 1;
-      if (gidx >= 2) {                        // buffer free once its previous MMAs completed
-        const bool done = wait_parity(&mbar[buf], use[buf] & 1, limit);
-        if (done) use[buf]++;
-        ok = __syncthreads_and(done) != 0;    // one decision for the whole block
-        if (!ok) break;
+  bool issued_all = true;
+  if (tid == 0) {
+    for (int c = 0; c < kc; ++c) {
+      const int buf = c % NB;
+      if (!wait_parity(&full[buf], seen_full[buf] & 1, limit)) {
+        issued_all = false;
+        break;
       }
+      seen_full[buf]++;
+      asm volatile("tcgen05.fence::after_thread_sync;");
       unsigned char* ah = sA + (size_t)buf * 2 * kTileM * 128;
       unsigned char* al = ah + (size_t)kTileM * 128;
-      const float4* gh = reinterpret_cast<const float4*>(Ahi + (size_t)gidx * kTileM * kChunkK);
-      const float4* gl = reinterpret_cast<const float4*>(Alo + (size_t)gidx * kTileM * kChunkK);
-      for (int i = tid; i < kTileM * kChunkK / 4; i += blockDim.x) {
-        reinterpret_cast<float4*>(ah)[i] = __ldg(gh + i);
-        reinterpret_cast<float4*>(al)[i] = __ldg(gl + i);
+      const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
+      const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
+      for (int ks = 0; ks < kChunkK / 8; ++ks) {
+        const uint32_t o = ks * 32;
+        const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+        mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
+        mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
+        mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
       }
-      asm volatile("fence.proxy.async.shared::cta;");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
-        const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
-        for (int ks = 0; ks < kChunkK / 8; ++ks) {
-          const uint32_t o = ks * 32;
-          const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
-          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
-          mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
+      commit(&empty[buf]);
+      commits[buf]++;
+      if (c + NB < kc) {                      // refill the stage once its MMAs are done
+        if (!wait_parity(&empty[buf], seen_empty[buf] & 1, limit)) {
+          issued_all = false;
+          break;
         }
-        commit(&mbar[buf]);
-        if (c == kc - 1) commit(&mbar[2]);
+        seen_empty[buf]++;
+        arrive_expect_tx(&full[buf], 2 * kChunkBytes);
+        bulk_g2s(ah, Ahi + (size_t)(c + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
+        bulk_g2s(al, Alo + (size_t)(c + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
+        copies[buf]++;
       }
-      issued[buf]++;
-      if (c == kc - 1) issued[2]++;
     }
-    if (!ok) break;
-    // accumulator of tile t ready
-    const bool acc_done = wait_parity(&mbar[2], use[2] & 1, limit);
-    if (acc_done) use[2]++;
-    ok = __syncthreads_and(acc_done) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok) break;
+    if (issued_all) {
+      commit(&accb[0]);
+      acc_commits = 1;
+    }
+  }
+  // accumulator ready (thread 0 committed it after the last chunk's MMAs)
+  const bool acc_done = wait_parity(&accb[0], 0, limit);
+  if (tid == 0 && acc_done) acc_seen = 1;
+  const bool ok = __syncthreads_and(acc_done && issued_all) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    float* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
+    const int rows_per_j = nops, jper = kTileM / nops;
     const int r = warp * 32 + lane;           // tile row = TMEM lane
     const int jl = r / rows_per_j, op = r % rows_per_j;
     const int j = t * jper + jl;
@@ -307,11 +347,11 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
       float P[4][16];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int qq = 0; qq < 4; ++qq)
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int src = (lane & ~(rows_per_j - 1)) | (q & (rows_per_j - 1));
-          P[q][i] = __shfl_sync(0xffffffffu, v[i], src);
+          const int src = (lane & ~(rows_per_j - 1)) | (qq & (rows_per_j - 1));
+          P[qq][i] = __shfl_sync(0xffffffffu, v[i], src);
         }
       if (j >= g.Mz) continue;
 #pragma unroll
@@ -357,12 +397,24 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
         }
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();                          // accumulator read before the next tile overwrites it
-    asm volatile("tcgen05.fence::after_thread_sync;");
   }
   if (!ok && tid == 0) flag_timeout(flags, err, b);   // a bounded wait gave up
-  if (tid == 0) drain(mbar, use, issued);
+  if (tid == 0) {
+    // nothing may be in flight when the kernel frees tensor memory and exits:
+    // the MMAs (their commits) and the bulk copies (their stages), with the
+    // default limit, in order
+    for (int i = 0; i < NB; ++i) {
+      while (seen_full[i] < copies[i]) {
+        if (!wait_parity(&full[i], seen_full[i] & 1, kWaitLimit)) break;
+        seen_full[i]++;
+      }
+      while (seen_empty[i] < commits[i]) {
+        if (!wait_parity(&empty[i], seen_empty[i] & 1, kWaitLimit)) break;
+        seen_empty[i]++;
+      }
+    }
+    if (acc_seen < acc_commits) wait_parity(&accb[0], 0, kWaitLimit);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -414,35 +466,77 @@ void tc_zfwd_build_images(const Grid& g, const double* zfwd, int p, float* hi, f
     }
 }
 
-size_t tc_zfwd_smem_bytes(const Grid& g) {
-  return (size_t)tc_zfwd_kchunks(g) * kTileN * 128 * 2 + 2 * 2 * (size_t)kTileM * 128 + 1024;
+// Image stages of k_zfwd_tc, as for k_zinv_tc.
+static int tc_zfwd_stages(const Grid& g) {
+  const int kc = tc_zfwd_kchunks(g);
+  for (int nb = std::min(kc, 4); nb > 1; --nb)
+    if ((size_t)kc * kTileN * 128 * 2 + (size_t)nb * 2 * kTileM * 128 + 1024 <= 200 * 1024) return nb;
+  return 1;
 }
-bool tc_zfwd_supported(const Grid& g) { return tc_zfwd_smem_bytes(g) <= 200 * 1024; }
 
+size_t tc_zfwd_smem_bytes(const Grid& g) {
+  return (size_t)tc_zfwd_kchunks(g) * kTileN * 128 * 2 + (size_t)tc_zfwd_stages(g) * 2 * kTileM * 128 + 1024;
+}
+// Grid-only choices (so a state gives the same bits in any batch): the tensor
+// cores take grids with at least 64 Chebyshev coefficients whose operands fit
+// in 200 KB of shared memory.  Below Nz = 64 a transform is one or two 32-wide
+// K-chunks, and the FP32 CUDA-core kernels finish sooner (measured on a
+// single 128 x 32 slice: 0.123 ms per RK443 step against 0.187 ms).
+bool tc_zfwd_supported(const Grid& g) { return g.Nz >= 64 && tc_zfwd_smem_bytes(g) <= 200 * 1024; }
+
+// CTA per (slice, field, parity, 64-column tile, 128-row tile of W's rows of
+// that parity); the images stream in through the bulk-copy ring of k_zinv_tc.
 __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict__ Whi0, const float* __restrict__ Wlo0,
                                                  const float* __restrict__ Whi1, const float* __restrict__ Wlo1,
                                                  const float* __restrict__ Q, double* __restrict__ F, size_t S, int B,
-                                                 const int* nsteps, const int* step, int* flags, int* err) {
+                                                 const int* nsteps, const int* step, int* flags, int* err, int NB) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t mbar[3];   // 0, 1: A-chunk buffers free; 2: accumulator ready
+  __shared__ __align__(8) uint64_t full[4], empty[4], accb[1];
   __shared__ uint32_t tmem_base;
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
-  const int per_b = 2 * 2 * ntile;
+  const int mtiles = tc_zfwd_mtiles(g);
+  const int per_b = 2 * 2 * ntile * mtiles;
   const int b = blockIdx.x / per_b;
   int rem = blockIdx.x - b * per_b;
-  const int f = rem / (2 * ntile);
-  rem -= f * 2 * ntile;
-  const int p = rem / ntile;
-  const int c0 = (rem - p * ntile) * kTileN;
+  const int f = rem / (2 * ntile * mtiles);
+  rem -= f * 2 * ntile * mtiles;
+  const int p = rem / (ntile * mtiles);
+  rem -= p * ntile * mtiles;
+  const int ct = rem / mtiles, t = rem - ct * mtiles;
+  const int c0 = ct * kTileN;
   if (b >= B || !(nsteps == nullptr || *step < nsteps[b])) return;   // uniform per block
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const float* Ahi = p == 0 ? Whi0 : Whi1;
-  const float* Alo = p == 0 ? Wlo0 : Wlo1;
-  const int kc = tc_zfwd_kchunks(g), mtiles = tc_zfwd_mtiles(g), Mh = (g.Mz + 1) / 2;
+  const int kc = tc_zfwd_kchunks(g), Mh = (g.Mz + 1) / 2;
+  const float* Ahi = (p == 0 ? Whi0 : Whi1) + (size_t)t * kc * kTileM * kChunkK;
+  const float* Alo = (p == 0 ? Wlo0 : Wlo1) + (size_t)t * kc * kTileM * kChunkK;
+  constexpr uint32_t kChunkBytes = kTileM * kChunkK * 4;
   unsigned char* sXhi = base;
   unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
-  unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [buf][hi, lo][128 x 128 B]
+  unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [stage][hi, lo][128 x 128 B]
+  uint32_t seen_full[4] = {0, 0, 0, 0}, copies[4] = {0, 0, 0, 0};
+  uint32_t seen_empty[4] = {0, 0, 0, 0}, commits[4] = {0, 0, 0, 0};
+  uint32_t acc_commits = 0, acc_seen = 0;
+  if (tid == 0) {
+    for (int i = 0; i < NB; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accb[0])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    for (int c = 0; c < NB && c < kc; ++c) {
+      unsigned char* ah = sA + (size_t)c * 2 * kTileM * 128;
+      arrive_expect_tx(&full[c], 2 * kChunkBytes);
+      bulk_g2s(ah, Ahi + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
+      bulk_g2s(ah + kTileM * 128, Alo + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
+      copies[c]++;
+    }
+  }
+  if (warp == 0) {
+    __syncwarp();                             // the warp converged again after thread 0's set-up
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
   // folds of parity p -> hi/lo TF32 operands, K-major (row = column of the tile, k = jh)
   // (four consecutive columns per item: 16-byte loads, several in flight)
   const float* q = Q + (size_t)(b * 2 + f) * g.Mz * g.nm * 2;
@@ -481,14 +575,6 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
       *reinterpret_cast<uint32_t*>(sXlo + o) = l;
     }
   }
-  if (tid == 0) {
-    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[i])));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(saddr(&tmem_base)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
   asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -496,52 +582,52 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
   const long long limit = g_wait_limit;
-  uint32_t use[3] = {0, 0, 0};                // completions observed: A buffers 0, 1, accumulator
-  uint32_t issued[3] = {0, 0, 0};             // commits issued on them
-  bool ok = true;
-  double* Fb = F + (size_t)b * S;
-  for (int t = 0; t < mtiles && ok; ++t) {
-    for (int c = 0; c < kc && ok; ++c) {
-      const int gidx = t * kc + c, buf = gidx & 1;
-      if (gidx >= 2) {                        // buffer free once its previous MMAs completed
-        const bool done = wait_parity(&mbar[buf], use[buf] & 1, limit);
-        if (done) use[buf]++;
-        ok = __syncthreads_and(done) != 0;    // one decision for the whole block
-        if (!ok) break;
+  bool issued_all = true;
+  if (tid == 0) {
+    for (int c = 0; c < kc; ++c) {
+      const int buf = c % NB;
+      if (!wait_parity(&full[buf], seen_full[buf] & 1, limit)) {
+        issued_all = false;
+        break;
       }
+      seen_full[buf]++;
+      asm volatile("tcgen05.fence::after_thread_sync;");
       unsigned char* ah = sA + (size_t)buf * 2 * kTileM * 128;
       unsigned char* al = ah + (size_t)kTileM * 128;
-      const float4* gh = reinterpret_cast<const float4*>(Ahi + (size_t)gidx * kTileM * kChunkK);
-      const float4* gl = reinterpret_cast<const float4*>(Alo + (size_t)gidx * kTileM * kChunkK);
-      for (int i = tid; i < kTileM * kChunkK / 4; i += blockDim.x) {
-        reinterpret_cast<float4*>(ah)[i] = __ldg(gh + i);
-        reinterpret_cast<float4*>(al)[i] = __ldg(gl + i);
+      const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
+      const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
+      for (int ks = 0; ks < kChunkK / 8; ++ks) {
+        const uint32_t o = ks * 32;
+        const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+        mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
+        mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
+        mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
       }
-      asm volatile("fence.proxy.async.shared::cta;");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
-        const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
-        for (int ks = 0; ks < kChunkK / 8; ++ks) {
-          const uint32_t o = ks * 32;
-          const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
-          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
-          mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
+      commit(&empty[buf]);
+      commits[buf]++;
+      if (c + NB < kc) {
+        if (!wait_parity(&empty[buf], seen_empty[buf] & 1, limit)) {
+          issued_all = false;
+          break;
         }
-        commit(&mbar[buf]);
-        if (c == kc - 1) commit(&mbar[2]);
+        seen_empty[buf]++;
+        arrive_expect_tx(&full[buf], 2 * kChunkBytes);
+        bulk_g2s(ah, Ahi + (size_t)(c + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
+        bulk_g2s(al, Alo + (size_t)(c + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
+        copies[buf]++;
       }
-      issued[buf]++;
-      if (c == kc - 1) issued[2]++;
     }
-    if (!ok) break;
-    const bool acc_done = wait_parity(&mbar[2], use[2] & 1, limit);
-    if (acc_done) use[2]++;
-    ok = __syncthreads_and(acc_done) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok) break;
+    if (issued_all) {
+      commit(&accb[0]);
+      acc_commits = 1;
+    }
+  }
+  const bool acc_done = wait_parity(&accb[0], 0, limit);
+  if (tid == 0 && acc_done) acc_seen = 1;
+  const bool ok = __syncthreads_and(acc_done && issued_all) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    double* Fb = F + (size_t)b * S;
     const int n = 2 * (t * kTileM + warp * 32 + lane) + p;   // tile row = TMEM lane
     for (int cc = 0; cc < kTileN; cc += 16) {
       float v[16];
@@ -554,12 +640,21 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
         *reinterpret_cast<double2*>(Fb + soff2(g, f, n, gc >> 1)) = make_double2((double)v[i], (double)v[i + 1]);
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();                          // accumulator read before the next tile overwrites it
-    asm volatile("tcgen05.fence::after_thread_sync;");
   }
   if (!ok && tid == 0) flag_timeout(flags, err, b);   // a bounded wait gave up
-  if (tid == 0) drain(mbar, use, issued);
+  if (tid == 0) {
+    for (int i = 0; i < NB; ++i) {
+      while (seen_full[i] < copies[i]) {
+        if (!wait_parity(&full[i], seen_full[i] & 1, kWaitLimit)) break;
+        seen_full[i]++;
+      }
+      while (seen_empty[i] < commits[i]) {
+        if (!wait_parity(&empty[i], seen_empty[i] & 1, kWaitLimit)) break;
+        seen_empty[i]++;
+      }
+    }
+    if (acc_seen < acc_commits) wait_parity(&accb[0], 0, kWaitLimit);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -575,9 +670,9 @@ cudaError_t launch_zfwd_tc(const Grid& g, const Tables& t, const Work& w, int B,
     allowed = (int)smem;
   }
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
-  k_zfwd_tc<<<(unsigned)(B * 2 * 2 * ntile), 128, smem, s>>>(g, t.tcW_hi[0], t.tcW_lo[0], t.tcW_hi[1], t.tcW_lo[1],
-                                                             reinterpret_cast<const float*>(w.Q), w.F,
-                                                             state_doubles(g), B, w.nsteps, w.step, w.flags, w.err);
+  k_zfwd_tc<<<(unsigned)(B * 2 * 2 * ntile * tc_zfwd_mtiles(g)), 128, smem, s>>>(
+      g, t.tcW_hi[0], t.tcW_lo[0], t.tcW_hi[1], t.tcW_lo[1], reinterpret_cast<const float*>(w.Q), w.F,
+      state_doubles(g), B, w.nsteps, w.step, w.flags, w.err, tc_zfwd_stages(g));
   return cudaGetLastError();
 }
 
@@ -591,12 +686,13 @@ cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const 
     allowed = (int)smem;
   }
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
-  k_zinv_tc<<<(unsigned)(B * 2 * ntile), 128, smem, s>>>(g, t.tcA_psi_hi, t.tcA_psi_lo, t.tcA_T_hi, t.tcA_T_lo, X,
-                                                         state_doubles(g), reinterpret_cast<float*>(w.Z), B, ns,
-                                                         w.step, w.flags, w.err);
+  const int tiles = tc_zinv_mtiles(g, 4) + tc_zinv_mtiles(g, 2);
+  k_zinv_tc<<<(unsigned)(B * ntile * tiles), 128, smem, s>>>(g, t.tcA_psi_hi, t.tcA_psi_lo, t.tcA_T_hi, t.tcA_T_lo, X,
+                                                             state_doubles(g), reinterpret_cast<float*>(w.Z), B, ns,
+                                                             w.step, w.flags, w.err, tc_zinv_stages(g));
   return cudaGetLastError();
 }
 
-bool tc_zinv_supported(const Grid& g) { return tc_zinv_smem_bytes(g) <= 200 * 1024; }
+bool tc_zinv_supported(const Grid& g) { return g.Nz >= 64 && tc_zinv_smem_bytes(g) <= 200 * 1024; }
 
 }  // namespace rbc

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "librbc.so")
 RBC_OK, RBC_EINVAL, RBC_ENOMEM, RBC_ECUDA, RBC_EDIVERGED, RBC_ETIMEOUT, RBC_ENOTCONVERGED = 0, -1, -2, -3, -4, -5, 1
 RBC_FP64, RBC_MIXED = 0, 1
 RBC_FIXED_T, RBC_FIXED_FLUX = 0, 1
-CRIT_FIXED, CRIT_DEFECT, CRIT_NU = 0, 1, 2
+CRIT_FIXED, CRIT_DEFECT, CRIT_NU, CRIT_STAT = 0, 1, 2, 3
 
 EXPORTS = [
     "rbc_last_error", "rbc_create", "rbc_destroy", "rbc_state_bytes", "rbc_workspace_bytes_per_state",
@@ -24,6 +24,7 @@ EXPORTS = [
     "rbc_profile_read", "rbc_launch_count", "rbc_nusselt_static", "rbc_step_batch_ra", "rbc_restrict",
     "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff", "parareal_set_schedule", "parareal_coarse_sms",
     "rbc_diag_size", "rbc_diagnostics", "rbc_set_wait_limit", "parareal_set_depth",
+    "rbc_step_batch_sampled", "rbc_stat_summary", "parareal_set_sampling", "parareal_stat_means",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -82,6 +83,10 @@ def load():
         "rbc_diagnostics": (I, [P, P, I, P, P]),
         "rbc_set_wait_limit": (I, [ctypes.c_longlong]),
         "parareal_set_depth": (I, [P, I]),
+        "rbc_step_batch_sampled": (I, [P, P, I, I, I, P, P, P]),
+        "rbc_stat_summary": (I, [I, D, D, PD, PD]),
+        "parareal_set_sampling": (I, [P, I, I]),
+        "parareal_stat_means": (I, [P, PD]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -224,6 +229,19 @@ class Propagator:
         _check(load().rbc_diagnostics(self.h, _ptr(states), B, _ptr(out), _stream(stream)))
         return out
 
+    def step_batch_sampled(self, states, nsteps, every, stat=None, nu=None, stream=None):
+        """rbc_step_batch_sampled: advance by nsteps with the Sec. 2.2 averages
+        sampled every `every` steps; returns the (B, diag_size) device tensor of
+        their trapezoid time integrals."""
+        import torch
+        B = states.shape[0]
+        if stat is None:
+            stat = torch.empty((B, self.diag_size), dtype=torch.float64, device=states.device)
+        assert stat.shape == (B, self.diag_size) and stat.is_contiguous()
+        _check(load().rbc_step_batch_sampled(self.h, _ptr(states), B, int(nsteps), int(every),
+                                             _ptr(nu) if nu is not None else None, _ptr(stat), _stream(stream)))
+        return stat
+
     def l2_temperature(self, state, stream=None):
         out = np.zeros(1)
         _check(load().rbc_l2_temperature(self.h, _ptr(state), _dptr(out), _stream(stream)))
@@ -256,6 +274,23 @@ def set_wait_limit(polls):
     """Test hook: polls before a tensor-core mbarrier wait gives up (0: at once;
     negative: the default), on the current device."""
     _check(load().rbc_set_wait_limit(int(polls)))
+
+
+STAT_SUMMARY = ("U", "Re", "NuV", "Nub", "Nut", "Nu_int", "P", "eps_U", "balance", "delta_t", "delta_T", "N_BL")
+
+
+def stat_summary(Nz, Ra, Pr, means):
+    """rbc_stat_summary: the Sec. 2.2 quantities from time means (6 + 2 Mz values):
+    a dict of STAT_SUMMARY plus "Trms" (Mz values at the padded points)."""
+    m = np.ascontiguousarray(means, dtype=np.float64)
+    Mz = 3 * Nz // 2
+    assert m.shape == (6 + 2 * Mz,)
+    out = np.zeros(12 + Mz)
+    _check(load().rbc_stat_summary(int(Nz), float(Ra), float(Pr), _dptr(m), _dptr(out)))
+    d = {k: float(out[i]) for i, k in enumerate(STAT_SUMMARY)}
+    d["N_BL"] = int(out[11])
+    d["Trms"] = out[12:].copy()
+    return d
 
 
 def launch_count():
@@ -295,6 +330,18 @@ class Parareal:
         partition for the coarse sweeps, of the overlapped schedule (timing only)."""
         fg = group if first_group is None else first_group
         _check(load().parareal_set_schedule(self.h, group, fg, fine_streams, coarse_priority, coarse_sms))
+
+    def set_sampling(self, every, window_first=None):
+        """Sample the Sec. 2.2 averages every `every` fine steps (and at slice
+        ends) over the window of slices [window_first, nslices)."""
+        wf = self.nslices // 2 if window_first is None else window_first
+        _check(load().parareal_set_sampling(self.h, int(every), int(wf)))
+
+    def stat_means(self):
+        """Window means (6 + 2 Mz) of the last evaluated iteration."""
+        out = np.zeros(6 + 2 * (3 * self.fine.Nz // 2))
+        _check(load().parareal_stat_means(self.h, _dptr(out)))
+        return out
 
     def set_depth(self, depth):
         """Iterations kept enqueued beyond the one being evaluated (0..6, timing only)."""

@@ -3,7 +3,9 @@ the mixed-precision tensor-core kernels give up, the library reports
 RBC_ETIMEOUT, leaves the states concerned as they were, and the context stays
 usable.
 
-The test lowers the wait limit to 0 polls (rbc_set_wait_limit), so that every
+The mixed mode runs its z transforms on the tensor cores on grids with at
+least 64 Chebyshev coefficients, so the tests use 64 x 64.  The test lowers
+the wait limit to 0 polls (rbc_set_wait_limit), so that every
 such wait gives up at once: a wait that nothing will end, made to run out.  The
 kernels then still drain the tensor-core work they issued (with the default
 limit) before they free tensor memory, so nothing is left in flight.
@@ -50,7 +52,7 @@ def mixed_states(rbc, Nx, Nz, B, seed0=30):
 
 @pytest.mark.parametrize("eager", [False, True])
 def test_wait_timeout_reports_etimeout_and_leaves_the_states_unchanged(rbc, eager):
-    Nx, Nz = 64, 32
+    Nx, Nz = 64, 64
     F, st = mixed_states(rbc, Nx, Nz, 3)
     if eager:
         F = rbc.Propagator(1e5, 1.0, 2.0, Nx, Nz, 1e-4, precision=rbc.RBC_MIXED, eager=True)
@@ -86,10 +88,10 @@ def test_fp64_handles_have_no_bounded_waits(rbc):
 
 
 def test_parareal_reports_a_wait_timeout(rbc):
-    Fm = rbc.Propagator(1e5, 1.0, 2.0, 64, 32, 1e-4, precision=rbc.RBC_MIXED)
-    Gm = rbc.Propagator(1e5, 1.0, 2.0, 32, 16, 2e-4, precision=rbc.RBC_MIXED)
+    Fm = rbc.Propagator(1e5, 1.0, 2.0, 64, 64, 1e-4, precision=rbc.RBC_MIXED)
+    Gm = rbc.Propagator(1e5, 1.0, 2.0, 32, 32, 2e-4, precision=rbc.RBC_MIXED)
     U0 = Fm.new_states(1)
-    Fm.set_state(U0[0], initial_temperature(64, 32, seed=5, amplitude=0.3))
+    Fm.set_state(U0[0], initial_temperature(64, 64, seed=5, amplitude=0.3))
     U = Fm.new_states(5)
     P = rbc.Parareal(Fm, Gm, 0.0, 4 * 8e-4, 4)
     with lowered_wait_limit(rbc, 0):

@@ -1,0 +1,86 @@
+"""Parity with the FP64 oracle at the largest grids of the workloads: 512 x 128
+(Ra = 1e7, 64 slices) and 1024 x 256 (Ra = 1e8, 128 slices), in FP64 and in the
+mixed mode, in the launch shape of a full batch.
+
+The batch holds copies of two nonlinear states (a strong seeded perturbation
+advanced by the oracle).  Sampled slices are compared element by element with
+the oracle after two RK443 steps; every copy of a state must equal the first
+bit for bit (a property of the batch at any size).  These sizes run the long
+Chebyshev recurrences of the banded solves, the row kernel at Mx = 768 and
+1536, and the multi-chunk, multi-tile tensor-core transforms of the mixed mode.
+
+Tolerances: 1e-10 relative (max norm over all coefficients) for FP64; for the
+mixed mode the stated 1e-5 (FP32 transforms and products, FP64 solves).
+"""
+import numpy as np
+import pytest
+
+from layout import from_abi, max_rel_diff, to_abi
+from oracle.rbc import RBC
+from paper_2001_01609_gb300.inputs import initial_temperature
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::DeprecationWarning")]
+
+CASES = {
+    "512x128": dict(Nx=512, Nz=128, Ra=1e7, dt=7.8125e-7, B=64),
+    "1024x256": dict(Nx=1024, Nz=256, Ra=1e8, dt=1.5625e-7, B=128),
+}
+STEPS = 2
+TOL = {0: 1e-10, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def rbc():
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc as r
+    r.load()
+    assert torch.cuda.is_available()
+    return r
+
+
+_oracle_cache = {}
+
+
+def oracle_case(name):
+    """Two developed states and their oracle runs (STEPS steps), computed once."""
+    if name not in _oracle_cache:
+        c = CASES[name]
+        o = RBC(c["Ra"], 1.0, 2.0, c["Nx"], c["Nz"], c["dt"])
+        starts, ends, nus = [], [], []
+        for seed in (7, 8):
+            X = o.from_grid(initial_temperature(c["Nx"], c["Nz"], seed=seed, amplitude=0.3))
+            for _ in range(2):
+                X, _ = o.step(X)
+            Y, integ = o.run(X, STEPS)
+            starts.append(X)
+            ends.append(Y)
+            nus.append(integ)
+        _oracle_cache[name] = (starts, ends, nus)
+    return _oracle_cache[name]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_full_batch_matches_oracle_at_large_grids(rbc, name, precision):
+    c = CASES[name]
+    starts, ends, nus = oracle_case(name)
+    B = c["B"]
+    F = rbc.Propagator(c["Ra"], 1.0, 2.0, c["Nx"], c["Nz"], c["dt"], precision=precision)
+    st = F.new_states(B)
+    abi = [torch.from_numpy(to_abi(X)) for X in starts]
+    for b in range(B):
+        st[b].copy_(abi[b % 2])
+    nu = torch.zeros(B, dtype=torch.float64, device="cuda")
+    F.step_batch(st, STEPS, nu)
+    assert F.check_diverged() == rbc.RBC_OK
+    for b in range(2, B):                           # every copy equals the first, bit for bit
+        assert torch.equal(st[b], st[b % 2]), b
+        assert nu[b].item() == nu[b % 2].item()
+    for b in (0, 1, B - 1):
+        err = max_rel_diff(from_abi(st[b].cpu().numpy()), ends[b % 2])
+        assert err < TOL[precision], (b, err)
+        assert abs(nu[b].item() - nus[b % 2]) <= TOL[precision] * abs(nus[b % 2])
+    del st, nu, F
+    torch.cuda.empty_cache()

@@ -4,9 +4,10 @@
   x-means there, Clenshaw-Curtis in z) on random states of several grids;
   the same bits for every batch size and for both handle precisions (the
   transforms run in FP64); B = 0 and bad arguments.
-* StatisticalParareal on the library against oracle.parareal with the
-  statistical criterion; with the fixed count it reproduces the library's own
-  parareal_iterate bit for bit (chunked fine sweeps take the same steps).
+* rbc_step_batch_sampled (the sampled time integrals of Sec. 2.2) against the
+  oracle's sampled run.
+* parareal_iterate with sampling and RBC_CRIT_STAT against oracle.parareal with
+  the statistical criterion; sampling changes no iterate.
 """
 import numpy as np
 import pytest
@@ -112,31 +113,102 @@ def small_problem(N=3, nf=6, nc=3, every=4):
     return Ra, X0, N * nf * fo.dt, oF, oG, diff, summarize
 
 
-@pytest.mark.parametrize("criterion,tol", [("stat", 0.05), ("fixed", 0.0)])
-def test_statistical_parareal_matches_oracle(rbc, criterion, tol):
-    from paper_2001_01609_gb300 import statistics as pst
+def oracle_rows(I, Mz):
+    """The oracle's integrals in rbc_step_batch_sampled's column order."""
+    return np.concatenate([[I[q] for q in ost.SCALARS], I["Tm"], I["T2"]])
+
+
+@pytest.mark.parametrize("nsteps,every", [(7, 3), (5, 50), (6, 1)])
+def test_sampled_run_matches_oracle(rbc, nsteps, every):
+    """rbc_step_batch_sampled: states and trapezoid integrals of the sampled
+    averages (a partial last interval, an interval longer than the run, every
+    step) against the oracle's sampled run, state by state."""
+    Nx, Nz, Ra = 16, 16, 3e4
+    o = RBC(Ra, 1.0, 2.0, Nx, Nz, 2e-3)
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, 2e-3)
+    Xs = [o.from_grid(initial_temperature(Nx, Nz, seed=s, amplitude=0.3)) for s in (1, 2)]
+    st = F.new_states(2)
+    for b, X in enumerate(Xs):
+        st[b].copy_(torch.from_numpy(to_abi(X)))
+    nu = torch.zeros(2, dtype=torch.float64, device="cuda")
+    stat = F.step_batch_sampled(st, nsteps, every, nu=nu)
+    torch.cuda.synchronize()
+    got = stat.cpu().numpy()
+    Mz = 3 * Nz // 2
+    for b, X in enumerate(Xs):
+        Xend, I = ost.run_sampled(o, X, nsteps, every)
+        assert max_rel_diff(from_abi(st[b].cpu().numpy()), Xend) < 1e-12
+        ref = oracle_rows(I, Mz)
+        np.testing.assert_allclose(got[b], ref, rtol=1e-11, atol=1e-15 * np.abs(ref).max())
+        _, integ = o.run(X, nsteps)
+        assert abs(nu[b].item() - integ) <= 1e-11 * abs(integ)
+    with pytest.raises(rbc.RBCError):
+        F.step_batch_sampled(st, 3, 0)
+
+
+def small_problem(N=3, nf=6, nc=3, every=4):
+    Ra = 3e4
+    fo = RBC(Ra, 1.0, 2.0, 16, 16, 2e-3)
+    co = RBC(Ra, 1.0, 2.0, 8, 8, 4e-3)
+    X0 = fo.from_grid(initial_temperature(16, 16, seed=0, amplitude=0.3))
+    zp = fo.padded_z()
+
+    def oF(X):
+        return ost.run_sampled(fo, X, nf, every)
+
+    def oG(X):
+        return prolong(co.run(restrict(X, 8, 8), nc)[0], 16, 16)
+
+    def diff(a, b):
+        return fo.l2_T(a - b) / fo.l2_T(a)
+
+    def summarize(Is):
+        return ost.averages(ost.combine(Is), Ra, 1.0, zp, 16)
+
+    return Ra, X0, N * nf * fo.dt, oF, oG, diff, summarize
+
+
+@pytest.mark.parametrize("criterion,tol,max_iters,depth", [("stat", 0.05, 3, 2), ("fixed", 0.0, 3, 0),
+                                                           ("stat", 1e-12, 2, 1)])
+def test_statistical_parareal_matches_oracle(rbc, criterion, tol, max_iters, depth):
+    """parareal_iterate with the sampled statistics and RBC_CRIT_STAT against
+    oracle.parareal with the statistical rule: the same iteration count and
+    status, iterates, defects and window statistics."""
     N = 3
     Ra, X0, t1, oF, oG, diff, summarize = small_problem(N)
     F = rbc.Propagator(Ra, 1.0, 2.0, 16, 16, 2e-3)
     G = rbc.Propagator(Ra, 1.0, 2.0, 8, 8, 4e-3)
-    P = pst.StatisticalParareal(F, G, 0.0, t1, N, every=4, tol=tol, window_first=1, criterion=criterion)
+    crit = rbc.CRIT_STAT if criterion == "stat" else rbc.CRIT_FIXED
+    P = rbc.Parareal(F, G, 0.0, t1, N, crit, tol)
+    P.set_sampling(4, window_first=1)
+    P.set_depth(depth)
     U0 = F.new_states(1)
     U0[0].copy_(torch.from_numpy(to_abi(X0)))
     U = F.new_states(N + 1)
-    res = P.iterate(U0[0], U, 3)
-    ref = parareal(X0, N, oF, oG, 3, diff, nu_window=(1, None), criterion=criterion, tol=tol,
+    st, k, defects, nus = P.iterate(U0[0], U, max_iters)
+    ref = parareal(X0, N, oF, oG, max_iters, diff, nu_window=(1, None), criterion=criterion, tol=tol,
                    summarize=summarize, change=ost.stat_change)
-    assert res["k"] == ref["k"] and res["status"] == rbc.RBC_OK
+    assert k == ref["k"]
+    if criterion == "stat" and tol < 1e-6:
+        assert st == rbc.RBC_ENOTCONVERGED
+    else:
+        assert st == rbc.RBC_OK
     for n in range(N + 1):
         assert max_rel_diff(from_abi(U[n].cpu().numpy()), ref["U"][n]) < 1e-11, n
-    np.testing.assert_allclose(res["defects"], ref["defects"], rtol=1e-8)
-    for a, b in zip(res["stats"], ref["nus"]):
-        for q in pst.STAT_QUANTITIES + ("Nu_int", "balance"):
-            assert abs(a[q] - b[q]) <= 1e-10 * abs(b[q]), q
+    np.testing.assert_allclose(defects, ref["defects"], rtol=1e-8)
+    got = rbc.stat_summary(16, Ra, 1.0, P.stat_means())
+    last = ref["nus"][-1]
+    for q in ("NuV", "Nub", "Nut", "Re", "P", "eps_U", "Nu_int", "balance", "delta_t"):
+        assert abs(got[q] - last[q]) <= 1e-10 * abs(last[q]), q
+    assert got["N_BL"] == last["N_BL"] and got["delta_T"] == pytest.approx(last["delta_T"], abs=1e-14)
+    # T_rms^2 = <T^2> - <T>^2 cancels at the walls (T fixed there): compare the squares
+    np.testing.assert_allclose(got["Trms"] ** 2, last["Trms"] ** 2, rtol=1e-8, atol=1e-13)
 
 
-def test_statistical_parareal_fixed_equals_library_parareal(rbc):
-    from paper_2001_01609_gb300 import statistics as pst
+def test_sampled_parareal_iterates_equal_the_unsampled_ones(rbc):
+    """Sampling the statistics changes no state: the iterates equal
+    parareal_iterate's without sampling bit for bit (the Nu integrals are
+    summed per sampling interval, so only their last bits may differ)."""
     N, nf, nc = 4, 10, 5
     F = rbc.Propagator(5e4, 1.0, 2.0, 32, 16, 1e-3)
     G = rbc.Propagator(5e4, 1.0, 2.0, 16, 8, 2e-3)
@@ -144,9 +216,14 @@ def test_statistical_parareal_fixed_equals_library_parareal(rbc):
     U0 = F.new_states(1)
     F.set_state(U0[0], initial_temperature(32, 16, seed=5, amplitude=0.3))
     U = F.new_states(N + 1)
-    res = pst.StatisticalParareal(F, G, 0.0, t1, N, every=3, criterion="fixed").iterate(U0[0], U, 2)
+    P = rbc.Parareal(F, G, 0.0, t1, N)
+    P.set_sampling(3)
+    st, k, de, nus = P.iterate(U0[0], U, 2)
     Ulib = F.new_states(N + 1)
-    st, k, de, _ = rbc.Parareal(F, G, 0.0, t1, N).iterate(U0[0], Ulib, 2)
-    assert st == rbc.RBC_OK and k == 2 and res["k"] == 2
+    st2, k2, de2, nus2 = rbc.Parareal(F, G, 0.0, t1, N).iterate(U0[0], Ulib, 2)
+    assert st == st2 == rbc.RBC_OK and k == k2 == 2
     assert torch.equal(U, Ulib)
-    np.testing.assert_allclose(res["defects"], de, rtol=1e-14)
+    np.testing.assert_array_equal(de, de2)
+    np.testing.assert_allclose(nus, nus2, rtol=1e-13)
+    with pytest.raises(rbc.RBCError):
+        rbc.Parareal(F, G, 0.0, t1, N, rbc.CRIT_STAT, 0.01).set_sampling(0)

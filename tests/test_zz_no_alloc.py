@@ -45,7 +45,8 @@ def test_static_scratch_nusselt_matches_rbc_nusselt_on_consecutive_calls():
 
 
 def test_static_scratch_nusselt_on_a_fresh_mixed_precision_handle_allocates_nothing():
-    """A mixed-precision handle runs the tensor-core z-inverse, whose bounded
+    """A mixed-precision handle on a grid of 64 Chebyshev coefficients runs the
+    tensor-core z-inverse, whose bounded
     waits report through an error word: the call keeps that word in the static
     array too.  The handle is fresh (it never reserved a workspace) and the
     device's free memory does not change across the calls."""
@@ -54,7 +55,7 @@ def test_static_scratch_nusselt_on_a_fresh_mixed_precision_handle_allocates_noth
     from paper_2001_01609_gb300 import rbc
     from paper_2001_01609_gb300.inputs import initial_temperature
 
-    Nx, Nz, Ra = 64, 32, 1e5
+    Nx, Nz, Ra = 64, 64, 1e5
     prep = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, 1e-5, precision=rbc.RBC_MIXED)
     st = prep.new_states(2)
     for b in range(2):
