@@ -182,7 +182,7 @@ def fine_group_starts(N, group, first, n0=0):
     return a
 
 
-def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=2):
+def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, reserve_sms=32):
     """Parareal to a stated tolerance against the serial all-FP64 fine propagator
     on the same GPU (Sec. 3.7: iterate until Nu_k is within tol of Nu_{k-1}).
 
@@ -190,7 +190,8 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=2):
     [0, t_end] (the same kernels), with the Nu_V integral of each slice.
     Parareal arms: mixed precision (fine and coarse propagators: FP32
     transforms and products, FP64 solves, correction and norms) and all FP64;
-    RBC_CRIT_NU with tol, iterations enqueued `depth` ahead.  "Equal
+    RBC_CRIT_NU with tol, iterations enqueued `depth` ahead, fine groups kept off
+    `reserve_sms` SMs (the sweeps on the coarse grid use all of them).  "Equal
     Nu accuracy": each arm's Nu (time mean over the second half of the slices)
     is compared with the serial FP64 one.  Device time with CUDA events on the
     caller's stream, after one untimed warm-up iteration per arm."""
@@ -232,6 +233,8 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=2):
         G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dv["dtc"], precision=pg)
         P = rbc.Parareal(F, G, 0.0, dv["t_end"], N, rbc.CRIT_NU, tol)
         P.set_depth(depth)
+        group = -(-N // 4)
+        P.set_schedule(group, -(-group // 4), 2, 1, reserve_sms)
         U = F.new_states(N + 1)
         P.iterate(U0[0], U, 1, stream=stream)                      # warm-up: graphs, workspaces
         el, (st, k, de, nus) = timed(lambda: P.iterate(U0[0], U, max_iters, stream=stream))
@@ -243,7 +246,8 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=2):
                     rbc.RBC_EDIVERGED: "diverged"}.get(st, str(st)),
             iterations=int(k), s=el, speedup_vs_serial_fp64=serial_s / el, defects=[float(x) for x in de],
             nus=[float(x) for x in nus], nu=nu, nu_rel_err_vs_serial_fp64=abs(nu - nu_serial) / abs(nu_serial),
-            equal_nu_accuracy=bool(abs(nu - nu_serial) <= tol * abs(nu_serial)), depth=depth)
+            equal_nu_accuracy=bool(abs(nu - nu_serial) <= tol * abs(nu_serial)), depth=depth,
+            reserve_sms=P.coarse_sms)
         del P, F, G, U
     return out
 
@@ -427,25 +431,108 @@ def run_gb300(args, w):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# Reference arm: the oracle's Parareal on all host cores (the fine solves of
+# the slices in a process pool, as the paper runs one slice per processor),
+# one iteration per step on a bounded sample of the workload.
+# --------------------------------------------------------------------------
+CPU_PARAREAL_SNIPPET = r"""
+import json, multiprocessing as mp, os, sys, time
+sys.path.insert(0, {root!r})
+w, nf, nc, iters, cores = {w!r}, {nf}, {nc}, {iters}, {cores}
+
+def make(Nx, Nz, dt):
+    from oracle.rbc import RBC
+    return RBC(w["Ra"], w["Pr"], w["Lx"], Nx, Nz, dt)
+
+def init():
+    global FINE
+    FINE = make(w["Nx"], w["Nz"], w["dt"])
+
+def fine(U):
+    return FINE.run(U, nf)
+
+if __name__ == "__main__":
+    from oracle.rbc import prolong, restrict
+    from paper_2001_01609_gb300.inputs import initial_temperature
+    N = w["slices"]
+    F = make(w["Nx"], w["Nz"], w["dt"])
+    G = make(w["Nxc"], w["Nzc"], w["dtc"])
+    def coarse(U):
+        return prolong(G.run(restrict(U, w["Nxc"], w["Nzc"]), nc)[0], w["Nx"], w["Nz"])
+    U0 = F.from_grid(initial_temperature(w["Nx"], w["Nz"], seed=w["seed"], Lx=w["Lx"]))
+    ctx = mp.get_context("spawn")
+    out = []
+    with ctx.Pool(cores, initializer=init) as pool:
+        pool.map(fine, [U0] * cores)                     # workers up
+        for it in range(iters):
+            t0 = time.perf_counter()
+            U, Gold = [U0], []
+            for n in range(N):                           # U^0: serial coarse sweep
+                Gold.append(coarse(U[n]))
+                U.append(Gold[-1])
+            Fres = pool.map(fine, U[:N])                 # fine sweep, one slice per worker task
+            Unew = [U0]
+            for n in range(N):                           # correction sweep (Eq. 20)
+                g = coarse(Unew[n])
+                Unew.append(Fres[n][0] + (g - Gold[n]))
+            out.append(time.perf_counter() - t0)
+    print(json.dumps(dict(seconds=out)))
+"""
+
+
+def cpu_model():
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
 def run_reference(args, w):
+    """The oracle's Parareal iteration on all host cores, per step: the coarse
+    sweep U^0, the fine solves of all slices in a process pool, the correction
+    sweep; a bounded sample of the workload (the slice count and grids kept,
+    10 fine and 8 coarse steps per slice: the workload's 3125 : 2500 ratio)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    rates = []
-    for i in range(args.warmup + args.steps):
-        rate, d = cpu_oracle_rate(w, budget_s=4.0)
-        if i >= args.warmup:
-            rates.append((rate, d))
-    total_steps = sum(d["steps"] for _, d in rates)
-    total_s = sum(d["seconds"] for _, d in rates)
-    value = 2 * w["Nx"] * w["Nz"] * total_steps / total_s
-    cpu = dict(value=value, unit=UNIT, cores=1, kind="oracle",
-               sample=f"per step: oracle fine propagator, one slice of the {w['Nx']}x{w['Nz']} grid, "
-                      f"RK443 steps for ~4 s on one host thread")
+    dv = derived(w)
+    cores = os.cpu_count() or 1
+    nf = 10
+    nc = max(1, int(round(nf * dv["nc"] / w["steps_per_slice"])))
+    wd = dict(w, dtc=dv["dtc"])
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = CPU_PARAREAL_SNIPPET.format(root=ROOT, w=wd, nf=nf, nc=nc, iters=args.warmup + args.steps, cores=cores)
+    import tempfile
+    with tempfile.TemporaryDirectory() as tmp:          # spawned workers import the script by path
+        script = os.path.join(tmp, "oracle_parareal.py")
+        with open(script, "w") as fh:
+            fh.write(code)
+        r = subprocess.run([sys.executable, script], capture_output=True, text=True, env=env, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle Parareal failed: " + r.stderr[-2000:])
+    secs = json.loads(r.stdout.strip().splitlines()[-1])["seconds"][args.warmup:]
+    total_s = sum(secs)
+    fine_dof_steps = w["slices"] * nf * dv["dof"]
+    value = fine_dof_steps * args.steps / total_s
+    sample = (f"per step: one oracle Parareal iteration of {w['slices']} slices ({w['Nx']}x{w['Nz']} fine, "
+              f"{w['Nxc']}x{w['Nzc']} coarse), {nf} fine and {nc} coarse steps per slice, fine solves in a "
+              f"pool of {cores} processes, coarse sweeps serial; CPU: {cpu_model()}")
+    cpu = dict(value=value, unit=UNIT, cores=cores, kind="oracle", sample=sample)
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=int(os.environ.get("WORLD_SIZE", "1")),
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=args.workload, Ra=w["Ra"], grid=f"{w['Nx']}x{w['Nz']}", dt=w["dt"]),
+                config=dict(workload=args.workload, Ra=w["Ra"], grid=f"{w['Nx']}x{w['Nz']}",
+                            coarse_grid=f"{w['Nxc']}x{w['Nzc']}", slices=w["slices"], dt=w["dt"],
+                            dt_coarse=dv["dtc"], fine_steps_per_slice_sampled=nf,
+                            coarse_steps_per_slice_sampled=nc,
+                            step="one Parareal iteration (coarse sweep, fine sweep on all cores, correction)"),
                 cpu_baseline=cpu, e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 

@@ -310,20 +310,20 @@ rbc_status parareal_iterate(parareal_t p, const void* d_U0, void* d_U, int max_i
  *                groups alternate over (default 2);
  *  coarse_priority: 1 runs the sweeps on the coarse grid on high-priority
  *                streams (default 1);
- *  coarse_sms:   0 (default) shares all SMs; n > 0 gives the sweeps on the
- *                coarse grid a partition of about n SMs of their own (a green
- *                context; rounded up to the device's partition granularity)
- *                and the fine groups the other SMs, so that the latency-bound
- *                coarse kernels never wait for SMs held by fine batches.
- *                The library's copies of the handles capture their step
- *                graphs in these partitions.  RBC_ECUDA if the driver cannot
+ *  coarse_sms:   0 (default) shares all SMs; n > 0 keeps the fine groups
+ *                off about n SMs (they run in a green context of the other
+ *                SMs; n is rounded up to the device's partition granularity),
+ *                while the sweeps on the coarse grid may use every SM, so
+ *                that their latency-bound kernels always find free SMs.  The
+ *                library's copies of the fine handle capture their step
+ *                graphs in that partition.  RBC_ECUDA if the driver cannot
  *                partition the device (the schedule is then unchanged).
  * RBC_EINVAL outside these ranges.                                          */
 rbc_status parareal_set_schedule(parareal_t p, int group, int first_group, int fine_streams, int coarse_priority,
                                  int coarse_sms);
 
 /* Iterations parareal_iterate keeps enqueued beyond the one it evaluates
- * next (0 to 6, default 2).  0 runs one iteration after another; with depth
+ * next (0 to 6, default 1).  0 runs one iteration after another; with depth
  * d, iteration k + 1 .. k + d run while the host waits for iteration k, and
  * run for nothing (stopped early) when iteration k meets the criterion.
  * Each extra level holds nslices + 1 and nslices fine states more.  Timing
@@ -342,7 +342,7 @@ rbc_status parareal_set_depth(parareal_t p, int depth);
 rbc_status parareal_set_sampling(parareal_t p, int every, int window_first);
 rbc_status parareal_stat_means(parareal_t p, double* out);
 
-/* SMs of the coarse partition in use (0: none), -1 for a NULL handle.      */
+/* SMs kept free of fine groups (0: none), -1 for a NULL handle.           */
 int parareal_coarse_sms(parareal_t p);
 
 /* ---- Instrumentation (outside the paper's method) ----

@@ -355,7 +355,7 @@ struct pr_s {
   int first_group = 0;        // first fine group
   int fine_streams = 2;       // fine groups of an iteration alternate over this many streams
   int coarse_priority = 1;    // 1: the sweeps on the coarse grid run on high-priority streams
-  int depth = 2;              // iterations enqueued beyond the one the host evaluates next
+  int depth = 1;              // iterations enqueued beyond the one the host evaluates next
   // Sampled time statistics of Sec. 2.2 along the fine sweeps (every > 0):
   // diagnostics every `every` fine steps and at each slice end, trapezoid
   // integrals per slice; window = slices [window_first, N).
@@ -394,8 +394,10 @@ struct pr_s {
   int* d_cancel = nullptr;    // read by the slots' step loops: set, they stop early
   cudaStream_t sCancel = nullptr;
   cudaEvent_t ev_begin = nullptr, ev_cancel = nullptr;
-  // Optional SM partition: the sweeps on the coarse grid on `coarse_sms` SMs of
-  // their own (green context 0), the fine groups on the rest (green context 1).
+  // Optional SM reserve: the fine groups run in a green context of the SMs
+  // outside `coarse_sms` reserved ones (gctx[1]; gctx[0] holds the reserve),
+  // while the sweeps on the coarse grid run on the whole device, so that their
+  // latency-bound kernels always find free SMs.
   int coarse_sms = 0;
   CUgreenCtx green[2] = {};
   CUcontext gctx[2] = {};
@@ -1466,28 +1468,19 @@ static rbc_status ensure_slot(pr_s* p, int i) {
   for (int j = 0; j < p->fine_streams; ++j)
     if (!S.sF[j]) CK(cudaStreamCreateWithFlags(&S.sF[j], cudaStreamNonBlocking));
   if (p->gctx[0]) {
-    {
-      CtxScope scope(p->gctx[0]);
-      if (!scope.ok()) return fail(RBC_ECUDA, "cannot enter the SM partition's context");
-      int l2 = 0, h2 = 0;
-      if (!S.pC)
-        CK(cudaDeviceGetStreamPriorityRange(&l2, &h2) == cudaSuccess
-               ? cudaStreamCreateWithPriority(&S.pC, cudaStreamNonBlocking, h2)
-               : cudaErrorUnknown);
-    }
     CtxScope scope(p->gctx[1]);
     if (!scope.ok()) return fail(RBC_ECUDA, "cannot enter the SM partition's context");
     for (int j = 0; j < p->fine_streams; ++j)
       if (!S.pF[j]) CK(cudaStreamCreateWithFlags(&S.pF[j], cudaStreamNonBlocking));
   }
   // handles capture their step graphs in the partition they run in
-  S.coarse->bind_ctx = p->gctx[0];
+  S.coarse->bind_ctx = nullptr;   // the sweeps on the coarse grid may use every SM
   for (int j = 0; j < p->fine_streams; ++j) S.fines[j]->bind_ctx = p->gctx[1];
   return RBC_OK;
 }
 
 static cudaStream_t sweep_stream(const pr_s* p, const pr_s::Slot& S) {
-  return p->gctx[0] ? S.pC : p->coarse_priority ? S.sC_hi : S.sC;
+  return p->coarse_priority ? S.sC_hi : S.sC;
 }
 static cudaStream_t fine_stream(const pr_s* p, const pr_s::Slot& S, int j) { return p->gctx[0] ? S.pF[j] : S.sF[j]; }
 
@@ -1518,7 +1511,7 @@ extern "C" rbc_status parareal_create(rbc_t fine, rbc_t coarse, double t0, doubl
   p->tol = tol;
   // default schedule: largest fine group N/4, first group a quarter of that,
   // groups alternating over two fine streams, sweeps on the coarse grid at high
-  // priority, two iterations enqueued ahead of the one being evaluated
+  // priority, one iteration enqueued ahead of the one being evaluated
   p->group = std::max(1, (nslices + 3) / 4);
   p->first_group = std::max(1, (p->group + 3) / 4);
   // the statistical criterion samples at the slice ends unless told otherwise
