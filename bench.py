@@ -137,11 +137,10 @@ class Clocks:
 # coarse: one slice of 128 x 32; the stage-kernel traffic summary in profiles/),
 # valid only while the kernel sources are those that were captured.
 NCU_TRAFFIC_SOURCES = ("paper_2001_01609_gb300/csrc/rbc_kernels.cu", "paper_2001_01609_gb300/csrc/rbc_internal.h")
-NCU_TRAFFIC_SHA256 = "296cd94db1f3676ad69d1a318435f4f31967abcecbebda345941d172be97d685"
+NCU_TRAFFIC_SHA256 = "566a2407764a7994c4243b817f66217b74a46d672b9bd3185c433a0d9afda09c"
 NCU_TRAFFIC = {
-    "coarse:k_zinv": 128384, "coarse:k_rows": 493568, "coarse:k_zfwd": 116544, "coarse:k_solve": 826688,
-    "fine:k_zinv": 8542144 + 681280, "fine:k_rows": 56724032 + 832, "fine:k_zfwd": 12629120,
-    "fine:k_solve": 23544128,
+    "coarse:k_zinv": 128154, "coarse:k_rows": 494848, "coarse:k_zfwd": 116992, "coarse:k_solve": 825920,
+    "fine:k_zinv": 8897690, "fine:k_rows": 56729088, "fine:k_zfwd": 12619776, "fine:k_solve": 23543488,
 }
 
 
@@ -234,7 +233,12 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
         P = rbc.Parareal(F, G, 0.0, dv["t_end"], N, rbc.CRIT_NU, tol)
         P.set_depth(depth)
         group = -(-N // 4)
-        P.set_schedule(group, -(-group // 4), 2, 1, reserve_sms)
+        first = -(-group // 4)
+        P.set_schedule(group, first, 2, 1, reserve_sms)
+        starts = fine_group_starts(N, group, first)
+        for Bg in sorted({b - a for a, b in zip(starts, starts[1:])}):
+            F.autotune(Bg)
+        G.autotune(1)
         U = F.new_states(N + 1)
         P.iterate(U0[0], U, 1, stream=stream)                      # warm-up: graphs, workspaces
         el, (st, k, de, nus) = timed(lambda: P.iterate(U0[0], U, max_iters, stream=stream))
@@ -285,6 +289,13 @@ def run_gb300(args, w):
     first = args.first_group if args.first_group else (group if group >= N else -(-group // 4))
     P.set_schedule(group, first, args.fine_streams, args.coarse_priority, args.coarse_sms)
     stream = torch.cuda.current_stream()
+    # launch shapes of the batch sizes the schedule uses, picked on the device
+    # (the results do not depend on them)
+    starts0 = fine_group_starts(N, group, first)
+    tuned = {}
+    for Bg in sorted({b - a for a, b in zip(starts0, starts0[1:])}):
+        tuned[f"fine_B{Bg}"] = F.autotune(Bg) + (F.tuned_shapes(Bg),)
+    tuned["coarse_B1"] = G.autotune(1) + (G.tuned_shapes(1),)
     U0 = F.new_states(1)
     Th = initial_temperature(w["Nx"], w["Nz"], seed=w["seed"] + rank, Lx=w["Lx"])
     F.set_state(U0[0], Th)
@@ -338,6 +349,26 @@ def run_gb300(args, w):
     G.profile(False)
     ck = clocks.stop()
     gpu_launches = rbc.launch_count() - launches0
+    # The batched fine propagator at the full batch (all slices in one launch):
+    # per-kernel CUDA-event times of 2 RK443 steps of the 32 fine states, with
+    # the library's algorithmic FP64 flops and bytes, against the FP64 peak and
+    # the measured HBM copy rate.
+    Fb = F.new_states(N)
+    Fb.copy_(U[:N])
+    F.step_batch(Fb, 1, stream=stream)
+    F.profile(True)
+    F.step_batch(Fb, 2, stream=stream)
+    pb = F.profile_read()
+    F.profile(False)
+    hbm = measured_hbm_gbs()
+    fine_batch = {}
+    for kname, v in pb.items():
+        if v["launches"]:
+            sec = v["ms"] / 1e3
+            fine_batch[kname] = dict(us_per_launch=1e6 * sec / v["launches"], fp64_tflops=v["flops"] / sec / 1e12,
+                                     frac_fp64_peak=v["flops"] / sec / 1e12 / (152 * 4 * 2070e6 / 1e12),
+                                     algorithmic_gbs=v["bytes"] / sec / 1e9, frac_hbm=v["bytes"] / sec / 1e9 / hbm)
+    del Fb
     # Time to tolerance (after the timed region): Parareal iterated until the
     # Nu criterion holds, against the serial all-FP64 fine run on this GPU.
     ttt = None if args.no_time_to_tol else time_to_tolerance(rbc, w, dv, U0, stream)
@@ -415,6 +446,9 @@ def run_gb300(args, w):
                                           if group >= N else
                                           "coarse sweep, fine groups and correction sweep overlapped on 3 streams"),
                                 l2="flushed between timed steps (256 MB write)",
+                                autotune={k: dict(heuristic_ms_per_step=v[0], tuned_ms_per_step=v[1],
+                                                  shapes_solve_zfwd_tm_zfwd_nch_rows_cl=list(v[2]))
+                                          for k, v in tuned.items()},
                                 parallelism=f"{world} independent problems" if world > 1 else "single GPU"),
                     e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(U0h.numel() * 8),
                              d2h_bytes_per_step=int(outh.numel() * 8)),
@@ -425,7 +459,12 @@ def run_gb300(args, w):
                                      frac_fp64=diag_flops / diag_s / 1e12 / peak_fp64,
                                      note="rbc_diagnostics (Sec. 2.2 averages) of all slices' fine states, "
                                           "FP64 z inverse plus Parseval and Clenshaw-Curtis reductions"),
-                    time_to_tol=ttt)
+                    time_to_tol=ttt,
+                    fine_batch_roofline=dict(
+                        batch=N, kernels=fine_batch, hbm_peak_gbs=hbm,
+                        note="one launch per kernel covers all 32 fine slices; FP64 peak derived "
+                             "(152 SMs x 4 flop/clk x 2070 MHz), HBM of measured; the batch's working "
+                             "set stays in L2, so the FP64 pipe, not HBM, bounds these kernels"))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -479,6 +518,15 @@ if __name__ == "__main__":
             out.append(time.perf_counter() - t0)
     print(json.dumps(dict(seconds=out)))
 """
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def cpu_model():
@@ -667,6 +715,8 @@ NCU_CASES = {
     "coarse_b1": (1e6, 128, 32, 1.5625e-5, 1),
     "parareal_small": None,   # one Parareal iteration, see run_ncu_case
     "mixed_b8": (1e7, 512, 128, 7.8125e-7, 8),   # RBC_MIXED: tensor-core z transforms
+    "mixed_b32": (1e6, 256, 64, 1.25e-5, 32),    # RBC_MIXED fine batch of the Parareal workload
+    "mixed_coarse_b1": (1e6, 128, 32, 1.5625e-5, 1),   # RBC_MIXED coarse slice (CUDA-core FP32 transforms)
 }
 
 

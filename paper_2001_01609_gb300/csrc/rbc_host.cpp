@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -319,6 +320,14 @@ struct rbc_s {
   std::vector<double> up_ra;
   Prof prof;
   Prof* profp = nullptr;   // the timing record in use: its own, or its template's (Parareal's copies)
+  // Launch shapes picked by rbc_autotune, per batch size; `gen` counts the
+  // changes, so that step graphs captured with other shapes are not reused.
+  struct Tuning {
+    std::map<int, Shapes> byB;
+    unsigned gen = 0;
+  };
+  Tuning tuning;
+  Tuning* tunep = nullptr;   // its own table, or its template's (Parareal's copies)
   // Step loops: a graph whose one node is a device-side while loop over the
   // captured RK443 step (4 stages + counter), so a call of any length is one
   // launch.  A few bindings (states, B, nu) are kept, least recently used out.
@@ -328,6 +337,7 @@ struct rbc_s {
     const void* nu = nullptr;
     int B = -1;
     CUcontext ctx = nullptr;   // the SM partition it was captured in (nullptr: whole GPU)
+    unsigned tune_gen = 0;     // the launch shapes it was captured with
     unsigned long long used = 0;
   };
   static constexpr int kGraphCache = 8;
@@ -754,6 +764,7 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   if (!h) return fail(RBC_ENOMEM, "host allocation");
   h->opts = o;
   h->profp = &h->prof;
+  h->tunep = &h->tuning;
   h->use_graphs = (o.eager == 0);
   cudaGetDevice(&h->device);
   Grid& g = h->g;
@@ -968,7 +979,7 @@ static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExe
   ++h->graph_clock;
   rbc_s::StepGraph* victim = &h->graphs[0];
   for (auto& sg : h->graphs) {
-    if (sg.exec && sg.X == X && sg.B == B && sg.nu == nu && sg.ctx == h->bind_ctx) {
+    if (sg.exec && sg.X == X && sg.B == B && sg.nu == nu && sg.ctx == h->bind_ctx && sg.tune_gen == h->tunep->gen) {
       sg.used = h->graph_clock;
       *out = sg.exec;
       return RBC_OK;
@@ -1029,6 +1040,7 @@ static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExe
   victim->B = B;
   victim->nu = nu;
   victim->ctx = h->bind_ctx;
+  victim->tune_gen = h->tunep->gen;
   victim->used = h->graph_clock;
   *out = victim->exec;
   return RBC_OK;
@@ -1098,6 +1110,10 @@ static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps
   if (!same) {
     rbc_status us = upload_steps(h, B, h_nsteps, h_ra, maxs, stream);
     if (us != RBC_OK) return us;
+  }
+  {
+    auto it = h->tunep->byB.find(B);
+    h->w.shapes = it == h->tunep->byB.end() ? nullptr : &it->second;
   }
   CK(cudaMemsetAsync(w.step, 0, sizeof(int), stream));
   CK(cudaMemsetAsync(w.flags, 0, (size_t)B * sizeof(int), stream));
@@ -1250,6 +1266,109 @@ extern "C" rbc_status rbc_diagnostics(rbc_t h, const void* d_states, int B, doub
   return RBC_OK;
 }
 
+// Device time (ms) of `steps` RK443 steps of the B states X, launched kernel by
+// kernel with the shapes `sh` (after one untimed step).
+static rbc_status time_shapes(rbc_t h, double* X, int B, const Shapes& sh, int steps, cudaStream_t s, float* ms) {
+  Work w = h->w;
+  w.shapes = &sh;
+  w.prof = nullptr;
+  std::vector<int> ns(B, steps + 1);
+  CK(cudaMemcpyAsync(w.nsteps, ns.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(w.step, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(w.flags, 0, (size_t)B * sizeof(int), s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = cudaSuccess;
+  for (int st = 0; st <= steps && e == cudaSuccess; ++st) {
+    if (st == 1) e = cudaEventRecord(e0, s);
+    for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage) e = launch_stage(h->g, h->t, w, X, B, stage, w.nu, s);
+    if (e == cudaSuccess) e = launch_advance(w, s);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(e);
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_autotune(rbc_t h, int B, double out_ms[2], cudaStream_t stream) {
+  if (!h || B < 1) return fail(RBC_EINVAL, "null handle or B < 1");
+  rbc_status s = rbc_reserve(h, B);
+  if (s != RBC_OK) return s;
+  const Grid& g = h->g;
+  const size_t es = g.mixed ? 4 : 8;
+  // a batch of conduction states (finite, and the timing does not depend on the values)
+  double* X = nullptr;
+  if (cudaMalloc(&X, (size_t)B * state_doubles(g) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RBC_ENOMEM, "autotune states");
+  }
+  struct Free {
+    double* p;
+    ~Free() { cudaFree(p); }
+  } fr{X};
+  CK(cudaMemsetAsync(X, 0, (size_t)B * state_doubles(g) * sizeof(double), stream));
+  CK(cudaMemsetAsync(h->w.ra, 0, (size_t)B * sizeof(double), stream));
+  h->up_ns.clear();   // the step counts and Rayleigh numbers on the device are
+  h->up_ra.clear();   // overwritten: the next rbc_step_batch uploads its own
+  const int steps = 3;
+  Shapes best;   // the heuristics
+  float t_best = 0.f;
+  s = time_shapes(h, X, B, best, steps, stream, &t_best);
+  if (s != RBC_OK) return s;
+  const float t_heur = t_best;
+  // coordinate search: row kernel form, then z-forward tile and chunks, then solve tile
+  auto trial = [&](Shapes c) -> rbc_status {
+    if (!shapes_valid(g, c, es)) return RBC_OK;
+    float t = 0.f;
+    rbc_status r = time_shapes(h, X, B, c, steps, stream, &t);
+    if (r != RBC_OK) return r;
+    if (t < t_best) {
+      t_best = t;
+      best = c;
+    }
+    return RBC_OK;
+  };
+  for (int cl = 0; cl <= 1; ++cl) {
+    Shapes c = best;
+    c.rows_cl = cl;
+    if ((s = trial(c)) != RBC_OK) return s;
+  }
+  for (int tm = 4; tm <= 32; tm *= 2)
+    for (int nch = 1; nch <= 8; nch *= 2) {
+      Shapes c = best;
+      c.zfwd_tm = tm;
+      c.zfwd_nch = nch;
+      if ((s = trial(c)) != RBC_OK) return s;
+    }
+  for (int tms = 1; tms <= 16; tms *= 2) {
+    Shapes c = best;
+    c.solve_tms = tms;
+    if ((s = trial(c)) != RBC_OK) return s;
+  }
+  h->tunep->byB[B] = best;
+  h->tunep->gen++;
+  if (out_ms) {
+    out_ms[0] = t_heur / steps;
+    out_ms[1] = t_best / steps;
+  }
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[4]) {
+  if (!h || !out) return fail(RBC_EINVAL, "null argument");
+  const auto it = h->tunep->byB.find(B);
+  const Shapes sh = it == h->tunep->byB.end() ? Shapes{} : it->second;
+  out[0] = sh.solve_tms;
+  out[1] = sh.zfwd_tm;
+  out[2] = sh.zfwd_nch;
+  out[3] = sh.rows_cl;
+  return RBC_OK;
+}
+
 // Buffers of a sampled run of B states (grown on demand, as the workspace).
 static rbc_status reserve_sampling(rbc_t h, int B) {
   if (B <= h->sbuf_cap) return RBC_OK;
@@ -1374,6 +1493,7 @@ static rbc_status clone_handle(rbc_t src, rbc_t* out) {
   h->max_residual = src->max_residual;
   h->t = src->t;                  // d_tables stays null: the tables are src's
   h->profp = src->profp;          // kernel timing goes to the template's record
+  h->tunep = src->tunep;          // and the template's launch shapes apply
   h->use_graphs = src->use_graphs;
   *out = h;
   return RBC_OK;

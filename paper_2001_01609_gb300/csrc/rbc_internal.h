@@ -101,6 +101,17 @@ struct Prof {
   void end(int k, cudaStream_t s, double fl, double by);
 };
 
+// Launch shapes that leave every result unchanged bit for bit (each column's
+// solve, each z-forward sum and each row's arithmetic do not depend on them),
+// picked per batch size by rbc_autotune; 0 (or -1 for rows_cl) keeps the
+// built-in heuristic.
+struct Shapes {
+  int solve_tms = 0;   // Fourier modes per k_solve block (power of two, <= 16)
+  int zfwd_tm = 0;     // Fourier modes per k_zfwd block (power of two, <= 32)
+  int zfwd_nch = 0;    // chunks of the n range per k_zfwd block (1, 2, 4, 8)
+  int rows_cl = -1;    // 1: the clustered row kernel, 0: one block per row
+};
+
 // Per-call workspace pointers (capacity >= B states).
 struct Work {
   double* Xs;      // stage state, B states
@@ -119,6 +130,7 @@ struct Work {
   double* small;   // [16] scalars
   double* ra;      // [B] Rayleigh number of each state
   const int* cancel;   // device word that ends the step loops early when set, or nullptr
+  const Shapes* shapes;   // tuned launch shapes of this batch size, or nullptr
   Prof* prof;      // timing, or nullptr
 };
 
@@ -171,6 +183,8 @@ cudaError_t launch_correct_norm(const Grid& gf, const Grid& gc, const Tables& tf
                                 const double* Gnew, double* Gold, double* C, const double* Uprev, double* U,
                                 double* Fnext, double* partial, unsigned* counter, double* norms, cudaStream_t s);
 size_t rows_smem_bytes(const Grid& g);
+// whether a launch shape can run on this grid (shared memory, threads)
+bool shapes_valid(const Grid& g, const Shapes& sh, size_t es);
 size_t static_scratch_doubles_needed(const Grid& g);
 constexpr size_t kStaticScratchCapacity = (size_t)3 << 17;   // doubles in the static scratch array (3 MiB)
 // Nusselt numbers with all scratch in the static array; *host_flags receives

@@ -1078,7 +1078,34 @@ static int solve_threads(const Grid& g, int tms) {
   const int items = g.nq * 2 * tms;
   return std::min(256, std::max(32, (items + 31) / 32 * 32));
 }
-static size_t solve_smem(const Grid& g, int B) { return (size_t)5 * g.nq * 2 * solve_tile(g, B) * 8; }
+static size_t solve_smem_tms(const Grid& g, int tms) { return (size_t)5 * g.nq * 2 * tms * 8; }
+static size_t solve_smem(const Grid& g, int B) { return solve_smem_tms(g, solve_tile(g, B)); }
+
+// The shapes of a launch: the tuned ones where set, else the heuristics.
+static int solve_tms_of(const Grid& g, const Work& w, int B) {
+  return (w.shapes && w.shapes->solve_tms > 0) ? w.shapes->solve_tms : solve_tile(g, B);
+}
+static int zfwd_tm_of(const Grid& g, const Work& w, int B, size_t es) {
+  return (w.shapes && w.shapes->zfwd_tm > 0) ? w.shapes->zfwd_tm : zfwd_tile(g, B, es);
+}
+static int zfwd_nch_of(const Grid& g, const Work& w, int B, int tm) {
+  return (w.shapes && w.shapes->zfwd_nch > 0) ? w.shapes->zfwd_nch : zfwd_chunks(g, B, tm);
+}
+static bool rows_cl_of(const Grid& g, const Work& w, int B, size_t es) {
+  return (w.shapes && w.shapes->rows_cl >= 0) ? w.shapes->rows_cl != 0 : rows_use_cluster(g, B, es);
+}
+
+bool shapes_valid(const Grid& g, const Shapes& sh, size_t es) {
+  if (sh.solve_tms > 0 && (sh.solve_tms > 16 || (sh.solve_tms & (sh.solve_tms - 1)) ||
+                           solve_smem_tms(g, sh.solve_tms) > 200 * 1024))
+    return false;
+  if (sh.zfwd_tm > 0 && (sh.zfwd_tm > 32 || (sh.zfwd_tm & (sh.zfwd_tm - 1)) ||
+                         (size_t)2 * ((g.Mz + 1) / 2) * sh.zfwd_tm * 2 * es > 200 * 1024))
+    return false;
+  if (sh.zfwd_nch > 0 && (sh.zfwd_nch > 8 || (sh.zfwd_nch & (sh.zfwd_nch - 1)))) return false;
+  if (sh.rows_cl == 1 && rows_cl_bytes(g, es) > 200 * 1024) return false;
+  return true;
+}
 
 __global__ void k_advance(int* step) { *step += 1; }
 
@@ -1205,7 +1232,7 @@ static void launch_transforms_in(const Grid& g, const Tables& t, const T* Bz, co
   if (pf) pf->end(RBC_KERNEL_ZINV, s, zinv_flops(g, B), zinv_bytes(g, B, sizeof(T)));
   const size_t es = sizeof(T);
   if (pf) pf->begin(RBC_KERNEL_ROWS, s);
-  if (rows_use_cluster(g, B, es))
+  if (rows_cl_of(g, w, B, es))
     k_rows_cl<T><<<(unsigned)(B * g.Mz * kRowsCluster), kRowsThreads, rows_cl_bytes(g, es), s>>>(g, tw, Z, Q, w.wT,
                                                                                                B, ns, w.step);
   else
@@ -1229,12 +1256,13 @@ cudaError_t launch_explicit(const Grid& g, const Tables& t, const Work& w, const
 template <typename T>
 static void launch_zfwd(const Grid& g, const T* W, const Work& w, int B, Prof* pf, cudaStream_t s) {
   const size_t S = state_doubles(g), es = sizeof(T);
-  const int tm = zfwd_tile(g, B, es);
+  const int tm = zfwd_tm_of(g, w, B, es);
   const int mt = (g.nm + tm - 1) / tm;
-  const int nch = zfwd_chunks(g, B, tm);
+  const int nch = zfwd_nch_of(g, w, B, tm);
+  const size_t smem = (size_t)2 * ((g.Mz + 1) / 2) * tm * 2 * es;
   if (pf) pf->begin(RBC_KERNEL_ZFWD, s);
-  k_zfwd<T><<<(unsigned)(B * 2 * mt * nch), 128, zfwd_smem(g, B, es), s>>>(g, W, reinterpret_cast<const T*>(w.Q), w.F,
-                                                                            S, B, tm, nch, w.nsteps, w.step);
+  k_zfwd<T><<<(unsigned)(B * 2 * mt * nch), 128, smem, s>>>(g, W, reinterpret_cast<const T*>(w.Q), w.F, S, B, tm, nch,
+                                                            w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_ZFWD, s, zfwd_flops(g, B), zfwd_bytes(g, B, es));
 }
 
@@ -1254,10 +1282,10 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
     launch_zfwd<float>(g, t.zfwd32, w, B, pf, s);
   else
     launch_zfwd<double>(g, t.zfwd, w, B, pf, s);
-  const int tms = solve_tile(g, B);
+  const int tms = solve_tms_of(g, w, B);
   const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
-  k_solve<<<(unsigned)(B * 2 * mtiles), solve_threads(g, tms), solve_smem(g, B), s>>>(
+  k_solve<<<(unsigned)(B * 2 * mtiles), solve_threads(g, tms), solve_smem_tms(g, tms), s>>>(
       g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags, w.err, B, stage, tms, w.ra, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);

@@ -25,6 +25,7 @@ EXPORTS = [
     "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff", "parareal_set_schedule", "parareal_coarse_sms",
     "rbc_diag_size", "rbc_diagnostics", "rbc_set_wait_limit", "parareal_set_depth",
     "rbc_step_batch_sampled", "rbc_stat_summary", "parareal_set_sampling", "parareal_stat_means",
+    "rbc_autotune", "rbc_tuned_shapes",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -87,6 +88,8 @@ def load():
         "rbc_stat_summary": (I, [I, D, D, PD, PD]),
         "parareal_set_sampling": (I, [P, I, I]),
         "parareal_stat_means": (I, [P, PD]),
+        "rbc_autotune": (I, [P, I, PD, P]),
+        "rbc_tuned_shapes": (I, [P, I, PI]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -241,6 +244,19 @@ class Propagator:
         _check(load().rbc_step_batch_sampled(self.h, _ptr(states), B, int(nsteps), int(every),
                                              _ptr(nu) if nu is not None else None, _ptr(stat), _stream(stream)))
         return stat
+
+    def autotune(self, B, stream=None):
+        """rbc_autotune: pick launch shapes for batches of B states (same results,
+        timing only); returns (ms per step with the heuristics, with the pick)."""
+        out = np.zeros(2)
+        _check(load().rbc_autotune(self.h, int(B), _dptr(out), _stream(stream)))
+        return float(out[0]), float(out[1])
+
+    def tuned_shapes(self, B):
+        """(solve modes, z-forward modes, z-forward chunks, clustered rows) kept for B."""
+        out = (ctypes.c_int * 4)()
+        _check(load().rbc_tuned_shapes(self.h, int(B), out))
+        return tuple(out)
 
     def l2_temperature(self, state, stream=None):
         out = np.zeros(1)

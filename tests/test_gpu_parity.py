@@ -396,3 +396,25 @@ def test_mixed_precision_few_steps_within_stated_tolerance(rbc, Nx, Nz, Ra):
     put(st64, 0, X0)
     F64.step_batch(st64, 4)
     assert max_rel_diff(get(st64, 0), ref) < 1e-11 < err
+
+
+@pytest.mark.parametrize("precision,Nx,Nz,B", [(0, 64, 32, 5), (1, 64, 64, 12), (0, 128, 32, 1)])
+def test_autotuned_shapes_give_identical_bits(rbc, precision, Nx, Nz, B):
+    """rbc_autotune only picks launch shapes: a handle with the tuned shapes gives
+    the bits of one with the heuristics."""
+    F = rbc.Propagator(2e4, 1.0, 2.0, Nx, Nz, 2e-4, precision)
+    T = rbc.Propagator(2e4, 1.0, 2.0, Nx, Nz, 2e-4, precision)
+    t_heur, t_best = T.autotune(B)
+    assert 0 < t_best <= t_heur
+    shapes = T.tuned_shapes(B)
+    assert len(shapes) == 4
+    a, b = F.new_states(B), T.new_states(B)
+    for i in range(B):
+        F.set_state(a[i], initial_temperature(Nx, Nz, seed=40 + i, amplitude=0.3))
+    b.copy_(a)
+    na = torch.zeros(B, dtype=torch.float64, device="cuda")
+    nb = torch.zeros(B, dtype=torch.float64, device="cuda")
+    F.step_batch(a, 4, na)
+    T.step_batch(b, 4, nb)
+    assert torch.equal(a, b) and torch.equal(na, nb)
+    assert F.check_diverged() == T.check_diverged() == rbc.RBC_OK
