@@ -372,6 +372,17 @@ def run_gb300(args, w):
     # Time to tolerance (after the timed region): Parareal iterated until the
     # Nu criterion holds, against the serial all-FP64 fine run on this GPU.
     ttt = None if args.no_time_to_tol else time_to_tolerance(rbc, w, dv, U0, stream)
+    # Serving leg (the metric's p50/p99): a short stream of requests of the serving mix
+    srv = None
+    if not args.no_serving and rank == 0:
+        sl = serve(args, "serving_leg", SERVING_LEG, cpu_leg=False, warmup=1)
+        srv = dict(requests=sl["config"]["requests"], latency_s=sl["latency"], requests_per_s=sl["requests_per_s"],
+                   dof_steps_per_s=sl["value"], offered_load=sl["config"]["offered_load"],
+                   peak_active_requests=sl["config"]["peak_active_requests"], failed=sl["failed"],
+                   classes=sorted(sl["config"]["classes"]),
+                   note="Poisson arrivals of the serving mix (Ra log-uniform 1e4..1e8, grids by the N_BL rule, "
+                        "4-64 slices, FP64 or mixed), 10 fine steps per slice, 2 iterations; the full 256-request "
+                        "run is --workload rbc_serving_256req_poisson")
     # Sec. 2.2 diagnostics of all fine states (one rbc_diagnostics call), after the timed region
     dout = F.diagnostics(U[:N])
     for _ in range(3):
@@ -459,7 +470,7 @@ def run_gb300(args, w):
                                      frac_fp64=diag_flops / diag_s / 1e12 / peak_fp64,
                                      note="rbc_diagnostics (Sec. 2.2 averages) of all slices' fine states, "
                                           "FP64 z inverse plus Parseval and Clenshaw-Curtis reductions"),
-                    time_to_tol=ttt,
+                    time_to_tol=ttt, serving=srv,
                     fine_batch_roofline=dict(
                         batch=N, kernels=fine_batch, hbm_peak_gbs=hbm,
                         note="one launch per kernel covers all 32 fine slices; FP64 peak derived "
@@ -590,17 +601,24 @@ SERVING = {
     "rbc_serving_256req_poisson": dict(requests=256, seed=4, fine_steps=10, coarse_ratio=2, max_iters=2,
                                        f_chunk=10, load=0.8),
 }
+# the serving leg of the default bench line: the same request mix, fewer requests
+SERVING_LEG = dict(requests=24, seed=4, fine_steps=10, coarse_ratio=2, max_iters=2, f_chunk=10, load=0.8)
 
 
 def run_serving(args, name):
-    """256 requests, Poisson arrivals at `load` x the calibrated capacity; Ra
+    print(json.dumps(serve(args, name, SERVING[name], cpu_leg=not args.no_cpu_baseline, warmup=args.warmup)),
+          flush=True)
+
+
+def serve(args, name, cfgw, cpu_leg=True, warmup=1):
+    """`requests` requests, Poisson arrivals at `load` x the calibrated capacity; Ra
     log-uniform in [1e4, 1e8], a grid drawn among those with >= 6 points in the
     thermal boundary layer, 4-64 slices, FP64 or mixed precision with p = 1/2,
-    `fine_steps` fine steps per slice and 2 Parareal iterations per request."""
+    `fine_steps` fine steps per slice and 2 Parareal iterations per request.
+    Returns the JSON line (a dict)."""
     import torch
-    cfgw = SERVING[name]
     cpu = None
-    if not args.no_cpu_baseline:
+    if cpu_leg:
         w0 = dict(Ra=1e4, Pr=1.0, Lx=2.0, Nx=64, Nz=32, dt=3.125e-5, seed=0)
         rate, d = cpu_oracle_rate(w0)
         cpu = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
@@ -658,7 +676,7 @@ def run_serving(args, name):
         t += g.exponential(1.0 / rate)
         r.arrival = t
     # warm-up: one request per class, arriving at once (graph captures, lazy setup)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         seen, warm = set(), []
         for r in reqs:
             if r.key not in seen:
@@ -691,7 +709,7 @@ def run_serving(args, name):
         requests=sum(1 for r in reqs if r.key == k), dt=eng.config_for(k).dt_fine,
         dt_coarse=eng.config_for(k).dt_coarse, fine_ms_per_slice_step=1e3 * cost[k][0],
         coarse_ms_per_step=1e3 * cost[k][1]) for k in eng.classes}
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=1, steps=1, warmup=max(1, args.warmup),
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=1, steps=1, warmup=max(1, warmup),
                 ms_per_step=1e3 * makespan, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64+mixed", data="synthetic",
                 config=dict(workload=name, requests=len(reqs), seed=cfgw["seed"], arrivals="Poisson",
@@ -705,8 +723,8 @@ def run_serving(args, name):
                 latency=lat, requests_per_s=len(reqs) / makespan, failed=bad,
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h)),
                 gpu_launches=int(launches), roofline=None, cpu_baseline=cpu, clocks=ck)
-    print(json.dumps(line), flush=True)
     eng.close()
+    return line
 
 
 NCU_CASES = {
@@ -832,6 +850,72 @@ def run_statistics_study():
                           same_iterates_as_unsampled=bool(torch.equal(U, U2)))), flush=True)
 
 
+def run_config3_study():
+    """Config 3 (Ra 1e8, 1024 x 256, 128 slices, mixed precision, Nu criterion):
+    the transient on 128 x 64, which survives it (t = 0.004, reading R24), is
+    prolonged to 1024 x 256; then mixed-precision Parareal to the 1% Nu
+    criterion against the serial all-FP64 fine run on the same GPU, over 40
+    fine steps of 7.8125e-8 per slice (coarse 256 x 64, 20 steps of 1.5625e-7)."""
+    import torch
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc
+    from paper_2001_01609_gb300.inputs import initial_temperature
+    Ra, N, nf, nc, dtf, dtc = 1e8, 128, 40, 20, 7.8125e-8, 1.5625e-7
+    D = rbc.Propagator(Ra, 1.0, 2.0, 128, 64, 1.5625e-7, precision=rbc.RBC_MIXED)
+    x = D.new_states(1)
+    D.set_state(x[0], initial_temperature(128, 64, seed=3))
+    D.step_batch(x, 25600)
+    if D.check_diverged() != rbc.RBC_OK:
+        raise RuntimeError("the 128 x 64 transient diverged")
+    F = rbc.Propagator(Ra, 1.0, 2.0, 1024, 256, dtf, precision=rbc.RBC_MIXED)
+    G = rbc.Propagator(Ra, 1.0, 2.0, 256, 64, dtc, precision=rbc.RBC_MIXED)
+    U0 = F.new_states(1)
+    rbc.prolong(F, D, x, U0)
+    T = N * nf * dtf
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, r
+
+    F64 = rbc.Propagator(Ra, 1.0, 2.0, 1024, 256, dtf)
+    warm = F64.new_states(1)
+    warm.copy_(U0)
+    F64.step_batch(warm, 3)
+    ser = F64.new_states(1)
+    ser.copy_(U0)
+    nus = torch.zeros(N, dtype=torch.float64, device="cuda")
+
+    def serial():
+        for n in range(N):
+            F64.step_batch(ser, nf, nus[n:n + 1])
+    ts, _ = timed(serial)
+    st_s = F64.check_diverged()
+    nu_serial = float(nus[N // 2:].sum().item()) / (T / 2)
+    P = rbc.Parareal(F, G, 0.0, T, N, rbc.CRIT_NU, 0.01)
+    P.set_depth(1)
+    P.set_schedule(32, 8, 2, 1, 32)
+    for Bg in (8, 16, 32):
+        F.autotune(Bg)
+    G.autotune(1)
+    U = F.new_states(N + 1)
+    P.iterate(U0[0], U, 1)
+    tp, (st, k, de, nu) = timed(lambda: P.iterate(U0[0], U, 5))
+    print(json.dumps(dict(study="config3", Ra=Ra, grid="1024x256", coarse_grid="256x64", slices=N,
+                          fine_steps_per_slice=nf, dt=dtf, coarse_steps_per_slice=nc, dt_coarse=dtc,
+                          start="128x64 transient to t = 0.004 (25600 steps of 1.5625e-7), prolonged",
+                          serial_fp64=dict(s=ts, status=st_s, nu=nu_serial),
+                          parareal_mixed=dict(s=tp, status=st, iterations=k, defects=list(map(float, de)),
+                                              nus=list(map(float, nu)), speedup=ts / tp,
+                                              nu_rel_err=abs(float(nu[-1]) - nu_serial) / abs(nu_serial)))),
+          flush=True)
+
+
 def run_ncu_case(name):
     """A small, self-ending case for ncu: one plain (graph-free) RK443 step of a
     batch, or one short Parareal iteration on the bench's grids."""
@@ -886,8 +970,9 @@ def main():
     ap.add_argument("--coarse-sms", type=int, default=0, help="SMs of the coarse sweeps' own partition (0: shared)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the Parareal-to-tolerance runs")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg of the default line")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
-    ap.add_argument("--study", choices=["coarsening", "statistics"],
+    ap.add_argument("--study", choices=["coarsening", "statistics", "config3"],
                     help="the coarsening and slice-count study, or the statistical Parareal run (not bench lines)")
     ap.add_argument("--study-coarse", default="",
                     help="coarse propagators of the coarsening study, e.g. 32x8:3.125e-5,64x16:1.5625e-5")
@@ -904,6 +989,9 @@ def main():
         return
     if args.study == "statistics":
         run_statistics_study()
+        return
+    if args.study == "config3":
+        run_config3_study()
         return
     if args.workload in SERVING:
         if args.impl == "reference":

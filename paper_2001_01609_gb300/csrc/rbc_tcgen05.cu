@@ -195,12 +195,18 @@ size_t tc_zinv_smem_bytes(const Grid& g) {
 
 // Output fields: psi (nops = 4): u, w, d_x omega, d_z omega, d_x u, d_z u (0..5);
 // T (nops = 2): T, d_x T, d_z T (6..8).
-// CTA per (slice, 64-column tile, 128-row tile of one field's operator rows):
-// thread 0 streams the K-chunks of the operator images into a ring of NB
-// stages with bulk (TMA) copies while all threads convert the X tile to hi/lo
-// TF32 operands; thread 0 then issues 3 x 4 MMAs per chunk as each lands,
-// refilling a stage once its MMAs completed; the four warps read the
-// accumulator and form the fields.
+// CTA per (slice, 64-column tile, field, group of 128-row tiles of the field's
+// operator rows): one row tile per CTA when K is at most two 32-wide chunks
+// (the X tile is cheap to convert, and a single slice spreads over more CTAs),
+// all of the field's row tiles otherwise (the X tile, converted once, serves
+// them all).  Thread 0 streams the K-chunks of the operator images, tile after
+// tile, into a ring of NB shared-memory stages with bulk (TMA) copies while all
+// threads convert the X tile to hi/lo TF32 operands; it issues 3 x 4 MMAs per
+// chunk as each lands, refilling a stage once its MMAs completed (so the next
+// tile's chunks arrive during the current tile's epilogue); after each tile
+// the four warps read the accumulator and form the fields.
+__host__ __device__ inline bool tc_zinv_tile_per_cta(const Grid& g) { return tc_zinv_kchunks(g) <= 2; }
+
 __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict__ Ahi_psi,
                                                  const float* __restrict__ Alo_psi, const float* __restrict__ Ahi_T,
                                                  const float* __restrict__ Alo_T, const double* __restrict__ X,
@@ -212,21 +218,25 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   __shared__ uint32_t tmem_base;
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
   const int mt4 = tc_zinv_mtiles(g, 4), mt2 = tc_zinv_mtiles(g, 2);
-  const int per_b = ntile * (mt4 + mt2);
+  const bool one = tc_zinv_tile_per_cta(g);
+  const int units = one ? mt4 + mt2 : 2;      // CTAs per (slice, column tile)
+  const int per_b = ntile * units;
   const int b = blockIdx.x / per_b;
   int rem = blockIdx.x - b * per_b;
-  const int ct = rem / (mt4 + mt2);
-  const int q = rem - ct * (mt4 + mt2);
-  const int fsel = q < mt4 ? 0 : 1;           // 0: psi (nops 4), 1: T (nops 2)
-  const int t = q < mt4 ? q : q - mt4;        // row tile of the field's operator rows
+  const int ct = rem / units;
+  const int q = rem - ct * units;
+  const int fsel = one ? (q < mt4 ? 0 : 1) : q;   // 0: psi (nops 4), 1: T (nops 2)
+  const int t0 = one ? (q < mt4 ? q : q - mt4) : 0;
+  const int t1 = one ? t0 + 1 : (fsel == 0 ? mt4 : mt2);
   const int c0 = ct * kTileN;
   if (b >= B || !(nsteps == nullptr || *step < nsteps[b])) return;   // uniform per block
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nops = fsel == 0 ? 4 : 2;
   const int f = fsel == 0 ? 1 : 0;            // state field: psi slot 1, T slot 0
   const int kc = tc_zinv_kchunks(g);
-  const float* Ahi = (fsel == 0 ? Ahi_psi : Ahi_T) + (size_t)t * kc * kTileM * kChunkK;
-  const float* Alo = (fsel == 0 ? Alo_psi : Alo_T) + (size_t)t * kc * kTileM * kChunkK;
+  const int nchunks = (t1 - t0) * kc;         // the chunks this CTA streams, tile after tile
+  const float* Ahi = (fsel == 0 ? Ahi_psi : Ahi_T) + (size_t)t0 * kc * kTileM * kChunkK;
+  const float* Alo = (fsel == 0 ? Alo_psi : Alo_T) + (size_t)t0 * kc * kTileM * kChunkK;
   constexpr uint32_t kChunkBytes = kTileM * kChunkK * 4;   // one image chunk, 16 KB
   unsigned char* sXhi = base;
   unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accb[0])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     // the first NB chunks of the operator images start streaming in at once
-    for (int c = 0; c < NB && c < kc; ++c) {
+    for (int c = 0; c < NB && c < nchunks; ++c) {
       unsigned char* ah = sA + (size_t)c * 2 * kTileM * 128;
       arrive_expect_tx(&full[c], 2 * kChunkBytes);
       bulk_g2s(ah, Ahi + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
@@ -292,52 +302,54 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
   const long long limit = g_wait_limit;
   bool issued_all = true;
-  if (tid == 0) {
-    for (int c = 0; c < kc; ++c) {
-      const int buf = c % NB;
-      if (!wait_parity(&full[buf], seen_full[buf] & 1, limit)) {
-        issued_all = false;
-        break;
-      }
-      seen_full[buf]++;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      unsigned char* ah = sA + (size_t)buf * 2 * kTileM * 128;
-      unsigned char* al = ah + (size_t)kTileM * 128;
-      const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
-      const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
-      for (int ks = 0; ks < kChunkK / 8; ++ks) {
-        const uint32_t o = ks * 32;
-        const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-        mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
-        mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
-        mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
-      }
-      commit(&empty[buf]);
-      commits[buf]++;
-      if (c + NB < kc) {                      // refill the stage once its MMAs are done
-        if (!wait_parity(&empty[buf], seen_empty[buf] & 1, limit)) {
+  bool ok = true;
+  float* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
+  for (int t = t0; t < t1 && ok; ++t) {
+    if (tid == 0) {
+      for (int c = 0; c < kc; ++c) {
+        const int gi = (t - t0) * kc + c, buf = gi % NB;
+        if (!wait_parity(&full[buf], seen_full[buf] & 1, limit)) {
           issued_all = false;
           break;
         }
-        seen_empty[buf]++;
-        arrive_expect_tx(&full[buf], 2 * kChunkBytes);
-        bulk_g2s(ah, Ahi + (size_t)(c + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
-        bulk_g2s(al, Alo + (size_t)(c + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
-        copies[buf]++;
+        seen_full[buf]++;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        unsigned char* ah = sA + (size_t)buf * 2 * kTileM * 128;
+        unsigned char* al = ah + (size_t)kTileM * 128;
+        const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
+        const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
+        for (int ks = 0; ks < kChunkK / 8; ++ks) {
+          const uint32_t o = ks * 32;
+          const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
+          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
+          mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
+        }
+        commit(&empty[buf]);
+        commits[buf]++;
+        if (gi + NB < nchunks) {              // refill the stage once its MMAs are done
+          if (!wait_parity(&empty[buf], seen_empty[buf] & 1, limit)) {
+            issued_all = false;
+            break;
+          }
+          seen_empty[buf]++;
+          arrive_expect_tx(&full[buf], 2 * kChunkBytes);
+          bulk_g2s(ah, Ahi + (size_t)(gi + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
+          bulk_g2s(al, Alo + (size_t)(gi + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
+          copies[buf]++;
+        }
+      }
+      if (issued_all) {
+        commit(&accb[0]);
+        acc_commits++;
       }
     }
-    if (issued_all) {
-      commit(&accb[0]);
-      acc_commits = 1;
-    }
-  }
-  // accumulator ready (thread 0 committed it after the last chunk's MMAs)
-  const bool acc_done = wait_parity(&accb[0], 0, limit);
-  if (tid == 0 && acc_done) acc_seen = 1;
-  const bool ok = __syncthreads_and(acc_done && issued_all) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok) {
-    float* Zb = Z + (size_t)b * 9 * g.Mz * g.nm * 2;
+    // accumulator of tile t ready (thread 0 committed it after the tile's last chunk)
+    const bool acc_done = wait_parity(&accb[0], (uint32_t)(t - t0) & 1, limit);
+    if (tid == 0 && acc_done) acc_seen++;
+    ok = __syncthreads_and(acc_done && issued_all) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) break;
     const int rows_per_j = nops, jper = kTileM / nops;
     const int r = warp * 32 + lane;           // tile row = TMEM lane
     const int jl = r / rows_per_j, op = r % rows_per_j;
@@ -397,6 +409,9 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
         }
       }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();                          // accumulator read before the next tile overwrites it
+    asm volatile("tcgen05.fence::after_thread_sync;");
   }
   if (!ok && tid == 0) flag_timeout(flags, err, b);   // a bounded wait gave up
   if (tid == 0) {
@@ -413,7 +428,7 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
         seen_empty[i]++;
       }
     }
-    if (acc_seen < acc_commits) wait_parity(&accb[0], 0, kWaitLimit);
+    if (acc_seen < acc_commits) wait_parity(&accb[0], acc_seen & 1, kWaitLimit);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -686,8 +701,8 @@ cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const 
     allowed = (int)smem;
   }
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
-  const int tiles = tc_zinv_mtiles(g, 4) + tc_zinv_mtiles(g, 2);
-  k_zinv_tc<<<(unsigned)(B * ntile * tiles), 128, smem, s>>>(g, t.tcA_psi_hi, t.tcA_psi_lo, t.tcA_T_hi, t.tcA_T_lo, X,
+  const int units = tc_zinv_tile_per_cta(g) ? tc_zinv_mtiles(g, 4) + tc_zinv_mtiles(g, 2) : 2;
+  k_zinv_tc<<<(unsigned)(B * ntile * units), 128, smem, s>>>(g, t.tcA_psi_hi, t.tcA_psi_lo, t.tcA_T_hi, t.tcA_T_lo, X,
                                                              state_doubles(g), reinterpret_cast<float*>(w.Z), B, ns,
                                                              w.step, w.flags, w.err, tc_zinv_stages(g));
   return cudaGetLastError();
