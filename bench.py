@@ -458,7 +458,7 @@ def run_gb300(args, w):
                                           "coarse sweep, fine groups and correction sweep overlapped on 3 streams"),
                                 l2="flushed between timed steps (256 MB write)",
                                 autotune={k: dict(heuristic_ms_per_step=v[0], tuned_ms_per_step=v[1],
-                                                  shapes_solve_zfwd_tm_zfwd_nch_rows_cl=list(v[2]))
+                                                  shapes_solve_zfwd_tm_zfwd_nch_rows_cl_rows_threads=list(v[2]))
                                           for k, v in tuned.items()},
                                 parallelism=f"{world} independent problems" if world > 1 else "single GPU"),
                     e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(U0h.numel() * 8),

@@ -349,16 +349,17 @@ int parareal_coarse_sms(parareal_t p);
  * RK443 steps of a batch of B states with candidate launch shapes that leave
  * every result unchanged bit for bit (modes per stage-solve block, modes and
  * n-chunks per z-forward block, the clustered or the one-block-per-row x-FFT
- * kernel; reduction orders depend on the grid only), by a coordinate search
+ * kernel and the latter's block size; reduction orders depend on the grid
+ * only), by a coordinate search
  * from the built-in heuristics, and keeps the fastest for batches of B states
  * on this handle (and on the library's copies of it that Parareal uses).
  * out_ms (may be NULL): the time per step with the heuristics and with the
  * shapes kept.  Synchronous on `stream`; allocates B scratch states for the
  * duration of the call; RBC_EINVAL for B < 1.  rbc_tuned_shapes writes the
- * shapes kept for B (0 / -1: the heuristic) to host out[4] = (solve modes,
- * z-forward modes, z-forward chunks, clustered rows).                      */
+ * shapes kept for B (0 / -1: the heuristic) to host out[5] = (solve modes,
+ * z-forward modes, z-forward chunks, clustered rows, row-kernel threads).  */
 rbc_status rbc_autotune(rbc_t h, int B, double out_ms[2], cudaStream_t stream);
-rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[4]);
+rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[5]);
 
 /* ---- Instrumentation (outside the paper's method) ----
  * Kernel kinds of one RK443 stage: z-inverse transform, row kernel (x-FFTs and

@@ -1337,6 +1337,11 @@ extern "C" rbc_status rbc_autotune(rbc_t h, int B, double out_ms[2], cudaStream_
     c.rows_cl = cl;
     if ((s = trial(c)) != RBC_OK) return s;
   }
+  for (int th = 512; th <= 1024; th *= 2) {   // block size of the one-block-per-row kernel
+    Shapes c = best;
+    c.rows_threads = th;
+    if ((s = trial(c)) != RBC_OK) return s;
+  }
   for (int tm = 4; tm <= 32; tm *= 2)
     for (int nch = 1; nch <= 8; nch *= 2) {
       Shapes c = best;
@@ -1358,7 +1363,7 @@ extern "C" rbc_status rbc_autotune(rbc_t h, int B, double out_ms[2], cudaStream_
   return RBC_OK;
 }
 
-extern "C" rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[4]) {
+extern "C" rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[5]) {
   if (!h || !out) return fail(RBC_EINVAL, "null argument");
   const auto it = h->tunep->byB.find(B);
   const Shapes sh = it == h->tunep->byB.end() ? Shapes{} : it->second;
@@ -1366,6 +1371,7 @@ extern "C" rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[4]) {
   out[1] = sh.zfwd_tm;
   out[2] = sh.zfwd_nch;
   out[3] = sh.rows_cl;
+  out[4] = sh.rows_threads;
   return RBC_OK;
 }
 

@@ -297,17 +297,19 @@ __device__ C2<T>* fft_smem(C2<T>* a, C2<T>* b, int N, int na, int sign, const C2
       const int arr = it / nb, jj = it - arr * nb;
       const V* xa = x + arr * N;
       V* ya = y + arr * N;
-      const int k = jj % Ns;
+      const int k = jj & (Ns - 1);                  // Ns is a power of two (the radix-3 pass is last)
       V v[4];
       for (int r = 0; r < R; ++r) v[r] = xa[jj + r * nb];
       if (Ns > 1) {
+        // k < Ns and r < R, so k r stride < Ns R stride = N: the index needs no reduction
+        const int kstr = k * stride;
         for (int r = 1; r < R; ++r) {
-          V wv = tw[(k * r * stride) % N];
+          V wv = tw[kstr * r];
           if (sign > 0) wv.y = -wv.y;
           v[r] = cmul(v[r], wv);
         }
       }
-      const int base = (jj / Ns) * Ns * R + k;
+      const int base = (jj - k) * R + k;            // (jj / Ns) Ns R + k
       if (R == 2) {
         ya[base] = v[0] + v[1];
         ya[base + Ns] = v[0] - v[1];
@@ -392,6 +394,27 @@ __device__ __forceinline__ C2<T> rows_packed(const Grid& g, const T* zrow, size_
   return c;
 }
 
+// block_sum over the first 256 threads (the others pass nothing and only meet
+// the barriers): the tree of block_sum at 256 threads, whatever blockDim is.
+__device__ double block_sum256(double v, double* red) {
+  if (threadIdx.x < 256) red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s >= 32; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) {
+    double x = red[threadIdx.x];
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
+    if (threadIdx.x == 0) red[0] = x;
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
 // ---------------------------------------------------------------------------
 // Row kernel (k_rows).  Block per (slice, padded row j).  Pairs of real fields
 // share one complex inverse FFT (C = A + iB with the Hermitian extensions);
@@ -400,7 +423,10 @@ __device__ __forceinline__ C2<T> rows_packed(const Grid& g, const T* zrow, size_
 //   <N_u>_x = <u u_x + w u_z>_x,  <w T>_x;
 // one packed forward FFT (N_T + i N_omega), truncation to m < nm.
 // Q[b][0][j][m] = N_T, Q[b][1][j][m] = N_omega (m >= 1), (<N_u>, 0) at m = 0.
-// The x-means are summed in FP64 in both precision modes.
+// The x-means are summed in FP64 in both precision modes, from per-point
+// terms staged in shared memory: thread t < 256 adds x = t, t + 256, ..., then
+// a 256-wide tree, so the bits do not depend on the block size (256 to 1024
+// threads, a launch shape) and equal those of k_rows_cl.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* __restrict__ Z, T* __restrict__ Q,
@@ -456,19 +482,28 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
   };
   // products into the first row of the buffer not holding the fields
   V* P = (fld == A) ? Bf : A;
-  double nU = 0.0, wt = 0.0;
+  V* P2 = (P == A) ? Bf : A;                           // scratch row for the ping-pong
+  // per-point x-mean terms: the rows after P (batched) or the scratch row
+  // (one row at a time, FP64 only: 2 Mx doubles fit in one complex row)
+  double* vU = reinterpret_cast<double*>(batched ? P + Mx : P2);
+  double* vW = vU + Mx;
   for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
     const T u = field(0, x), w = field(1, x);
     const T nO = fma(u, field(2, x), w * field(3, x));
-    nU += (double)fma(u, field(4, x), w * field(5, x));
+    vU[x] = (double)fma(u, field(4, x), w * field(5, x));
     const T nT = fma(u, field(7, x), w * field(8, x));
-    wt += (double)(w * field(6, x));
+    vW[x] = (double)(w * field(6, x));
     P[x] = mk2<T>(nT, nO);
   }
   __syncthreads();
-  const double sU = block_sum(nU, red);
-  const double sW = block_sum(wt, red);
-  V* P2 = (P == A) ? Bf : A;                           // scratch row for the ping-pong
+  double nU = 0.0, wt = 0.0;
+  if (threadIdx.x < 256)
+    for (int x = threadIdx.x; x < Mx; x += 256) {
+      nU += vU[x];
+      wt += vW[x];
+    }
+  const double sU = block_sum256(nU, red);
+  const double sW = block_sum256(wt, red);
   const V* C = fft_smem<T>(P, P2, Mx, 1, -1, tws);
   const T inv = (T)1 / (T)Mx;
   const T half = (T)0.5 * inv;
@@ -489,7 +524,7 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_rows(Grid g, const C2<T>* __restrict__ tw, const T* __restrict__ Z,
+__global__ void __launch_bounds__(1024) k_rows(Grid g, const C2<T>* __restrict__ tw, const T* __restrict__ Z,
                                               T* __restrict__ Q, double* __restrict__ wT, int B, int batched,
                                               const int* nsteps, const int* step) {
   rows_item<T>(g, tw, Z, Q, wT, B, batched, nsteps, nsteps ? *step : 0, blockIdx.x);
@@ -1094,6 +1129,9 @@ static int zfwd_nch_of(const Grid& g, const Work& w, int B, int tm) {
 static bool rows_cl_of(const Grid& g, const Work& w, int B, size_t es) {
   return (w.shapes && w.shapes->rows_cl >= 0) ? w.shapes->rows_cl != 0 : rows_use_cluster(g, B, es);
 }
+static int rows_threads_of(const Work& w) {
+  return (w.shapes && w.shapes->rows_threads > 0) ? w.shapes->rows_threads : kRowsThreads;
+}
 
 bool shapes_valid(const Grid& g, const Shapes& sh, size_t es) {
   if (sh.solve_tms > 0 && (sh.solve_tms > 16 || (sh.solve_tms & (sh.solve_tms - 1)) ||
@@ -1104,6 +1142,8 @@ bool shapes_valid(const Grid& g, const Shapes& sh, size_t es) {
     return false;
   if (sh.zfwd_nch > 0 && (sh.zfwd_nch > 8 || (sh.zfwd_nch & (sh.zfwd_nch - 1)))) return false;
   if (sh.rows_cl == 1 && rows_cl_bytes(g, es) > 200 * 1024) return false;
+  if (sh.rows_threads != 0 && sh.rows_threads != 256 && sh.rows_threads != 512 && sh.rows_threads != 1024)
+    return false;
   return true;
 }
 
@@ -1236,7 +1276,7 @@ static void launch_transforms_in(const Grid& g, const Tables& t, const T* Bz, co
     k_rows_cl<T><<<(unsigned)(B * g.Mz * kRowsCluster), kRowsThreads, rows_cl_bytes(g, es), s>>>(g, tw, Z, Q, w.wT,
                                                                                                B, ns, w.step);
   else
-    k_rows<T><<<(unsigned)(B * g.Mz), kRowsThreads, rows_smem_for(g, es), s>>>(
+    k_rows<T><<<(unsigned)(B * g.Mz), rows_threads_of(w), rows_smem_for(g, es), s>>>(
         g, tw, Z, Q, w.wT, B, rows_batched(g, es) ? 1 : 0, ns, w.step);
   if (pf) pf->end(RBC_KERNEL_ROWS, s, rows_flops(g, B), rows_bytes(g, B, sizeof(T)));
 }

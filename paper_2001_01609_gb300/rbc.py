@@ -253,8 +253,8 @@ class Propagator:
         return float(out[0]), float(out[1])
 
     def tuned_shapes(self, B):
-        """(solve modes, z-forward modes, z-forward chunks, clustered rows) kept for B."""
-        out = (ctypes.c_int * 4)()
+        """(solve modes, z-forward modes, z-forward chunks, clustered rows, row threads) kept for B."""
+        out = (ctypes.c_int * 5)()
         _check(load().rbc_tuned_shapes(self.h, int(B), out))
         return tuple(out)
 

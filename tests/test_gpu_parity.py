@@ -407,7 +407,7 @@ def test_autotuned_shapes_give_identical_bits(rbc, precision, Nx, Nz, B):
     t_heur, t_best = T.autotune(B)
     assert 0 < t_best <= t_heur
     shapes = T.tuned_shapes(B)
-    assert len(shapes) == 4
+    assert len(shapes) == 5
     a, b = F.new_states(B), T.new_states(B)
     for i in range(B):
         F.set_state(a[i], initial_temperature(Nx, Nz, seed=40 + i, amplitude=0.3))
