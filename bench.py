@@ -188,7 +188,9 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
     Serial fine: one trajectory, B = 1, all FP64, every slice in turn over
     [0, t_end] (the same kernels), with the Nu_V integral of each slice.
     Parareal arms: mixed precision (fine and coarse propagators: FP32
-    transforms and products, FP64 solves, correction and norms) and all FP64;
+    transforms and products, FP64 solves, correction and norms; TF32 hi/lo
+    operands in the fine grid's tensor-core z transforms), the same with BF16
+    hi/lo operands in the fine transforms, and all FP64;
     RBC_CRIT_NU with tol, iterations enqueued `depth` ahead, fine groups kept off
     `reserve_sms` SMs (the sweeps on the coarse grid use all of them).  "Equal
     Nu accuracy": each arm's Nu (time mean over the second half of the slices)
@@ -227,7 +229,10 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
                serial_fine=dict(precision="fp64", s=serial_s, nu=nu_serial,
                                 run=f"B = 1, {N} slices x {nf} steps in turn, same kernels"),
                arms={})
-    for name, pf, pg in (("mixed", rbc.RBC_MIXED, rbc.RBC_MIXED), ("fp64", rbc.RBC_FP64, rbc.RBC_FP64)):
+    pname = {rbc.RBC_MIXED: "mixed", rbc.RBC_MIXED_BF16: "mixed_bf16", rbc.RBC_FP64: "fp64"}
+    for name, pf, pg in (("mixed", rbc.RBC_MIXED, rbc.RBC_MIXED),
+                         ("mixed_bf16", rbc.RBC_MIXED_BF16, rbc.RBC_MIXED),
+                         ("fp64", rbc.RBC_FP64, rbc.RBC_FP64)):
         F = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"], precision=pf)
         G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dv["dtc"], precision=pg)
         P = rbc.Parareal(F, G, 0.0, dv["t_end"], N, rbc.CRIT_NU, tol)
@@ -244,8 +249,7 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
         el, (st, k, de, nus) = timed(lambda: P.iterate(U0[0], U, max_iters, stream=stream))
         nu = float(nus[-1]) if len(nus) else float("nan")
         out["arms"][name] = dict(
-            fine_precision="mixed" if pf == rbc.RBC_MIXED else "fp64",
-            coarse_precision="mixed" if pg == rbc.RBC_MIXED else "fp64",
+            fine_precision=pname[pf], coarse_precision=pname[pg],
             status={rbc.RBC_OK: "tolerance met", rbc.RBC_ENOTCONVERGED: "not converged",
                     rbc.RBC_EDIVERGED: "diverged"}.get(st, str(st)),
             iterations=int(k), s=el, speedup_vs_serial_fp64=serial_s / el, defects=[float(x) for x in de],

@@ -61,14 +61,19 @@ typedef enum {
   RBC_ENOTCONVERGED = 1 /* Parareal reached max_iters without meeting tol      */
 } rbc_status;
 
-enum { RBC_FP64 = 0, RBC_MIXED = 1 };         /* rbc_opts.precision */
+enum { RBC_FP64 = 0, RBC_MIXED = 1, RBC_MIXED_BF16 = 2 };   /* rbc_opts.precision */
 enum { RBC_FIXED_T = 0, RBC_FIXED_FLUX = 1 }; /* rbc_opts.bc (Eqs. 6, 7) */
 enum { RBC_CRIT_FIXED = 0, RBC_CRIT_DEFECT = 1, RBC_CRIT_NU = 2, RBC_CRIT_STAT = 3 };
 
 typedef struct {
   int precision;   /* RBC_FP64: every step in FP64.  RBC_MIXED: transforms and
                       products in FP32, solves, RK combination, Parareal update
-                      and norms in FP64.                                        */
+                      and norms in FP64; from Nz = 64 the z transforms run on
+                      the tensor cores with TF32 operands split in hi and lo
+                      parts (three products: about FP32 accuracy).
+                      RBC_MIXED_BF16: the same with BF16 hi/lo operands (three
+                      products: about 16 bits of the operands, a relative
+                      error near 1e-5 in the transforms).                      */
   int bc;          /* RBC_FIXED_T: T = 1, 0 at the bottom and top walls (Eq. 6).
                       RBC_FIXED_FLUX: dT/dz = -1 at both walls (Eq. 7); Ra is
                       then the flux Rayleigh number Ra_f of Eq. 8.  No-slip

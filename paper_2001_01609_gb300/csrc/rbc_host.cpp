@@ -754,7 +754,7 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   rbc_opts o{RBC_FP64, RBC_FIXED_T, 0};
   if (opts) o = *opts;
   if (o.eager != 0 && o.eager != 1) return fail(RBC_EINVAL, "eager must be 0 or 1");
-  if (o.precision != RBC_FP64 && o.precision != RBC_MIXED)
+  if (o.precision != RBC_FP64 && o.precision != RBC_MIXED && o.precision != RBC_MIXED_BF16)
     return fail(RBC_EINVAL, "precision mode %d not available", o.precision);
   if (o.bc != RBC_FIXED_T && o.bc != RBC_FIXED_FLUX) return fail(RBC_EINVAL, "boundary condition %d not available", o.bc);
   // padded x length 3 Nx / 2 must be 3 * 2^p for the FFT
@@ -779,7 +779,8 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   g.Lx = Lx;
   g.dt = dt;
   g.kfac = 2.0 * M_PI / Lx;
-  g.mixed = (o.precision == RBC_MIXED) ? 1 : 0;
+  g.mixed = (o.precision == RBC_MIXED || o.precision == RBC_MIXED_BF16) ? 1 : 0;
+  g.tcbf16 = (o.precision == RBC_MIXED_BF16) ? 1 : 0;
   g.bc = o.bc;
   rbc_status s = upload_tables(h);
   if (s == RBC_OK) {

@@ -20,7 +20,8 @@ struct Grid {
   int nq;         // coefficients per Chebyshev parity (Nz/2)
   double Ra, Pr, Lx, dt;
   double kfac;    // 2 pi / Lx, k_m = kfac * m
-  int mixed;      // 1: transforms and products in FP32 (RBC_MIXED)
+  int mixed;      // 1: transforms and products in FP32 (RBC_MIXED, RBC_MIXED_BF16)
+  int tcbf16;     // 1: the tensor-core z transforms with BF16 operands (RBC_MIXED_BF16), else TF32
   int bc;         // RBC_FIXED_T or RBC_FIXED_FLUX (temperature boundary rows)
 };
 

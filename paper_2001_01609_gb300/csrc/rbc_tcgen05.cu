@@ -22,6 +22,7 @@
 // Operands are K-major with the 128-byte swizzle; every mbarrier wait is bounded
 // and reports through the slice's error flag, and nothing (MMA or copy) is in
 // flight when a kernel frees its tensor memory.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,14 +37,17 @@ namespace {
 
 constexpr int kTileN = 64;       // columns per CTA (32 Fourier modes x re/im)
 constexpr int kTileM = 128;      // rows per MMA tile
-constexpr int kChunkK = 32;      // TF32 elements per 128-byte swizzle row
+constexpr int kChunkFloats = kTileM * 32;   // one 128-row image chunk of 128-byte rows: 16 KB
 constexpr long long kWaitLimit = 1LL << 24;   // default spin limit of a bounded wait
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// byte offset of element (r, k) (k < 32) in a K-major, 128B-swizzled tile
-__device__ __forceinline__ uint32_t swz(int r, int k) {
-  return (uint32_t)(r * 128 + ((((k * 4) >> 4) ^ (r & 7)) << 4) + ((k * 4) & 15));
+// K-elements per 128-byte swizzle row: 32 TF32 or 64 BF16 values
+__host__ __device__ inline int tc_ke(const Grid& g) { return g.tcbf16 ? 64 : 32; }
+
+// byte offset of the element at byte `kb` (< 128) of row r in a K-major, 128B-swizzled tile
+__host__ __device__ inline uint32_t swz_b(int r, int kb) {
+  return (uint32_t)(r * 128 + (((kb >> 4) ^ (r & 7)) << 4) + (kb & 15));
 }
 
 // shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
@@ -58,6 +62,18 @@ __device__ __forceinline__ uint32_t instr_desc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator, K-major, M x N
+__device__ __forceinline__ uint32_t instr_desc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -69,6 +85,36 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// 3 MMAs (hi*hi, hi*lo, lo*hi) of one 32-byte K-step of the A and X operands
+__device__ __forceinline__ void mma3(bool bf, uint32_t tmem, uint32_t ah, uint32_t al, uint32_t xh, uint32_t xl,
+                                     uint32_t idesc, uint32_t acc0) {
+  if (bf) {
+    mma_bf16(tmem, smem_desc(ah), smem_desc(xh), idesc, acc0);
+    mma_bf16(tmem, smem_desc(ah), smem_desc(xl), idesc, 1u);
+    mma_bf16(tmem, smem_desc(al), smem_desc(xh), idesc, 1u);
+  } else {
+    mma_tf32(tmem, smem_desc(ah), smem_desc(xh), idesc, acc0);
+    mma_tf32(tmem, smem_desc(ah), smem_desc(xl), idesc, 1u);
+    mma_tf32(tmem, smem_desc(al), smem_desc(xh), idesc, 1u);
+  }
+}
+
+// hi/lo split of an FP32 value x into the operand type, stored at byte offset
+// o of the hi and lo tiles: TF32 (cvt.rna) or BF16 (round to nearest even)
+__device__ __forceinline__ void store_split(bool bf, float x, unsigned char* hi, unsigned char* lo, uint32_t o) {
+  if (bf) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    *reinterpret_cast<__nv_bfloat16*>(hi + o) = h;
+    *reinterpret_cast<__nv_bfloat16*>(lo + o) = l;
+  } else {
+    const uint32_t h = to_tf32(x);
+    const uint32_t l = to_tf32(x - __uint_as_float(h));
+    *reinterpret_cast<uint32_t*>(hi + o) = h;
+    *reinterpret_cast<uint32_t*>(lo + o) = l;
+  }
 }
 
 __device__ __forceinline__ void commit(uint64_t* mbar) {
@@ -143,38 +189,63 @@ cudaError_t tc_set_wait_limit(long long limit) {
 
 // Number of 128-row tiles and K-chunks of the operator images (host and device agree).
 __host__ __device__ int tc_zinv_mtiles(const Grid& g, int nops) { return (nops * g.Mz + kTileM - 1) / kTileM; }
-__host__ __device__ int tc_zinv_kchunks(const Grid& g) { return (g.Nz + kChunkK - 1) / kChunkK; }
+__host__ __device__ int tc_zinv_kchunks(const Grid& g) { return (g.Nz + tc_ke(g) - 1) / tc_ke(g); }
 size_t tc_zinv_image_floats(const Grid& g, int nops) {
-  return (size_t)tc_zinv_mtiles(g, nops) * tc_zinv_kchunks(g) * kTileM * kChunkK;
+  return (size_t)tc_zinv_mtiles(g, nops) * tc_zinv_kchunks(g) * kChunkFloats;
+}
+
+// hi/lo split of v into the operand type of the grid, written at byte offset
+// `off` of the hi and lo chunks: TF32 (hi = v rounded to 10 mantissa bits, lo
+// = the rest, rounded alike) or BF16 (hi = v rounded to nearest even on 7
+// mantissa bits, lo = the rest, rounded alike).
+static void split_store(const Grid& g, double v, float* hi, float* lo, int off) {
+  if (g.tcbf16) {
+    auto bf = [](float x) {
+      uint32_t u;
+      memcpy(&u, &x, 4);
+      u += 0x7FFFu + ((u >> 16) & 1u);          // round to nearest, ties to even
+      return (uint16_t)(u >> 16);
+    };
+    auto fl = [](uint16_t b) {
+      const uint32_t u = (uint32_t)b << 16;
+      float x;
+      memcpy(&x, &u, 4);
+      return x;
+    };
+    const uint16_t h = bf((float)v);
+    const uint16_t l = bf((float)(v - (double)fl(h)));
+    memcpy(reinterpret_cast<unsigned char*>(hi) + off, &h, 2);
+    memcpy(reinterpret_cast<unsigned char*>(lo) + off, &l, 2);
+    return;
+  }
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  float h;
+  memcpy(&h, &u, 4);
+  float l = (float)(v - (double)h);
+  memcpy(&u, &l, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  memcpy(&l, &u, 4);
+  memcpy(reinterpret_cast<unsigned char*>(hi) + off, &h, 4);
+  memcpy(reinterpret_cast<unsigned char*>(lo) + off, &l, 4);
 }
 
 // Pre-swizzled hi/lo operator images for field f (nops operators per row j),
 // [mtile][kchunk][128 x 32 swizzled].  d[q][j][n] = d^q T_n / ds^q at s_j.
 void tc_zinv_build_images(const Grid& g, const double* zinv, int nops, float* hi, float* lo) {
-  const int mt = tc_zinv_mtiles(g, nops), kc = tc_zinv_kchunks(g);
+  const int mt = tc_zinv_mtiles(g, nops), kc = tc_zinv_kchunks(g), ke = tc_ke(g), es = 128 / ke;
   for (int t = 0; t < mt; ++t)
     for (int c = 0; c < kc; ++c) {
-      float* bh = hi + ((size_t)t * kc + c) * kTileM * kChunkK;
-      float* bl = lo + ((size_t)t * kc + c) * kTileM * kChunkK;
+      float* bh = hi + ((size_t)t * kc + c) * kChunkFloats;
+      float* bl = lo + ((size_t)t * kc + c) * kChunkFloats;
       for (int r = 0; r < kTileM; ++r)
-        for (int k = 0; k < kChunkK; ++k) {
-          const int row = t * kTileM + r, j = row / nops, q = row % nops, n = c * kChunkK + k;
+        for (int k = 0; k < ke; ++k) {
+          const int row = t * kTileM + r, j = row / nops, q = row % nops, n = c * ke + k;
           double v = 0.0;
           if (j < g.Mz && n < g.Nz) v = zinv[((size_t)q * g.Mz + j) * g.Nz + n];
-          // TF32 split: hi = v rounded to 10 mantissa bits, lo = the rest
-          float f = (float)v;
-          uint32_t u;
-          memcpy(&u, &f, 4);
-          u = (u + 0x1000u) & 0xFFFFE000u;
-          float h;
-          memcpy(&h, &u, 4);
-          float l = (float)(v - (double)h);
-          memcpy(&u, &l, 4);
-          u = (u + 0x1000u) & 0xFFFFE000u;
-          memcpy(&l, &u, 4);
-          const int off = r * 128 + ((((k * 4) >> 4) ^ (r & 7)) << 4) + ((k * 4) & 15);
-          bh[off / 4] = h;
-          bl[off / 4] = l;
+          split_store(g, v, bh, bl, (int)swz_b(r, k * es));
         }
     }
 }
@@ -235,9 +306,11 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   const int f = fsel == 0 ? 1 : 0;            // state field: psi slot 1, T slot 0
   const int kc = tc_zinv_kchunks(g);
   const int nchunks = (t1 - t0) * kc;         // the chunks this CTA streams, tile after tile
-  const float* Ahi = (fsel == 0 ? Ahi_psi : Ahi_T) + (size_t)t0 * kc * kTileM * kChunkK;
-  const float* Alo = (fsel == 0 ? Alo_psi : Alo_T) + (size_t)t0 * kc * kTileM * kChunkK;
-  constexpr uint32_t kChunkBytes = kTileM * kChunkK * 4;   // one image chunk, 16 KB
+  const float* Ahi = (fsel == 0 ? Ahi_psi : Ahi_T) + (size_t)t0 * kc * kChunkFloats;
+  const float* Alo = (fsel == 0 ? Alo_psi : Alo_T) + (size_t)t0 * kc * kChunkFloats;
+  constexpr uint32_t kChunkBytes = kChunkFloats * 4;   // one image chunk, 16 KB
+  const bool bf = g.tcbf16 != 0;
+  const int ke = tc_ke(g), es = 128 / ke;
   unsigned char* sXhi = base;
   unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
   unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [stage][hi, lo][128 x 128 B]
@@ -255,8 +328,8 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
     for (int c = 0; c < NB && c < nchunks; ++c) {
       unsigned char* ah = sA + (size_t)c * 2 * kTileM * 128;
       arrive_expect_tx(&full[c], 2 * kChunkBytes);
-      bulk_g2s(ah, Ahi + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
-      bulk_g2s(ah + kTileM * 128, Alo + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
+      bulk_g2s(ah, Ahi + (size_t)c * kChunkFloats, kChunkBytes, &full[c]);
+      bulk_g2s(ah + kTileM * 128, Alo + (size_t)c * kChunkFloats, kChunkBytes, &full[c]);
       copies[c]++;
     }
   }
@@ -269,7 +342,7 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   // (four consecutive columns, two modes, per item: 16-byte loads, several in flight)
   const double* Xb = X + (size_t)b * S;
 #pragma unroll 4
-  for (int it = tid; it < kc * kChunkK * (kTileN / 4); it += blockDim.x) {
+  for (int it = tid; it < kc * ke * (kTileN / 4); it += blockDim.x) {
     const int n = it / (kTileN / 4), col = (it - n * (kTileN / 4)) * 4;
     const int gc = c0 + col;                  // even: columns gc .. gc+3 are modes gc/2, gc/2 + 1
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -286,12 +359,8 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float x = (float)v[e];
-      const uint32_t h = to_tf32(x);
-      const uint32_t l = to_tf32(x - __uint_as_float(h));
-      const uint32_t o = (uint32_t)(n / kChunkK) * kTileN * 128 + swz(col + e, n % kChunkK);
-      *reinterpret_cast<uint32_t*>(sXhi + o) = h;
-      *reinterpret_cast<uint32_t*>(sXlo + o) = l;
+      const uint32_t o = (uint32_t)(n / ke) * kTileN * 128 + swz_b(col + e, (n % ke) * es);
+      store_split(bf, (float)v[e], sXhi, sXlo, o);
     }
   }
   asm volatile("fence.proxy.async.shared::cta;");
@@ -299,7 +368,7 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
+  const uint32_t idesc = bf ? instr_desc_bf16(kTileM, kTileN) : instr_desc_tf32(kTileM, kTileN);
   const long long limit = g_wait_limit;
   bool issued_all = true;
   bool ok = true;
@@ -318,12 +387,10 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
         unsigned char* al = ah + (size_t)kTileM * 128;
         const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
         const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
-        for (int ks = 0; ks < kChunkK / 8; ++ks) {
+        for (int ks = 0; ks < 4; ++ks) {       // four 32-byte K-steps per 128-byte row
           const uint32_t o = ks * 32;
           const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
-          mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
-          mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
+          mma3(bf, tmem, saddr(ah) + o, saddr(al) + o, xh + o, xl + o, idesc, acc0);
         }
         commit(&empty[buf]);
         commits[buf]++;
@@ -334,8 +401,8 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
           }
           seen_empty[buf]++;
           arrive_expect_tx(&full[buf], 2 * kChunkBytes);
-          bulk_g2s(ah, Ahi + (size_t)(gi + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
-          bulk_g2s(al, Alo + (size_t)(gi + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
+          bulk_g2s(ah, Ahi + (size_t)(gi + NB) * kChunkFloats, kChunkBytes, &full[buf]);
+          bulk_g2s(al, Alo + (size_t)(gi + NB) * kChunkFloats, kChunkBytes, &full[buf]);
           copies[buf]++;
         }
       }
@@ -451,32 +518,20 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
 // The waits, the drain and the tensor-memory release follow k_zinv_tc.
 // ---------------------------------------------------------------------------
 __host__ __device__ int tc_zfwd_mtiles(const Grid& g) { return (g.Nz / 2 + kTileM - 1) / kTileM; }
-__host__ __device__ int tc_zfwd_kchunks(const Grid& g) { return ((g.Mz + 1) / 2 + kChunkK - 1) / kChunkK; }
-size_t tc_zfwd_image_floats(const Grid& g) { return (size_t)tc_zfwd_mtiles(g) * tc_zfwd_kchunks(g) * kTileM * kChunkK; }
+__host__ __device__ int tc_zfwd_kchunks(const Grid& g) { return ((g.Mz + 1) / 2 + tc_ke(g) - 1) / tc_ke(g); }
+size_t tc_zfwd_image_floats(const Grid& g) { return (size_t)tc_zfwd_mtiles(g) * tc_zfwd_kchunks(g) * kChunkFloats; }
 
 void tc_zfwd_build_images(const Grid& g, const double* zfwd, int p, float* hi, float* lo) {
-  const int mt = tc_zfwd_mtiles(g), kc = tc_zfwd_kchunks(g), Mh = (g.Mz + 1) / 2;
+  const int mt = tc_zfwd_mtiles(g), kc = tc_zfwd_kchunks(g), Mh = (g.Mz + 1) / 2, ke = tc_ke(g), es = 128 / ke;
   for (int t = 0; t < mt; ++t)
     for (int c = 0; c < kc; ++c) {
-      float* bh = hi + ((size_t)t * kc + c) * kTileM * kChunkK;
-      float* bl = lo + ((size_t)t * kc + c) * kTileM * kChunkK;
+      float* bh = hi + ((size_t)t * kc + c) * kChunkFloats;
+      float* bl = lo + ((size_t)t * kc + c) * kChunkFloats;
       for (int r = 0; r < kTileM; ++r)
-        for (int k = 0; k < kChunkK; ++k) {
-          const int n = 2 * (t * kTileM + r) + p, jh = c * kChunkK + k;
+        for (int k = 0; k < ke; ++k) {
+          const int n = 2 * (t * kTileM + r) + p, jh = c * ke + k;
           const double v = (n < g.Nz && jh < Mh) ? zfwd[(size_t)n * g.Mz + jh] : 0.0;
-          float f = (float)v;
-          uint32_t u;
-          memcpy(&u, &f, 4);
-          u = (u + 0x1000u) & 0xFFFFE000u;
-          float h;
-          memcpy(&h, &u, 4);
-          float l = (float)(v - (double)h);
-          memcpy(&u, &l, 4);
-          u = (u + 0x1000u) & 0xFFFFE000u;
-          memcpy(&l, &u, 4);
-          const int off = r * 128 + ((((k * 4) >> 4) ^ (r & 7)) << 4) + ((k * 4) & 15);
-          bh[off / 4] = h;
-          bl[off / 4] = l;
+          split_store(g, v, bh, bl, (int)swz_b(r, k * es));
         }
     }
 }
@@ -523,9 +578,11 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
   if (b >= B || !(nsteps == nullptr || *step < nsteps[b])) return;   // uniform per block
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int kc = tc_zfwd_kchunks(g), Mh = (g.Mz + 1) / 2;
-  const float* Ahi = (p == 0 ? Whi0 : Whi1) + (size_t)t * kc * kTileM * kChunkK;
-  const float* Alo = (p == 0 ? Wlo0 : Wlo1) + (size_t)t * kc * kTileM * kChunkK;
-  constexpr uint32_t kChunkBytes = kTileM * kChunkK * 4;
+  const float* Ahi = (p == 0 ? Whi0 : Whi1) + (size_t)t * kc * kChunkFloats;
+  const float* Alo = (p == 0 ? Wlo0 : Wlo1) + (size_t)t * kc * kChunkFloats;
+  constexpr uint32_t kChunkBytes = kChunkFloats * 4;
+  const bool bf = g.tcbf16 != 0;
+  const int ke = tc_ke(g), es = 128 / ke;
   unsigned char* sXhi = base;
   unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
   unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [stage][hi, lo][128 x 128 B]
@@ -542,8 +599,8 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
     for (int c = 0; c < NB && c < kc; ++c) {
       unsigned char* ah = sA + (size_t)c * 2 * kTileM * 128;
       arrive_expect_tx(&full[c], 2 * kChunkBytes);
-      bulk_g2s(ah, Ahi + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
-      bulk_g2s(ah + kTileM * 128, Alo + (size_t)c * kTileM * kChunkK, kChunkBytes, &full[c]);
+      bulk_g2s(ah, Ahi + (size_t)c * kChunkFloats, kChunkBytes, &full[c]);
+      bulk_g2s(ah + kTileM * 128, Alo + (size_t)c * kChunkFloats, kChunkBytes, &full[c]);
       copies[c]++;
     }
   }
@@ -557,7 +614,7 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
   const float* q = Q + (size_t)(b * 2 + f) * g.Mz * g.nm * 2;
   const bool vec = (2 * g.nm) % 4 == 0;
 #pragma unroll 4
-  for (int it = tid; it < kc * kChunkK * (kTileN / 4); it += blockDim.x) {
+  for (int it = tid; it < kc * ke * (kTileN / 4); it += blockDim.x) {
     const int jh = it / (kTileN / 4), col = (it - jh * (kTileN / 4)) * 4;
     const int jr = g.Mz - 1 - jh;
     float a[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
@@ -583,11 +640,8 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
     for (int e = 0; e < 4; ++e) {
       float x = 0.f;
       if (jh < Mh && c0 + col + e < 2 * g.nm) x = (jr != jh) ? (p == 0 ? a[e] + c[e] : a[e] - c[e]) : (p == 0 ? a[e] : 0.f);
-      const uint32_t h = to_tf32(x);
-      const uint32_t l = to_tf32(x - __uint_as_float(h));
-      const uint32_t o = (uint32_t)(jh / kChunkK) * kTileN * 128 + swz(col + e, jh % kChunkK);
-      *reinterpret_cast<uint32_t*>(sXhi + o) = h;
-      *reinterpret_cast<uint32_t*>(sXlo + o) = l;
+      const uint32_t o = (uint32_t)(jh / ke) * kTileN * 128 + swz_b(col + e, (jh % ke) * es);
+      store_split(bf, x, sXhi, sXlo, o);
     }
   }
   asm volatile("fence.proxy.async.shared::cta;");
@@ -595,7 +649,7 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = instr_desc_tf32(kTileM, kTileN);
+  const uint32_t idesc = bf ? instr_desc_bf16(kTileM, kTileN) : instr_desc_tf32(kTileM, kTileN);
   const long long limit = g_wait_limit;
   bool issued_all = true;
   if (tid == 0) {
@@ -611,12 +665,10 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
       unsigned char* al = ah + (size_t)kTileM * 128;
       const uint32_t xh = saddr(sXhi) + (uint32_t)c * kTileN * 128;
       const uint32_t xl = saddr(sXlo) + (uint32_t)c * kTileN * 128;
-      for (int ks = 0; ks < kChunkK / 8; ++ks) {
+      for (int ks = 0; ks < 4; ++ks) {         // four 32-byte K-steps per 128-byte row
         const uint32_t o = ks * 32;
         const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-        mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xh + o), idesc, acc0);
-        mma_tf32(tmem, smem_desc(saddr(ah) + o), smem_desc(xl + o), idesc, 1u);
-        mma_tf32(tmem, smem_desc(saddr(al) + o), smem_desc(xh + o), idesc, 1u);
+        mma3(bf, tmem, saddr(ah) + o, saddr(al) + o, xh + o, xl + o, idesc, acc0);
       }
       commit(&empty[buf]);
       commits[buf]++;
@@ -627,8 +679,8 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
         }
         seen_empty[buf]++;
         arrive_expect_tx(&full[buf], 2 * kChunkBytes);
-        bulk_g2s(ah, Ahi + (size_t)(c + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
-        bulk_g2s(al, Alo + (size_t)(c + NB) * kTileM * kChunkK, kChunkBytes, &full[buf]);
+        bulk_g2s(ah, Ahi + (size_t)(c + NB) * kChunkFloats, kChunkBytes, &full[buf]);
+        bulk_g2s(al, Alo + (size_t)(c + NB) * kChunkFloats, kChunkBytes, &full[buf]);
         copies[buf]++;
       }
     }

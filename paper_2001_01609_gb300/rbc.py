@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librbc.so")
 
 RBC_OK, RBC_EINVAL, RBC_ENOMEM, RBC_ECUDA, RBC_EDIVERGED, RBC_ETIMEOUT, RBC_ENOTCONVERGED = 0, -1, -2, -3, -4, -5, 1
-RBC_FP64, RBC_MIXED = 0, 1
+RBC_FP64, RBC_MIXED, RBC_MIXED_BF16 = 0, 1, 2
 RBC_FIXED_T, RBC_FIXED_FLUX = 0, 1
 CRIT_FIXED, CRIT_DEFECT, CRIT_NU, CRIT_STAT = 0, 1, 2, 3
 

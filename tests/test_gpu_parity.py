@@ -133,7 +133,7 @@ def test_batched_uneven_steps_equal_solo_runs_and_oracle(rbc):
     assert torch.equal(st[1].cpu(), torch.from_numpy(to_abi(Xs[1])))   # 0 steps: untouched
 
 
-@pytest.mark.parametrize("precision,Nx,Nz,B", [(0, 32, 16, 160), (1, 32, 16, 160), (1, 64, 64, 40)])
+@pytest.mark.parametrize("precision,Nx,Nz,B", [(0, 32, 16, 160), (1, 32, 16, 160), (1, 64, 64, 40), (2, 64, 64, 40)])
 def test_small_and_large_batch_kernel_shapes_give_identical_bits(rbc, precision, Nx, Nz, B):
     """A batch of 160 states takes the large-batch launch shapes (one row kernel
     block per row, 16-mode solve tiles, 32-mode z-forward tiles); one state
@@ -366,10 +366,13 @@ def test_parareal_schedule_does_not_change_results(rbc, precision):
             P.set_schedule(*bad)
 
 
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("Nx,Nz,Ra", [(64, 32, 1e5), (32, 18, 2e5), (64, 64, 3e5), (256, 64, 1e6)])
-def test_mixed_precision_few_steps_within_stated_tolerance(rbc, Nx, Nz, Ra):
+def test_mixed_precision_few_steps_within_stated_tolerance(rbc, Nx, Nz, Ra, precision):
     """RBC_MIXED: FP32 transforms and products, FP64 solves and RK combination
     (the z transforms on tensor cores from Nz = 64, on CUDA cores below).
+    RBC_MIXED_BF16: the same with BF16 instead of TF32 hi/lo operands in the
+    tensor-core transforms (about 16 bits of each operand).
 
     Stated tolerance: 1e-5 relative to the largest coefficient after 4 steps
     (FP32 rounding of the explicit terms, ~1e-7, enters the state through
@@ -378,7 +381,7 @@ def test_mixed_precision_few_steps_within_stated_tolerance(rbc, Nx, Nz, Ra):
     dt = 1e-4 if Ra < 1e6 else 1e-5
     o = RBC(Ra, 1.0, 2.0, Nx, Nz, dt)
     X0 = developed_state(o, seed=Nx + 7)
-    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt, precision=rbc.RBC_MIXED)
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt, precision=precision)
     st = F.new_states(1)
     put(st, 0, X0)
     nu = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -386,7 +389,7 @@ def test_mixed_precision_few_steps_within_stated_tolerance(rbc, Nx, Nz, Ra):
     assert F.check_diverged() == rbc.RBC_OK
     ref, integ = o.run(X0, 4)
     err = max_rel_diff(get(st, 0), ref)
-    print(f"mixed {Nx}x{Nz} Ra={Ra:g}: state rel err {err:.3e}, Nu integral rel err "
+    print(f"precision {precision} {Nx}x{Nz} Ra={Ra:g}: state rel err {err:.3e}, Nu integral rel err "
           f"{abs(nu.item() - integ) / abs(integ):.3e}")
     assert err < 1e-5
     assert abs(nu.item() - integ) < 1e-5 * abs(integ)
@@ -398,7 +401,7 @@ def test_mixed_precision_few_steps_within_stated_tolerance(rbc, Nx, Nz, Ra):
     assert max_rel_diff(get(st64, 0), ref) < 1e-11 < err
 
 
-@pytest.mark.parametrize("precision,Nx,Nz,B", [(0, 64, 32, 5), (1, 64, 64, 12), (0, 128, 32, 1)])
+@pytest.mark.parametrize("precision,Nx,Nz,B", [(0, 64, 32, 5), (1, 64, 64, 12), (2, 64, 64, 12), (0, 128, 32, 1)])
 def test_autotuned_shapes_give_identical_bits(rbc, precision, Nx, Nz, B):
     """rbc_autotune only picks launch shapes: a handle with the tuned shapes gives
     the bits of one with the heuristics."""
