@@ -10,7 +10,8 @@ It is a slow, obviously-correct restatement of the method in NumPy/SciPy:
   operators (the tau discretisation in z of the linear terms, Sec. 3.2).
 * ``rbc``            - the Boussinesq equations (Eqs. 3-6) in streamfunction form,
   Fourier(x) x Chebyshev(z) collocation with 3/2-rule dealiasing, IMEX RK443
-  time stepping (Sec. 3.2, Sec. 3.6), the Nusselt numbers (Eqs. 9-11).
+  time stepping (Sec. 3.2, Sec. 3.6; the lower-order RK222 and RK111 of the
+  same family for coarse propagators), the Nusselt numbers (Eqs. 9-11).
 * ``parareal``       - the Parareal iteration (Eq. 20) with the defect and
   Nusselt stopping norms (Sec. 3.7) and a statistical stopping rule.
 * ``statistics``     - sampled time means and the consistency checks of

@@ -26,7 +26,11 @@ truncated back (dealiasing; the paper is silent, this is the reading).  Linear
 terms (diffusion, pressure, buoyancy) are implicit (Sec. 3.2) with the
 ultraspherical tau method; nonlinear terms explicit.  Time stepping: the
 4-stage, 3rd-order IMEX Runge-Kutta RK443 of Ascher, Ruuth & Spiteri (Sec. 3.2,
-Sec. 3.6), written M X_t = L X + F(X).
+Sec. 3.6), written M X_t = L X + F(X).  The lower-order coarse steppers that
+Sec. 3.6 reports trying are read as the two smaller schemes of the same family:
+ARS(2,2,2) ("RK222", 2 stages, 2nd order) and ARS(1,1,1) ("RK111",
+forward-backward Euler, 1st order).  All three have an explicit first stage, a
+constant implicit diagonal gamma and are stiffly accurate (X_{n+1} = last stage).
 
 State: ``State(T, psi, U)`` with T, psi complex (Nx/2, Nz) (psi[0] unused, kept
 zero) and U real (Nz,) = mean horizontal velocity.
@@ -54,6 +58,33 @@ RK443_AE = [
     [5 / 6, -5 / 6, 1 / 2, 0, 0],
     [1 / 4, 7 / 4, 3 / 4, -7 / 4, 0],
 ]
+
+
+# ARS(2,2,2): gamma = 1 - 1/sqrt(2) (the root of gamma^2 - 2 gamma + 1/2 = 0 in
+# (0, 1): second order and L-stable), delta = 1 - 1/(2 gamma).
+_G2 = 1.0 - 1.0 / np.sqrt(2.0)
+_D2 = 1.0 - 1.0 / (2.0 * _G2)
+RK222_C = [0.0, _G2, 1.0]
+RK222_AI = [
+    [0, 0, 0],
+    [0, _G2, 0],
+    [0, 1 - _G2, _G2],
+]
+RK222_AE = [
+    [0, 0, 0],
+    [_G2, 0, 0],
+    [_D2, 1 - _D2, 0],
+]
+# ARS(1,1,1): explicit Euler for F, implicit Euler for L.
+RK111_C = [0.0, 1.0]
+RK111_AI = [[0, 0], [0, 1.0]]
+RK111_AE = [[0, 0], [1.0, 0]]
+
+SCHEMES = {
+    "RK443": (RK443_C, RK443_AI, RK443_AE),
+    "RK222": (RK222_C, RK222_AI, RK222_AE),
+    "RK111": (RK111_C, RK111_AI, RK111_AE),
+}
 
 
 class State:
@@ -87,16 +118,24 @@ def native_points(Nx, Nz, Lx):
 class RBC:
     """Fine (or coarse) propagator of Sec. 3.2 on one grid with one time step."""
 
-    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, bc="fixed_T"):
+    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, bc="fixed_T", scheme="RK443"):
         """bc: "fixed_T" (Eq. 6: T = 1, 0 at z = -1/2, 1/2) or "fixed_flux"
         (Eq. 7: dT/dz = -1 at both walls, with Ra read as the flux Rayleigh
-        number Ra_f of Eq. 8); no-slip walls in both."""
+        number Ra_f of Eq. 8); no-slip walls in both.  scheme: the IMEX
+        Runge-Kutta pair, "RK443" (the paper's) or the lower-order "RK222",
+        "RK111" (Sec. 3.6)."""
         if Nx % 2 or Nx < 4 or Nz < 8 or Nz % 2 or dt <= 0:
             raise ValueError("need even Nx >= 4, even Nz >= 8, dt > 0")
         if bc not in ("fixed_T", "fixed_flux"):
             raise ValueError("bc must be fixed_T or fixed_flux")
+        if scheme not in SCHEMES:
+            raise ValueError("scheme must be one of " + ", ".join(SCHEMES))
         self.Ra, self.Pr, self.Lx, self.Nx, self.Nz, self.dt = Ra, Pr, Lx, Nx, Nz, dt
         self.bc = bc
+        self.scheme = scheme
+        self.c_rk, self.AI, self.AE = SCHEMES[scheme]
+        self.stages = len(self.AI) - 1
+        self.gamma = self.AI[1][1]             # the constant implicit diagonal
         self.nm = Nx // 2
         self.Mx = 3 * Nx // 2
         self.Mz = 3 * Nz // 2
@@ -146,10 +185,10 @@ class RBC:
     def _factor(self):
         """LU factors of the stage matrices (M - dt a_ii L) with boundary rows.
 
-        Every diagonal coefficient of RK443's implicit tableau is 1/2, so one
-        matrix per Fourier mode serves all four stages.
+        Every diagonal coefficient of the implicit tableau is gamma (1/2 for
+        RK443), so one matrix per Fourier mode serves all stages.
         """
-        h = 0.5 * self.dt
+        h = self.gamma * self.dt
         Nz = self.Nz
         M, L = self.ops_T(0.0)
         A = np.vstack([M - h * L, self.T_bc_lo, self.T_bc_hi])
@@ -242,7 +281,7 @@ class RBC:
         return State(T, P, U), wT
 
     def solve_stage(self, r):
-        """Solve (M - dt/2 L) X = r in tau rows, boundary rows of Eq. 6 (or Eq. 7)."""
+        """Solve (M - gamma dt L) X = r in tau rows, boundary rows of Eq. 6 (or Eq. 7)."""
         Nz = self.Nz
         T = np.zeros((self.nm, Nz), dtype=complex)
         psi = np.zeros((self.nm, Nz), dtype=complex)
@@ -259,16 +298,18 @@ class RBC:
         return State(T, psi, U)
 
     def step(self, X):
-        """One RK443 step X_n -> X_{n+1}; also returns Nu_V(t_n) (Eq. 9).
+        """One step X_n -> X_{n+1} of the IMEX scheme (RK443 unless chosen
+        otherwise); also returns Nu_V(t_n) (Eq. 9).
 
         Stage i: (M - dt a_ii L) X_i = M X_0 + dt sum_{j<i} (aE_ij F(X_j) + aI_ij L X_j);
-        the scheme is stiffly accurate, X_{n+1} = X_4.
+        the schemes are stiffly accurate, X_{n+1} = X_s (s = 4, 2 or 1 stages).
         """
         dt = self.dt
+        AE, AI, ns = self.AE, self.AI, self.stages
         MX0 = self.apply_M(X)
         Xs, Fs, LXs = [X], [], [None]
         nu0 = None
-        for i in range(1, 5):
+        for i in range(1, ns + 1):
             F, wT = self.explicit(Xs[i - 1])
             if i == 1:
                 nu0 = self.nusselt_from(Xs[0], wT)[0]
@@ -277,12 +318,12 @@ class RBC:
                 LXs.append(self.apply_L(Xs[i - 1]))
             r = MX0
             for j in range(i):
-                term = _scale(Fs[j], dt * RK443_AE[i][j])
+                term = _scale(Fs[j], dt * AE[i][j])
                 if j >= 1:
-                    term = term + _scale(LXs[j], dt * RK443_AI[i][j])
+                    term = term + _scale(LXs[j], dt * AI[i][j])
                 r = r + term
             Xs.append(self.solve_stage(r))
-        return Xs[4], nu0
+        return Xs[ns], nu0
 
     def run(self, X, nsteps):
         """nsteps steps; returns the end state and the trapezoid integral of Nu_V dt."""

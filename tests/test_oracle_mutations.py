@@ -241,3 +241,32 @@ def test_prolongation_with_shifted_chebyshev_modes_fails_the_point_evaluation_pi
     monkeypatch.setattr(orbc, "prolong", prolong)
     with pytest.raises(AssertionError):
         transfer.test_prolongation_represents_the_same_fields((8, 8), (16, 12))
+
+
+def test_swapped_explicit_weights_of_rk222_fail_its_order_pin(monkeypatch):
+    import test_oracle_schemes as schemes
+    c, AI, AE = orbc.SCHEMES["RK222"]
+    bad = [row[:] for row in AE]
+    bad[2][0], bad[2][1] = bad[2][1], bad[2][0]      # delta and 1 - delta exchanged
+    monkeypatch.setitem(orbc.SCHEMES, "RK222", (c, AI, bad))
+    ref = schemes._convect(0.024 / 1536, "RK443")
+    with pytest.raises(AssertionError):
+        schemes.test_S4_observed_order_of_convergence("RK222", ref)
+
+
+@pytest.mark.parametrize("name", ["RK222", "RK111"])
+def test_wrong_implicit_diagonal_fails_the_closed_form_decay_pin(monkeypatch, name):
+    import test_oracle_schemes as schemes
+    c, AI, AE = orbc.SCHEMES[name]
+    bad = [row[:] for row in AI]
+    for i in range(1, len(bad)):
+        bad[i][i] = 0.9 * bad[i][i]
+    monkeypatch.setitem(orbc.SCHEMES, name, (c, bad, AE))
+    with pytest.raises(AssertionError):
+        schemes.test_S3_temperature_mode_decays_by_the_closed_form(name)
+
+
+def test_unmutated_lower_order_schemes_pass_the_same_pins():
+    import test_oracle_schemes as schemes
+    for name in ("RK222", "RK111"):
+        schemes.test_S3_temperature_mode_decays_by_the_closed_form(name)
