@@ -181,7 +181,7 @@ def fine_group_starts(N, group, first, n0=0):
     return a
 
 
-def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, reserve_sms=32):
+def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, reserve_sms=32, arms=None):
     """Parareal to a stated tolerance against the serial all-FP64 fine propagator
     on the same GPU (Sec. 3.7: iterate until Nu_k is within tol of Nu_{k-1}).
 
@@ -190,7 +190,8 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
     Parareal arms: mixed precision (fine and coarse propagators: FP32
     transforms and products, FP64 solves, correction and norms; TF32 hi/lo
     operands in the fine grid's tensor-core z transforms), the same with BF16
-    hi/lo operands in the fine transforms, and all FP64;
+    hi/lo operands in the fine transforms, and all FP64 (or the given `arms`:
+    (name, fine precision, coarse precision, coarse scheme, coarse dt));
     RBC_CRIT_NU with tol, iterations enqueued `depth` ahead, fine groups kept off
     `reserve_sms` SMs (the sweeps on the coarse grid use all of them).  "Equal
     Nu accuracy": each arm's Nu (time mean over the second half of the slices)
@@ -230,11 +231,14 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
                                 run=f"B = 1, {N} slices x {nf} steps in turn, same kernels"),
                arms={})
     pname = {rbc.RBC_MIXED: "mixed", rbc.RBC_MIXED_BF16: "mixed_bf16", rbc.RBC_FP64: "fp64"}
-    for name, pf, pg in (("mixed", rbc.RBC_MIXED, rbc.RBC_MIXED),
-                         ("mixed_bf16", rbc.RBC_MIXED_BF16, rbc.RBC_MIXED),
-                         ("fp64", rbc.RBC_FP64, rbc.RBC_FP64)):
+    sname = {rbc.RBC_RK443: "RK443", rbc.RBC_RK222: "RK222", rbc.RBC_RK111: "RK111"}
+    if arms is None:
+        arms = (("mixed", rbc.RBC_MIXED, rbc.RBC_MIXED, rbc.RBC_RK443, dv["dtc"]),
+                ("mixed_bf16", rbc.RBC_MIXED_BF16, rbc.RBC_MIXED, rbc.RBC_RK443, dv["dtc"]),
+                ("fp64", rbc.RBC_FP64, rbc.RBC_FP64, rbc.RBC_RK443, dv["dtc"]))
+    for name, pf, pg, scheme, dtc in arms:
         F = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"], precision=pf)
-        G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dv["dtc"], precision=pg)
+        G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dtc, precision=pg, scheme=scheme)
         P = rbc.Parareal(F, G, 0.0, dv["t_end"], N, rbc.CRIT_NU, tol)
         P.set_depth(depth)
         group = -(-N // 4)
@@ -249,7 +253,7 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
         el, (st, k, de, nus) = timed(lambda: P.iterate(U0[0], U, max_iters, stream=stream))
         nu = float(nus[-1]) if len(nus) else float("nan")
         out["arms"][name] = dict(
-            fine_precision=pname[pf], coarse_precision=pname[pg],
+            fine_precision=pname[pf], coarse_precision=pname[pg], coarse_scheme=sname[scheme], coarse_dt=dtc,
             status={rbc.RBC_OK: "tolerance met", rbc.RBC_ENOTCONVERGED: "not converged",
                     rbc.RBC_EDIVERGED: "diverged"}.get(st, str(st)),
             iterations=int(k), s=el, speedup_vs_serial_fp64=serial_s / el, defects=[float(x) for x in de],
@@ -920,6 +924,72 @@ def run_config3_study():
           flush=True)
 
 
+COARSE_NC = (625, 1000, 1250, 1600, 2000, 2500, 3125, 4000, 5000, 6250, 8000, 10000, 12500)
+
+
+def run_coarse_scheme_study():
+    """Lower-order coarse steppers (Sec. 3.6) on the Parareal workload (Ra 1e6,
+    fine 256 x 64 RK443 with dt 1.25e-5, coarse 128 x 32, 32 slices of 3125
+    fine steps).  Per scheme (RK443, RK222, RK111): the largest stable coarse
+    step, found by serial coarse runs over the whole horizon from the restricted
+    initial state (mixed precision, dt = slice length / nc for nc in COARSE_NC,
+    largest step first; stable = every slice ends finite with |Nu_V| < 100), the
+    coarse step's device time at that step, and Parareal with that coarse
+    propagator to the 1% Nu criterion against the serial FP64 fine run."""
+    import torch
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc
+    from paper_2001_01609_gb300.inputs import initial_temperature
+    w = WORKLOADS[DEFAULT]
+    dv = derived(w)
+    N = w["slices"]
+    stream = torch.cuda.current_stream()
+    F = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"], precision=rbc.RBC_MIXED)
+    U0 = F.new_states(1)
+    F.set_state(U0[0], initial_temperature(w["Nx"], w["Nz"], seed=w["seed"], Lx=w["Lx"]))
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    schemes = (("RK443", rbc.RBC_RK443), ("RK222", rbc.RBC_RK222), ("RK111", rbc.RBC_RK111))
+    scan, arms = {}, []
+    for name, sc in schemes:
+        tried = []
+        for nc in COARSE_NC:
+            dtc = dv["slice_len"] / nc
+            G = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nxc"], w["Nzc"], dtc, precision=rbc.RBC_MIXED,
+                               scheme=sc)
+            x = G.new_states(1)
+            rbc.restrict(F, G, U0, x)
+            w0 = x.clone()
+            G.step_batch(w0, 10)                               # graphs, untimed
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ok, done = True, 0
+            e0.record(stream)
+            for n in range(N):
+                G.step_batch(x, nc)
+                done += 1
+                nu = G.nusselt(x[0])[0]
+                if G.check_diverged() != rbc.RBC_OK or not math.isfinite(nu) or abs(nu) >= 100.0:
+                    ok = False
+                    break
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / (done * nc)
+            tried.append(dict(nc=nc, dt=dtc, stable=ok, slices_run=done, ms_per_step=ms))
+            print(json.dumps(dict(scheme=name, **tried[-1])), file=sys.stderr, flush=True)
+            G.close()
+            if ok:
+                arms.append((f"coarse_{name}", rbc.RBC_MIXED, rbc.RBC_MIXED, sc, dtc))
+                break
+        scan[name] = tried
+    res = time_to_tolerance(rbc, w, dv, U0, stream, arms=arms)
+    ck = clocks.stop()
+    print(json.dumps(dict(study="coarse_schemes", Ra=w["Ra"], grid=f"{w['Nx']}x{w['Nz']}",
+                          coarse_grid=f"{w['Nxc']}x{w['Nzc']}", slices=N, dt=w["dt"],
+                          fine_steps_per_slice=w["steps_per_slice"], stability_scan=scan, clocks=ck, **res)),
+          flush=True)
+
+
 def run_ncu_case(name):
     """A small, self-ending case for ncu: one plain (graph-free) RK443 step of a
     batch, or one short Parareal iteration on the bench's grids."""
@@ -976,7 +1046,7 @@ def main():
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the Parareal-to-tolerance runs")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg of the default line")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
-    ap.add_argument("--study", choices=["coarsening", "statistics", "config3"],
+    ap.add_argument("--study", choices=["coarsening", "statistics", "config3", "coarse_schemes"],
                     help="the coarsening and slice-count study, or the statistical Parareal run (not bench lines)")
     ap.add_argument("--study-coarse", default="",
                     help="coarse propagators of the coarsening study, e.g. 32x8:3.125e-5,64x16:1.5625e-5")
@@ -996,6 +1066,9 @@ def main():
         return
     if args.study == "config3":
         run_config3_study()
+        return
+    if args.study == "coarse_schemes":
+        run_coarse_scheme_study()
         return
     if args.workload in SERVING:
         if args.impl == "reference":

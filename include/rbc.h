@@ -64,6 +64,7 @@ typedef enum {
 enum { RBC_FP64 = 0, RBC_MIXED = 1, RBC_MIXED_BF16 = 2 };   /* rbc_opts.precision */
 enum { RBC_FIXED_T = 0, RBC_FIXED_FLUX = 1 }; /* rbc_opts.bc (Eqs. 6, 7) */
 enum { RBC_CRIT_FIXED = 0, RBC_CRIT_DEFECT = 1, RBC_CRIT_NU = 2, RBC_CRIT_STAT = 3 };
+enum { RBC_RK443 = 0, RBC_RK222 = 1, RBC_RK111 = 2 };   /* rbc_opts.scheme (Sec. 3.6) */
 
 typedef struct {
   int precision;   /* RBC_FP64: every step in FP64.  RBC_MIXED: transforms and
@@ -72,8 +73,9 @@ typedef struct {
                       the tensor cores with TF32 operands split in hi and lo
                       parts (three products: about FP32 accuracy).
                       RBC_MIXED_BF16: the same with BF16 hi/lo operands (three
-                      products: about 16 bits of the operands, a relative
-                      error near 1e-5 in the transforms).                      */
+                      products of about 16-bit operands; the transforms' error
+                      enters the state through dt times the explicit terms and
+                      stays within the FP32 products' 1e-5 bound).           */
   int bc;          /* RBC_FIXED_T: T = 1, 0 at the bottom and top walls (Eq. 6).
                       RBC_FIXED_FLUX: dT/dz = -1 at both walls (Eq. 7); Ra is
                       then the flux Rayleigh number Ra_f of Eq. 8.  No-slip
@@ -84,6 +86,15 @@ typedef struct {
                       device-side loop); 1: every kernel is launched from the
                       host, so per-kernel profilers see each launch (slower).
                       Same results either way.                               */
+  int scheme;      /* IMEX Runge-Kutta pair of Ascher, Ruuth & Spiteri (1997):
+                      RBC_RK443 (4 stages, 3rd order; the paper's, Sec. 3.2),
+                      or the lower-order coarse steppers Sec. 3.6 reports
+                      trying: RBC_RK222 = ARS(2,2,2) (2 stages, 2nd order,
+                      implicit diagonal 1 - 1/sqrt(2)) and RBC_RK111 =
+                      ARS(1,1,1) (forward-backward Euler).  All three have an
+                      explicit first stage and are stiffly accurate; a step
+                      launches 4 kernels per stage.  Zero-initialise the
+                      struct: 0 is RK443.                                    */
 } rbc_opts;
 
 /* Text of the last error seen by this thread (static storage, never NULL). */

@@ -538,7 +538,7 @@ static rbc_status upload_tables(rbc_t h) {
     }
 
   // ---- stage matrices and their UL factors ----
-  const double hdt = 0.5 * g.dt;
+  const double hdt = g.gamma * g.dt;       // stage matrices M - gamma dt L
   auto layout = [&](std::vector<double>& dst, const std::vector<double>& src, int p, int rows, int D, int nmod,
                     int mi) {
     for (int c = 0; c < rows; ++c)
@@ -751,12 +751,14 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
     return fail(RBC_EINVAL, "need even Nx in [4, 1024] and even Nz in [8, 512]");
   if (!(dt > 0) || !(Pr > 0) || !(Lx > 0) || !(Ra >= 0) || !std::isfinite(Ra) || !std::isfinite(dt))
     return fail(RBC_EINVAL, "need dt > 0, Pr > 0, Lx > 0, Ra >= 0");
-  rbc_opts o{RBC_FP64, RBC_FIXED_T, 0};
+  rbc_opts o{RBC_FP64, RBC_FIXED_T, 0, RBC_RK443};
   if (opts) o = *opts;
   if (o.eager != 0 && o.eager != 1) return fail(RBC_EINVAL, "eager must be 0 or 1");
   if (o.precision != RBC_FP64 && o.precision != RBC_MIXED && o.precision != RBC_MIXED_BF16)
     return fail(RBC_EINVAL, "precision mode %d not available", o.precision);
   if (o.bc != RBC_FIXED_T && o.bc != RBC_FIXED_FLUX) return fail(RBC_EINVAL, "boundary condition %d not available", o.bc);
+  if (o.scheme != RBC_RK443 && o.scheme != RBC_RK222 && o.scheme != RBC_RK111)
+    return fail(RBC_EINVAL, "time-stepping scheme %d not available", o.scheme);
   // padded x length 3 Nx / 2 must be 3 * 2^p for the FFT
   int Mx = 3 * Nx / 2, r = Mx / 3;
   if (Mx % 3 || (r & (r - 1))) return fail(RBC_EINVAL, "Nx must be a power of two (3/2-padded FFT length 3*2^p)");
@@ -782,9 +784,16 @@ extern "C" rbc_status rbc_create(double Ra, double Pr, double Lx, int Nx, int Nz
   g.mixed = (o.precision == RBC_MIXED || o.precision == RBC_MIXED_BF16) ? 1 : 0;
   g.tcbf16 = (o.precision == RBC_MIXED_BF16) ? 1 : 0;
   g.bc = o.bc;
+  g.scheme = o.scheme;
+  {
+    double ae[5][5], ai[5][5];
+    scheme_tableau(o.scheme, ae, ai, &g.ns, &g.gamma);
+    g.inv_gamma = 1.0 / g.gamma;
+  }
   rbc_status s = upload_tables(h);
   if (s == RBC_OK) {
     cudaError_t e = configure_kernels(g);
+    if (e == cudaSuccess) e = upload_schemes();
     if (e != cudaSuccess) s = fail(RBC_ECUDA, "configure: %s", cudaGetErrorString(e));
   }
   if (s == RBC_OK) {
@@ -1015,7 +1024,7 @@ static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExe
   const unsigned long long before = launches_so_far();
   e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage)
+    for (int stage = 1; stage <= h->g.ns && e == cudaSuccess; ++stage)
       e = launch_stage(h->g, h->t, h->w, X, B, stage, nu, cap);
     if (e == cudaSuccess) e = launch_advance_loop(h->w, loop, cap);
     cudaGraph_t captured = nullptr;
@@ -1026,11 +1035,11 @@ static rbc_status step_graph(rbc_t h, double* X, int B, double* nu, cudaGraphExe
     cudaGraphDestroy(gr);
     return fail(RBC_ECUDA, "step loop capture: %s", cudaGetErrorString(e));
   }
-  if (launches_so_far() - before != (unsigned long long)kStepKernels) {
+  if (launches_so_far() - before != (unsigned long long)step_kernels(h->g)) {
     cudaGraphDestroy(gr);
     return fail(RBC_ECUDA, "step graph: unexpected kernel count");
   }
-  add_launches(~0ull - (unsigned long long)kStepKernels + 1ull);   // captured, not executed
+  add_launches(~0ull - (unsigned long long)step_kernels(h->g) + 1ull);   // captured, not executed
   e = cudaGraphInstantiate(&victim->exec, gr, 0);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) {
@@ -1126,7 +1135,7 @@ static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps
   Prof& pr = *h->profp;
   const int eager = !pr.on ? 0 : pr.once ? std::min(maxs, kProfileSampleSteps) : maxs;
   for (int st = 0; st < eager; ++st) {
-    for (int stage = 1; stage <= 4; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
+    for (int stage = 1; stage <= h->g.ns; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
     CK(launch_advance(w, stream));
   }
   if (pr.once) pr.on = false;
@@ -1136,10 +1145,10 @@ static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps
     rbc_status gs = step_graph(h, X, B, nu, &ex);
     if (gs != RBC_OK) return gs;
     CK(cudaGraphLaunch(ex, stream));
-    add_launches((unsigned long long)rest * kStepKernels);
+    add_launches((unsigned long long)rest * step_kernels(h->g));
   } else {
     for (int st = 0; st < rest; ++st) {
-      for (int stage = 1; stage <= 4; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
+      for (int stage = 1; stage <= h->g.ns; ++stage) CK(launch_stage(h->g, h->t, w, X, B, stage, nu, stream));
       CK(launch_advance(w, stream));
     }
   }
@@ -1283,7 +1292,7 @@ static rbc_status time_shapes(rbc_t h, double* X, int B, const Shapes& sh, int s
   cudaError_t e = cudaSuccess;
   for (int st = 0; st <= steps && e == cudaSuccess; ++st) {
     if (st == 1) e = cudaEventRecord(e0, s);
-    for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage) e = launch_stage(h->g, h->t, w, X, B, stage, w.nu, s);
+    for (int stage = 1; stage <= h->g.ns && e == cudaSuccess; ++stage) e = launch_stage(h->g, h->t, w, X, B, stage, w.nu, s);
     if (e == cudaSuccess) e = launch_advance(w, s);
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, s);

@@ -23,6 +23,10 @@ struct Grid {
   int mixed;      // 1: transforms and products in FP32 (RBC_MIXED, RBC_MIXED_BF16)
   int tcbf16;     // 1: the tensor-core z transforms with BF16 operands (RBC_MIXED_BF16), else TF32
   int bc;         // RBC_FIXED_T or RBC_FIXED_FLUX (temperature boundary rows)
+  int scheme;     // RBC_RK443, RBC_RK222 or RBC_RK111 (index of the tableaux)
+  int ns;         // implicit stages per step: 4, 2 or 1
+  double gamma;   // the constant implicit diagonal of the scheme (1/2 for RK443)
+  double inv_gamma;
 };
 
 // Right-hand side of the temperature boundary row of the mean profile (m = 0)
@@ -195,7 +199,12 @@ cudaError_t launch_nusselt_static(const Grid& g, const Tables& t, const double* 
                                   int* host_flags, cudaStream_t s);
 unsigned long long launches_so_far();
 void add_launches(unsigned long long n);   // kernels launched through a replayed graph
-constexpr int kStepKernels = 17;           // 4 stages x 4 kernels + step counter
+// kernels of one captured step: 4 per stage + the step counter
+inline int step_kernels(const Grid& g) { return 4 * g.ns + 1; }
+// tableaux of the IMEX pairs (host copy), stage count and implicit diagonal
+void scheme_tableau(int scheme, double AE[5][5], double AI[5][5], int* ns, double* gamma);
+// copies the three schemes' tableaux to the device's constant memory
+cudaError_t upload_schemes();
 constexpr int kProfileSampleSteps = 8;     // steps recorded kernel by kernel in a sampled call
 cudaError_t configure_kernels(const Grid& g);
 // tensor-core z inverse transform (rbc_tcgen05.cu)

@@ -25,19 +25,65 @@
 
 namespace rbc {
 
-// RK443 (Ascher, Ruuth & Spiteri 1997, the (4,4,3) pair; Sec. 3.6).
-__constant__ double c_AE[5][5] = {
-    {0, 0, 0, 0, 0},
-    {1.0 / 2, 0, 0, 0, 0},
-    {11.0 / 18, 1.0 / 18, 0, 0, 0},
-    {5.0 / 6, -5.0 / 6, 1.0 / 2, 0, 0},
-    {1.0 / 4, 7.0 / 4, 3.0 / 4, -7.0 / 4, 0}};
-__constant__ double c_AI[5][5] = {
-    {0, 0, 0, 0, 0},
-    {0, 1.0 / 2, 0, 0, 0},
-    {0, 1.0 / 6, 1.0 / 2, 0, 0},
-    {0, -1.0 / 2, 1.0 / 2, 1.0 / 2, 0},
-    {0, 3.0 / 2, -3.0 / 2, 1.0 / 2, 1.0 / 2}};
+// IMEX Runge-Kutta pairs of Ascher, Ruuth & Spiteri (1997), [scheme][i][j]:
+// coefficient of stage j in stage i, stage 0 explicit, zero-padded to 5 x 5.
+// RK443 is the paper's (Sec. 3.2, Sec. 3.6); ARS(2,2,2) and ARS(1,1,1) are the
+// lower-order coarse steppers of Sec. 3.6.  Filled by upload_schemes().
+__constant__ double c_AE[3][5][5];
+__constant__ double c_AI[3][5][5];
+
+void scheme_tableau(int scheme, double AE[5][5], double AI[5][5], int* ns, double* gamma) {
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) AE[i][j] = AI[i][j] = 0.0;
+  if (scheme == RBC_RK222) {
+    // gamma = 1 - 1/sqrt(2): second order and L-stable; delta = 1 - 1/(2 gamma)
+    const double gm = 1.0 - 1.0 / std::sqrt(2.0), dl = 1.0 - 1.0 / (2.0 * gm);
+    AI[1][1] = gm;
+    AI[2][1] = 1.0 - gm;
+    AI[2][2] = gm;
+    AE[1][0] = gm;
+    AE[2][0] = dl;
+    AE[2][1] = 1.0 - dl;
+    *ns = 2;
+    *gamma = gm;
+  } else if (scheme == RBC_RK111) {
+    // explicit Euler for the nonlinear terms, implicit Euler for the linear ones
+    AI[1][1] = 1.0;
+    AE[1][0] = 1.0;
+    *ns = 1;
+    *gamma = 1.0;
+  } else {
+    const double ae[5][5] = {{0, 0, 0, 0, 0},
+                             {1.0 / 2, 0, 0, 0, 0},
+                             {11.0 / 18, 1.0 / 18, 0, 0, 0},
+                             {5.0 / 6, -5.0 / 6, 1.0 / 2, 0, 0},
+                             {1.0 / 4, 7.0 / 4, 3.0 / 4, -7.0 / 4, 0}};
+    const double ai[5][5] = {{0, 0, 0, 0, 0},
+                             {0, 1.0 / 2, 0, 0, 0},
+                             {0, 1.0 / 6, 1.0 / 2, 0, 0},
+                             {0, -1.0 / 2, 1.0 / 2, 1.0 / 2, 0},
+                             {0, 3.0 / 2, -3.0 / 2, 1.0 / 2, 1.0 / 2}};
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) {
+        AE[i][j] = ae[i][j];
+        AI[i][j] = ai[i][j];
+      }
+    *ns = 4;
+    *gamma = 0.5;
+  }
+}
+
+cudaError_t upload_schemes() {
+  double ae[3][5][5], ai[3][5][5];
+  for (int sc = 0; sc < 3; ++sc) {
+    int ns;
+    double gm;
+    scheme_tableau(sc, ae[sc], ai[sc], &ns, &gm);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_AE, ae, sizeof(ae));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_AI, ai, sizeof(ai));
+  return e;
+}
 
 __device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
 __device__ __forceinline__ void st2(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
@@ -789,6 +835,7 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
     if (t + j < nq) fv = fma(SY::tapF(g, tb, p, t, j), sm.F[(t + j) * W + col], fv);
   if (KIND != KP) fv = -fv;
   const double dt = g.dt;
+  const int sc = g.scheme, ns = g.ns;
   const size_t ro = soff(g, f, 2 * t + p, m) + c;
   double r;
   if (stage == 1) {
@@ -796,28 +843,29 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
 #pragma unroll
     for (int j = 0; j <= SY::LAM; ++j)
       if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), sm.X[(t + j) * W + col], mx);
-    r = fma(dt * c_AE[1][0], fv, mx);
+    r = fma(dt * c_AE[sc][1][0], fv, mx);
 #pragma unroll
-    for (int l = 2; l <= 4; ++l) R[(size_t)(l - 1) * S + ro] = fma(dt * c_AE[l][0], fv, mx);
+    for (int l = 2; l <= 4; ++l)
+      if (l <= ns) R[(size_t)(l - 1) * S + ro] = fma(dt * c_AE[sc][l][0], fv, mx);
   } else {
     double Rl[3];
     const double Ri = *(R + (size_t)(stage - 1) * S + ro);
 #pragma unroll
-    for (int l = 0; l < 3; ++l) Rl[l] = (l + 2 > stage) ? *(R + (size_t)(l + 1) * S + ro) : 0.0;
-    r = fma(dt * c_AE[stage][stage - 1], fv, Ri);
+    for (int l = 0; l < 3; ++l) Rl[l] = (l + 2 > stage && l + 2 <= ns) ? *(R + (size_t)(l + 1) * S + ro) : 0.0;
+    r = fma(dt * c_AE[sc][stage][stage - 1], fv, Ri);
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      if (l + 2 > stage) R[(size_t)(l + 1) * S + ro] = fma(dt * c_AE[l + 2][stage - 1], fv, Rl[l]);
+      if (l + 2 > stage && l + 2 <= ns) R[(size_t)(l + 1) * S + ro] = fma(dt * c_AE[sc][l + 2][stage - 1], fv, Rl[l]);
   }
   sm.r[t * W + col] = r;
   double bv = r;
   if (KIND == KP) {
-    // + dt/2 (-i k Pr Ra) S4 T_i: real part + k.. Im(S4 T), imaginary part - k.. Re(S4 T)
+    // + gamma dt (-i k Pr Ra) S4 T_i: real part + k.. Im(S4 T), imaginary part - k.. Re(S4 T)
     double st = 0.0;
 #pragma unroll
     for (int j = 0; j <= 4; ++j)
       if (t + j < nq) st = fma(__ldg(tb.s4 + (p * nq + t) * 5 + j), sm.T[(t + j) * W + (col ^ 1)], st);
-    const double cpl = (c == 0 ? 1.0 : -1.0) * 0.5 * dt * g.Pr * sm.Ra * (g.kfac * m);
+    const double cpl = (c == 0 ? 1.0 : -1.0) * g.gamma * dt * g.Pr * sm.Ra * (g.kfac * m);
     bv = fma(cpl, st, bv);
   }
   sm.y[(t + SY::D) * W + col] = bv;
@@ -950,13 +998,13 @@ __device__ __forceinline__ void solve_lx(const Grid& g, const Tables& tb, int st
 #pragma unroll
   for (int j = 0; j <= SY::LAM; ++j)
     if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), xs[(t + j) * W + col], mx);
-  const double lx2 = 2.0 * (mx - sm.r[t * W + col]);
+  const double lx2 = g.inv_gamma * (mx - sm.r[t * W + col]);   // dt (L X_i + coupling)
   const size_t ro = soff(g, f, 2 * t + p, m) + c;
 #pragma unroll
   for (int l = 0; l < 3; ++l)
-    if (l + 2 > stage) {
+    if (l + 2 > stage && l + 2 <= g.ns) {
       double* Rl = R + (size_t)(l + 1) * S + ro;
-      *Rl = fma(c_AI[l + 2][stage], lx2, *(Rl));
+      *Rl = fma(c_AI[g.scheme][l + 2][stage], lx2, *(Rl));
     }
 }
 
@@ -985,12 +1033,14 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
   sm.r = sm.y + (size_t)nq * W;
   sm.T = sm.r + (size_t)nq * W;
   double* X0 = X + (size_t)b * S;
-  double* Xo = (stage == 4) ? X0 : Xs + (size_t)b * S;
+  double* Xo = (stage == g.ns) ? X0 : Xs + (size_t)b * S;   // stiffly accurate: last stage = new state
   const double* Fb = F + (size_t)b * S;
   double* Rb = R + (size_t)b * 4 * S;
-  if (stage == 1 && m0 == 0 && p == 0 && threadIdx.x == 0 && nu != nullptr) {
+  if (stage == 1 && m0 == 0 && p == 1 && threadIdx.x == 0 && nu != nullptr) {
     // Nu_V(t_n) (Eq. 9) of the step-start state: wall temperature difference of
     // the mean profile + Clenshaw-Curtis integral of <wT>_x; trapezoid weight.
+    // The odd coefficients read here belong to this block, which overwrites
+    // them only after the barriers below (a one-stage scheme writes X0 here).
     double cond = 0.0;
     for (int n = 1; n < g.Nz; n += 2) cond -= 2.0 * *(X0 + soff(g, 0, n, 0));
     double adv = 0.0;
@@ -1070,7 +1120,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
     __syncthreads();
     const double* xs = dense ? sm.X : sm.y;
     // phase 4
-    if (stage < 4) {
+    if (stage < g.ns) {
       for (int it = threadIdx.x; it < ntmax * W; it += blockDim.x) {
         const int t = it / W, col = it - t * W;
         if (col >= ncol) continue;

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "librbc.so")
 RBC_OK, RBC_EINVAL, RBC_ENOMEM, RBC_ECUDA, RBC_EDIVERGED, RBC_ETIMEOUT, RBC_ENOTCONVERGED = 0, -1, -2, -3, -4, -5, 1
 RBC_FP64, RBC_MIXED, RBC_MIXED_BF16 = 0, 1, 2
 RBC_FIXED_T, RBC_FIXED_FLUX = 0, 1
+RBC_RK443, RBC_RK222, RBC_RK111 = 0, 1, 2
 CRIT_FIXED, CRIT_DEFECT, CRIT_NU, CRIT_STAT = 0, 1, 2, 3
 
 EXPORTS = [
@@ -37,7 +38,8 @@ class RBCError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("bc", ctypes.c_int), ("eager", ctypes.c_int)]
+    _fields_ = [("precision", ctypes.c_int), ("bc", ctypes.c_int), ("eager", ctypes.c_int),
+                ("scheme", ctypes.c_int)]
 
 
 _lib = None
@@ -122,13 +124,15 @@ def _dptr(a):
 class Propagator:
     """F (or G) of Eq. 20 on one grid: rbc_create(Ra, Pr, Lx, Nx, Nz, dt)."""
 
-    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, precision=RBC_FP64, eager=False, bc=RBC_FIXED_T):
-        """bc: RBC_FIXED_T (Eq. 6) or RBC_FIXED_FLUX (Eq. 7, Ra = Ra_f of Eq. 8)."""
+    def __init__(self, Ra, Pr, Lx, Nx, Nz, dt, precision=RBC_FP64, eager=False, bc=RBC_FIXED_T,
+                 scheme=RBC_RK443):
+        """bc: RBC_FIXED_T (Eq. 6) or RBC_FIXED_FLUX (Eq. 7, Ra = Ra_f of Eq. 8);
+        scheme: RBC_RK443, or the lower-order RBC_RK222 / RBC_RK111 (Sec. 3.6)."""
         lib = load()
         self.Ra, self.Pr, self.Lx, self.Nx, self.Nz, self.dt = Ra, Pr, Lx, Nx, Nz, dt
-        self.precision, self.bc = precision, bc
+        self.precision, self.bc, self.scheme = precision, bc, scheme
         h = ctypes.c_void_p()
-        opts = _Opts(precision, bc, 1 if eager else 0)
+        opts = _Opts(precision, bc, 1 if eager else 0, scheme)
         _check(lib.rbc_create(Ra, Pr, Lx, Nx, Nz, dt, ctypes.byref(opts), ctypes.byref(h)))
         self.h = h
 
