@@ -189,9 +189,11 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
     [0, t_end] (the same kernels), with the Nu_V integral of each slice.
     Parareal arms: mixed precision (fine and coarse propagators: FP32
     transforms and products, FP64 solves, correction and norms; TF32 hi/lo
-    operands in the fine grid's tensor-core z transforms), the same with BF16
-    hi/lo operands in the fine transforms, and all FP64 (or the given `arms`:
-    (name, fine precision, coarse precision, coarse scheme, coarse dt));
+    operands in the fine grid's tensor-core z transforms; RK443 in both, the
+    paper's choice), "mixed_fast" (BF16 hi/lo operands in the fine transforms
+    and the coarse propagator on ARS(2,2,2), Sec. 3.6, at the same coarse
+    step), and all FP64 (or the given `arms`: (name, fine precision, coarse
+    precision, coarse scheme, coarse dt));
     RBC_CRIT_NU with tol, iterations enqueued `depth` ahead, fine groups kept off
     `reserve_sms` SMs (the sweeps on the coarse grid use all of them).  "Equal
     Nu accuracy": each arm's Nu (time mean over the second half of the slices)
@@ -234,7 +236,7 @@ def time_to_tolerance(rbc, w, dv, U0, stream, tol=0.01, max_iters=6, depth=1, re
     sname = {rbc.RBC_RK443: "RK443", rbc.RBC_RK222: "RK222", rbc.RBC_RK111: "RK111"}
     if arms is None:
         arms = (("mixed", rbc.RBC_MIXED, rbc.RBC_MIXED, rbc.RBC_RK443, dv["dtc"]),
-                ("mixed_bf16", rbc.RBC_MIXED_BF16, rbc.RBC_MIXED, rbc.RBC_RK443, dv["dtc"]),
+                ("mixed_fast", rbc.RBC_MIXED_BF16, rbc.RBC_MIXED, rbc.RBC_RK222, dv["dtc"]),
                 ("fp64", rbc.RBC_FP64, rbc.RBC_FP64, rbc.RBC_RK443, dv["dtc"]))
     for name, pf, pg, scheme, dtc in arms:
         F = rbc.Propagator(w["Ra"], w["Pr"], w["Lx"], w["Nx"], w["Nz"], w["dt"], precision=pf)

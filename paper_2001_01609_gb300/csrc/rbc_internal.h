@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
+#include <utility>
 #include <vector>
 
 #include "../../include/rbc.h"
@@ -142,6 +143,36 @@ struct Work {
 
 #ifdef __CUDACC__
 #define RBC_HD __host__ __device__
+
+// Programmatic dependent launch of the step kernels.  Each is launched with
+// programmatic stream serialisation, so its CTAs may be scheduled while the
+// previous kernel on the stream is still running, and each begins with
+// pdl_enter(): griddepcontrol.wait returns once the previous grid has
+// completed and its writes are visible (a hardware dependency, like the
+// stream order it replaces, not a spin), and only then may the next kernel be
+// scheduled, so at most two step kernels are resident at a time.  Launched
+// without the attribute (or first in a graph body) both instructions are
+// no-ops.  The arithmetic, and so every bit, is that of plain stream order.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 #else
 #define RBC_HD
 #endif

@@ -304,6 +304,7 @@ __device__ void zinv_item(const Grid& g, const T* __restrict__ Bz, const double*
 template <typename T>
 __global__ void __launch_bounds__(256) k_zinv(Grid g, const T* __restrict__ Bz, const double* __restrict__ X, size_t S,
                                               T* __restrict__ Z, int B, const int* nsteps, const int* step) {
+  pdl_enter();
   zinv_item<T>(g, Bz, X, S, Z, B, nsteps, nsteps ? *step : 0, blockIdx.x, blockDim.x / 32);
 }
 
@@ -573,6 +574,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_rows(Grid g, const C2<T>* __restrict__ tw, const T* __restrict__ Z,
                                               T* __restrict__ Q, double* __restrict__ wT, int B, int batched,
                                               const int* nsteps, const int* step) {
+  pdl_enter();
   rows_item<T>(g, tw, Z, Q, wT, B, batched, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
@@ -607,6 +609,7 @@ __global__ void __cluster_dims__(kRowsCluster, 1, 1) __launch_bounds__(kRowsThre
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ double red[kRowsThreads];
+  pdl_enter();
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
   const int row = blockIdx.x / kRowsCluster;
@@ -747,6 +750,7 @@ __device__ void zfwd_item(const Grid& g, const T* __restrict__ W, const T* __res
 template <typename T>
 __global__ void k_zfwd(Grid g, const T* __restrict__ W, const T* __restrict__ Q, double* __restrict__ F, size_t S,
                        int B, int tm, int nch, const int* nsteps, const int* step) {
+  pdl_enter();
   zfwd_item<T>(g, W, Q, F, S, B, tm, nch, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
@@ -1145,6 +1149,7 @@ __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, dou
                                                size_t S, const double* wT, double* nu, int* flags, int* err, int B,
                                                int stage, int tms, const double* ra, const int* nsteps,
                                                const int* step) {
+  pdl_enter();
   solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, err, B, stage, tms, ra, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
@@ -1197,13 +1202,17 @@ bool shapes_valid(const Grid& g, const Shapes& sh, size_t es) {
   return true;
 }
 
-__global__ void k_advance(int* step) { *step += 1; }
+__global__ void k_advance(int* step) {
+  pdl_enter();
+  *step += 1;
+}
 
 // Body end of the device-side step loop: the loop ends once every state of the
 // batch has taken its steps (maxs is written by the host before each launch).
 // cancel (may be null): a word another stream sets to stop the loop early
 // (work whose result is no longer wanted, e.g. a speculative Parareal iteration)
 __global__ void k_advance_loop(int* step, const int* maxs, const int* cancel, cudaGraphConditionalHandle loop) {
+  pdl_enter();
   const int s = *step + 1;
   *step = s;
   const bool stop = cancel != nullptr && *(const volatile int*)cancel != 0;
@@ -1318,16 +1327,17 @@ static void launch_transforms_in(const Grid& g, const Tables& t, const T* Bz, co
   if (sizeof(T) == 4 && t.tcA_psi_hi != nullptr)
     launch_zinv_tc(g, t, w, X, B, ns, s);              // tensor cores, TF32 with split compensation
   else
-    k_zinv<T><<<zb, 32 * kp, kp > 1 ? (size_t)kp * 12 * 32 * 2 * sizeof(T) : 0, s>>>(g, Bz, X, S, Z, B, ns, w.step);
+    launch_pdl(k_zinv<T>, zb, 32 * kp, kp > 1 ? (size_t)kp * 12 * 32 * 2 * sizeof(T) : 0, s, g, Bz, X, S, Z, B, ns,
+               w.step);
   if (pf) pf->end(RBC_KERNEL_ZINV, s, zinv_flops(g, B), zinv_bytes(g, B, sizeof(T)));
   const size_t es = sizeof(T);
   if (pf) pf->begin(RBC_KERNEL_ROWS, s);
   if (rows_cl_of(g, w, B, es))
-    k_rows_cl<T><<<(unsigned)(B * g.Mz * kRowsCluster), kRowsThreads, rows_cl_bytes(g, es), s>>>(g, tw, Z, Q, w.wT,
-                                                                                               B, ns, w.step);
+    launch_pdl(k_rows_cl<T>, (unsigned)(B * g.Mz * kRowsCluster), kRowsThreads, rows_cl_bytes(g, es), s, g, tw, Z, Q,
+               w.wT, B, ns, w.step);
   else
-    k_rows<T><<<(unsigned)(B * g.Mz), rows_threads_of(w), rows_smem_for(g, es), s>>>(
-        g, tw, Z, Q, w.wT, B, rows_batched(g, es) ? 1 : 0, ns, w.step);
+    launch_pdl(k_rows<T>, (unsigned)(B * g.Mz), rows_threads_of(w), rows_smem_for(g, es), s, g, tw, Z, Q, w.wT, B,
+               rows_batched(g, es) ? 1 : 0, ns, w.step);
   if (pf) pf->end(RBC_KERNEL_ROWS, s, rows_flops(g, B), rows_bytes(g, B, sizeof(T)));
 }
 
@@ -1351,8 +1361,8 @@ static void launch_zfwd(const Grid& g, const T* W, const Work& w, int B, Prof* p
   const int nch = zfwd_nch_of(g, w, B, tm);
   const size_t smem = (size_t)2 * ((g.Mz + 1) / 2) * tm * 2 * es;
   if (pf) pf->begin(RBC_KERNEL_ZFWD, s);
-  k_zfwd<T><<<(unsigned)(B * 2 * mt * nch), 128, smem, s>>>(g, W, reinterpret_cast<const T*>(w.Q), w.F, S, B, tm, nch,
-                                                            w.nsteps, w.step);
+  launch_pdl(k_zfwd<T>, (unsigned)(B * 2 * mt * nch), 128, smem, s, g, W, reinterpret_cast<const T*>(w.Q), w.F, S, B,
+             tm, nch, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_ZFWD, s, zfwd_flops(g, B), zfwd_bytes(g, B, es));
 }
 
@@ -1375,21 +1385,21 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   const int tms = solve_tms_of(g, w, B);
   const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
-  k_solve<<<(unsigned)(B * 2 * mtiles), solve_threads(g, tms), solve_smem_tms(g, tms), s>>>(
-      g, t, X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags, w.err, B, stage, tms, w.ra, w.nsteps, w.step);
+  launch_pdl(k_solve, (unsigned)(B * 2 * mtiles), solve_threads(g, tms), solve_smem_tms(g, tms), s, g, t, X, w.Xs,
+             w.F, w.R, S, w.wT, nu, w.flags, w.err, B, stage, tms, w.ra, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_advance(const Work& w, cudaStream_t s) {
-  k_advance<<<1, 1, 0, s>>>(w.step);
+  launch_pdl(k_advance, 1, 1, 0, s, w.step);
   count();
   return cudaGetLastError();
 }
 
 cudaError_t launch_advance_loop(const Work& w, cudaGraphConditionalHandle loop, cudaStream_t s) {
-  k_advance_loop<<<1, 1, 0, s>>>(w.step, w.maxs, w.cancel, loop);
+  launch_pdl(k_advance_loop, 1, 1, 0, s, w.step, w.maxs, w.cancel, loop);
   count();
   return cudaGetLastError();
 }
