@@ -1019,7 +1019,7 @@ def run_ncu_case(name):
         return
     Ra, Nx, Nz, dt, B = NCU_CASES[name]
     prec = rbc.RBC_MIXED if name.startswith("mixed") else rbc.RBC_FP64
-    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt, prec)
+    F = rbc.Propagator(Ra, 1.0, 2.0, Nx, Nz, dt, prec, eager=True)
     st = F.new_states(B)
     for b in range(B):
         F.set_state(st[b], initial_temperature(Nx, Nz, seed=b, amplitude=0.3))
