@@ -1125,6 +1125,7 @@ static rbc_status step_batch(rbc_t h, void* d_states, int B, const int* h_nsteps
     auto it = h->tunep->byB.find(B);
     h->w.shapes = it == h->tunep->byB.end() ? nullptr : &it->second;
   }
+  h->w.pdl = B <= kPdlMaxBatch ? 1 : 0;
   CK(cudaMemsetAsync(w.step, 0, sizeof(int), stream));
   CK(cudaMemsetAsync(w.flags, 0, (size_t)B * sizeof(int), stream));
   CK(cudaMemsetAsync(nu, 0, (size_t)B * sizeof(double), stream));

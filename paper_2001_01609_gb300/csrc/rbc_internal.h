@@ -138,28 +138,32 @@ struct Work {
   double* ra;      // [B] Rayleigh number of each state
   const int* cancel;   // device word that ends the step loops early when set, or nullptr
   const Shapes* shapes;   // tuned launch shapes of this batch size, or nullptr
+  int pdl;         // 1: step kernels with programmatic dependent launch (batches of <= kPdlMaxBatch)
   Prof* prof;      // timing, or nullptr
 };
+
+// largest batch whose step kernels use programmatic dependent launch (below)
+constexpr int kPdlMaxBatch = 2;
 
 #ifdef __CUDACC__
 #define RBC_HD __host__ __device__
 
-// Programmatic dependent launch of the step kernels.  Each is launched with
-// programmatic stream serialisation, so its CTAs may be scheduled while the
-// previous kernel on the stream is still running, and each begins with
-// pdl_enter(): griddepcontrol.wait returns once the previous grid has
-// completed and its writes are visible (a hardware dependency, like the
-// stream order it replaces, not a spin), and only then may the next kernel be
-// scheduled, so at most two step kernels are resident at a time.  Launched
-// without the attribute (or first in a graph body) both instructions are
-// no-ops.  The arithmetic, and so every bit, is that of plain stream order.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// Programmatic dependent launch of the step kernels of small batches (at most
+// kPdlMaxBatch states, the coarse sweeps): such a kernel is launched with
+// programmatic stream serialisation and begins with pdl_wait(), which returns
+// once the previous kernel on the stream has completed and its writes are
+// visible (griddepcontrol.wait: a hardware dependency, like the stream order
+// it replaces, not a spin).  No kernel triggers its dependents early, so the
+// next kernel is launched as the previous one's blocks exit: its launch is
+// hidden behind their tail, and its blocks are placed on an idle GPU as in
+// plain stream order (triggering at kernel entry placed them beside running
+// blocks and slowed single-slice steps by up to 10 %).  Launched without the
+// attribute (larger batches, or first in a graph body) the wait is a no-op.
+// The arithmetic, and so every bit, is that of plain stream order.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+inline cudaError_t launch_pdl(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args&&... args) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid;
@@ -170,7 +174,7 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 #else

@@ -73,6 +73,7 @@ void scheme_tableau(int scheme, double AE[5][5], double AI[5][5], int* ns, doubl
   }
 }
 
+
 cudaError_t upload_schemes() {
   double ae[3][5][5], ai[3][5][5];
   for (int sc = 0; sc < 3; ++sc) {
@@ -304,7 +305,7 @@ __device__ void zinv_item(const Grid& g, const T* __restrict__ Bz, const double*
 template <typename T>
 __global__ void __launch_bounds__(256) k_zinv(Grid g, const T* __restrict__ Bz, const double* __restrict__ X, size_t S,
                                               T* __restrict__ Z, int B, const int* nsteps, const int* step) {
-  pdl_enter();
+  pdl_wait();
   zinv_item<T>(g, Bz, X, S, Z, B, nsteps, nsteps ? *step : 0, blockIdx.x, blockDim.x / 32);
 }
 
@@ -574,7 +575,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_rows(Grid g, const C2<T>* __restrict__ tw, const T* __restrict__ Z,
                                               T* __restrict__ Q, double* __restrict__ wT, int B, int batched,
                                               const int* nsteps, const int* step) {
-  pdl_enter();
+  pdl_wait();
   rows_item<T>(g, tw, Z, Q, wT, B, batched, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
@@ -609,7 +610,7 @@ __global__ void __cluster_dims__(kRowsCluster, 1, 1) __launch_bounds__(kRowsThre
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ double red[kRowsThreads];
-  pdl_enter();
+  pdl_wait();
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
   const int row = blockIdx.x / kRowsCluster;
@@ -750,7 +751,7 @@ __device__ void zfwd_item(const Grid& g, const T* __restrict__ W, const T* __res
 template <typename T>
 __global__ void k_zfwd(Grid g, const T* __restrict__ W, const T* __restrict__ Q, double* __restrict__ F, size_t S,
                        int B, int tm, int nch, const int* nsteps, const int* step) {
-  pdl_enter();
+  pdl_wait();
   zfwd_item<T>(g, W, Q, F, S, B, tm, nch, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
@@ -782,18 +783,20 @@ static size_t zfwd_smem(const Grid& g, int B, size_t es) {
 //           the stage, updates of the later RK accumulators;
 //   phase 2 (one thread per column): backward elimination with the UL factors;
 //   phase 3 (same thread): boundary block, forward substitution;
-//   phase 4 (all threads): dt L X_i = 2 (M X_i - r_i) into later accumulators.
-// Inputs are staged in shared memory with coalesced loads, so the sequential
-// phases never wait on global memory.
+//   phase 4 (all threads): dt L X_i = (M X_i - r_i) / gamma into later accumulators.
+// Phase 1 reads F and the step-start state straight from global memory
+// (consecutive threads take consecutive (m, re/im) columns, so the loads
+// coalesce); the right-hand sides, r_i and T_i live in shared memory, three
+// arrays of nq x 2 tms doubles, so that more blocks share an SM.
 // ---------------------------------------------------------------------------
 enum { KT = 0, KP = 1, KU = 2 };
 
 struct SolveSmem {
-  double* F;    // [nq][W] explicit-term coefficients of the system's field
-  double* X;    // [nq][W] step-start state (stage 1)
+  const double* F;   // explicit terms of this slice (global; read in phase 1, coalesced over the columns)
+  const double* X;   // step-start state of this slice (global; stage 1)
   double* y;    // [nq][W] right-hand side, then solution
   double* r;    // [nq][W] r_i of the tau rows
-  double* T;    // [nq][W] T_i, kept for the psi coupling
+  double* T;    // [nq][W] T_i, kept for the psi coupling; the dense path's solution of each system
   int W;        // columns = 2 * tms
   double Ra;    // Rayleigh number of this slice
 };
@@ -836,7 +839,7 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
   double fv = 0.0;
 #pragma unroll
   for (int j = 0; j <= SY::LAM; ++j)
-    if (t + j < nq) fv = fma(SY::tapF(g, tb, p, t, j), sm.F[(t + j) * W + col], fv);
+    if (t + j < nq) fv = fma(SY::tapF(g, tb, p, t, j), sm.F[soff(g, f, 2 * (t + j) + p, m) + c], fv);
   if (KIND != KP) fv = -fv;
   const double dt = g.dt;
   const int sc = g.scheme, ns = g.ns;
@@ -846,7 +849,7 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
     double mx = 0.0;
 #pragma unroll
     for (int j = 0; j <= SY::LAM; ++j)
-      if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), sm.X[(t + j) * W + col], mx);
+      if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), sm.X[soff(g, f, 2 * (t + j) + p, m) + c], mx);
     r = fma(dt * c_AE[sc][1][0], fv, mx);
 #pragma unroll
     for (int l = 2; l <= 4; ++l)
@@ -984,9 +987,8 @@ __device__ __forceinline__ bool solve_dense(const Grid& g, const Tables& tb, int
   }
   if (nq & 1) acc0 = fma(__ldg(row + (size_t)(nq - 1) * nmod), sm.y[(nq - 1) * W + col], acc0);
   const double x = acc0 + acc1;
-  sm.X[r * W + col] = x;
+  sm.T[r * W + col] = x;
   Xo[soff(g, f, 2 * r + p, m) + c] = x;
-  if (KIND == KT) sm.T[r * W + col] = x;
   return isfinite(x);
 }
 
@@ -1031,14 +1033,14 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
   SolveSmem sm;
   sm.W = W;
   sm.Ra = ra ? ra[b] : g.Ra;
-  sm.F = sbuf;
-  sm.X = sm.F + (size_t)nq * W;
-  sm.y = sm.X + (size_t)nq * W;
+  sm.y = sbuf;
   sm.r = sm.y + (size_t)nq * W;
   sm.T = sm.r + (size_t)nq * W;
   double* X0 = X + (size_t)b * S;
   double* Xo = (stage == g.ns) ? X0 : Xs + (size_t)b * S;   // stiffly accurate: last stage = new state
   const double* Fb = F + (size_t)b * S;
+  sm.F = Fb;
+  sm.X = X0;
   double* Rb = R + (size_t)b * 4 * S;
   if (stage == 1 && m0 == 0 && p == 1 && threadIdx.x == 0 && nu != nullptr) {
     // Nu_V(t_n) (Eq. 9) of the step-start state: wall temperature difference of
@@ -1054,19 +1056,6 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
   bool ok = true;
   for (int sys = 0; sys < 2; ++sys) {
     const int f = sys;                               // field 0 = T, 1 = psi / U
-    // stage the field's coefficients of this parity and tile
-    for (int it = threadIdx.x; it < nq * W; it += blockDim.x) {
-      const int q = it / W, col = it - q * W;
-      double fv = 0.0, xv = 0.0;
-      if (col < ncol) {
-        const size_t o = soff(g, f, 2 * q + p, m0 + col / 2) + (col & 1);
-        fv = *(Fb + o);
-        if (stage == 1) xv = *(X0 + o);
-      }
-      sm.F[it] = fv;
-      sm.X[it] = xv;
-    }
-    __syncthreads();
     // phase 1
     const int ntmax = nq - 1;
     for (int it = threadIdx.x; it < ntmax * W; it += blockDim.x) {
@@ -1122,7 +1111,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
       ok = ok && o2;
     }
     __syncthreads();
-    const double* xs = dense ? sm.X : sm.y;
+    const double* xs = dense ? sm.T : sm.y;
     // phase 4
     if (stage < g.ns) {
       for (int it = threadIdx.x; it < ntmax * W; it += blockDim.x) {
@@ -1149,18 +1138,20 @@ __global__ void __launch_bounds__(256) k_solve(Grid g, Tables tb, double* X, dou
                                                size_t S, const double* wT, double* nu, int* flags, int* err, int B,
                                                int stage, int tms, const double* ra, const int* nsteps,
                                                const int* step) {
-  pdl_enter();
+  pdl_wait();
   solve_item(g, tb, X, Xs, F, R, S, wT, nu, flags, err, B, stage, tms, ra, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
 // Modes per k_solve block.  Every column's arithmetic is independent of the
 // tiling, so a small batch (a coarse sweep) takes single-mode tiles and spreads
 // over the SMs instead of leaving most of them idle.
+// shared memory of a k_solve block: y, r and T, nq x 2 tms doubles each
+static size_t solve_smem_tms(const Grid& g, int tms) { return (size_t)3 * g.nq * 2 * tms * 8; }
 static int solve_tile(const Grid& g, int B) {
   int tms = 16;
   while (tms > 1 && (long)B * 2 * ((g.nm + tms - 1) / tms) < 2L * 152) tms >>= 1;
   if (tms > g.nm) tms = g.nm;
-  while (tms > 1 && (size_t)5 * g.nq * 2 * tms * 8 > 200 * 1024) tms >>= 1;
+  while (tms > 1 && solve_smem_tms(g, tms) > 200 * 1024) tms >>= 1;
   return tms;
 }
 // threads of a k_solve block: one per (row, column) of the tile, whole warps, at most 256
@@ -1168,7 +1159,6 @@ static int solve_threads(const Grid& g, int tms) {
   const int items = g.nq * 2 * tms;
   return std::min(256, std::max(32, (items + 31) / 32 * 32));
 }
-static size_t solve_smem_tms(const Grid& g, int tms) { return (size_t)5 * g.nq * 2 * tms * 8; }
 static size_t solve_smem(const Grid& g, int B) { return solve_smem_tms(g, solve_tile(g, B)); }
 
 // The shapes of a launch: the tuned ones where set, else the heuristics.
@@ -1203,7 +1193,7 @@ bool shapes_valid(const Grid& g, const Shapes& sh, size_t es) {
 }
 
 __global__ void k_advance(int* step) {
-  pdl_enter();
+  pdl_wait();
   *step += 1;
 }
 
@@ -1212,7 +1202,7 @@ __global__ void k_advance(int* step) {
 // cancel (may be null): a word another stream sets to stop the loop early
 // (work whose result is no longer wanted, e.g. a speculative Parareal iteration)
 __global__ void k_advance_loop(int* step, const int* maxs, const int* cancel, cudaGraphConditionalHandle loop) {
-  pdl_enter();
+  pdl_wait();
   const int s = *step + 1;
   *step = s;
   const bool stop = cancel != nullptr && *(const volatile int*)cancel != 0;
@@ -1327,17 +1317,17 @@ static void launch_transforms_in(const Grid& g, const Tables& t, const T* Bz, co
   if (sizeof(T) == 4 && t.tcA_psi_hi != nullptr)
     launch_zinv_tc(g, t, w, X, B, ns, s);              // tensor cores, TF32 with split compensation
   else
-    launch_pdl(k_zinv<T>, zb, 32 * kp, kp > 1 ? (size_t)kp * 12 * 32 * 2 * sizeof(T) : 0, s, g, Bz, X, S, Z, B, ns,
-               w.step);
+    launch_pdl(w.pdl != 0, k_zinv<T>, zb, 32 * kp, kp > 1 ? (size_t)kp * 12 * 32 * 2 * sizeof(T) : 0, s, g, Bz, X,
+               S, Z, B, ns, w.step);
   if (pf) pf->end(RBC_KERNEL_ZINV, s, zinv_flops(g, B), zinv_bytes(g, B, sizeof(T)));
   const size_t es = sizeof(T);
   if (pf) pf->begin(RBC_KERNEL_ROWS, s);
   if (rows_cl_of(g, w, B, es))
-    launch_pdl(k_rows_cl<T>, (unsigned)(B * g.Mz * kRowsCluster), kRowsThreads, rows_cl_bytes(g, es), s, g, tw, Z, Q,
-               w.wT, B, ns, w.step);
+    launch_pdl(w.pdl != 0, k_rows_cl<T>, (unsigned)(B * g.Mz * kRowsCluster), kRowsThreads, rows_cl_bytes(g, es), s,
+               g, tw, Z, Q, w.wT, B, ns, w.step);
   else
-    launch_pdl(k_rows<T>, (unsigned)(B * g.Mz), rows_threads_of(w), rows_smem_for(g, es), s, g, tw, Z, Q, w.wT, B,
-               rows_batched(g, es) ? 1 : 0, ns, w.step);
+    launch_pdl(w.pdl != 0, k_rows<T>, (unsigned)(B * g.Mz), rows_threads_of(w), rows_smem_for(g, es), s, g, tw, Z, Q,
+               w.wT, B, rows_batched(g, es) ? 1 : 0, ns, w.step);
   if (pf) pf->end(RBC_KERNEL_ROWS, s, rows_flops(g, B), rows_bytes(g, B, sizeof(T)));
 }
 
@@ -1361,8 +1351,8 @@ static void launch_zfwd(const Grid& g, const T* W, const Work& w, int B, Prof* p
   const int nch = zfwd_nch_of(g, w, B, tm);
   const size_t smem = (size_t)2 * ((g.Mz + 1) / 2) * tm * 2 * es;
   if (pf) pf->begin(RBC_KERNEL_ZFWD, s);
-  launch_pdl(k_zfwd<T>, (unsigned)(B * 2 * mt * nch), 128, smem, s, g, W, reinterpret_cast<const T*>(w.Q), w.F, S, B,
-             tm, nch, w.nsteps, w.step);
+  launch_pdl(w.pdl != 0, k_zfwd<T>, (unsigned)(B * 2 * mt * nch), 128, smem, s, g, W, reinterpret_cast<const T*>(w.Q),
+             w.F, S, B, tm, nch, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_ZFWD, s, zfwd_flops(g, B), zfwd_bytes(g, B, es));
 }
 
@@ -1385,21 +1375,21 @@ cudaError_t launch_stage(const Grid& g, const Tables& t, const Work& w, double* 
   const int tms = solve_tms_of(g, w, B);
   const int mtiles = (g.nm + tms - 1) / tms;
   if (pf) pf->begin(RBC_KERNEL_SOLVE, s);
-  launch_pdl(k_solve, (unsigned)(B * 2 * mtiles), solve_threads(g, tms), solve_smem_tms(g, tms), s, g, t, X, w.Xs,
-             w.F, w.R, S, w.wT, nu, w.flags, w.err, B, stage, tms, w.ra, w.nsteps, w.step);
+  launch_pdl(w.pdl != 0, k_solve, (unsigned)(B * 2 * mtiles), solve_threads(g, tms), solve_smem_tms(g, tms), s, g, t,
+             X, w.Xs, w.F, w.R, S, w.wT, nu, w.flags, w.err, B, stage, tms, w.ra, w.nsteps, w.step);
   if (pf) pf->end(RBC_KERNEL_SOLVE, s, solve_flops(g, B), solve_bytes(g, B));
   count(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_advance(const Work& w, cudaStream_t s) {
-  launch_pdl(k_advance, 1, 1, 0, s, w.step);
+  launch_pdl(w.pdl != 0, k_advance, 1, 1, 0, s, w.step);
   count();
   return cudaGetLastError();
 }
 
 cudaError_t launch_advance_loop(const Work& w, cudaGraphConditionalHandle loop, cudaStream_t s) {
-  launch_pdl(k_advance_loop, 1, 1, 0, s, w.step, w.maxs, w.cancel, loop);
+  launch_pdl(w.pdl != 0, k_advance_loop, 1, 1, 0, s, w.step, w.maxs, w.cancel, loop);
   count();
   return cudaGetLastError();
 }

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
                                                  const float* __restrict__ Alo_T, const double* __restrict__ X,
                                                  size_t S, float* __restrict__ Z, int B, const int* nsteps,
                                                  const int* step, int* flags, int* err, int NB) {
-  pdl_enter();
+  pdl_wait();
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[4], empty[4], accb[1];
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
                                                  const float* __restrict__ Whi1, const float* __restrict__ Wlo1,
                                                  const float* __restrict__ Q, double* __restrict__ F, size_t S, int B,
                                                  const int* nsteps, const int* step, int* flags, int* err, int NB) {
-  pdl_enter();
+  pdl_wait();
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[4], empty[4], accb[1];
@@ -739,9 +739,9 @@ cudaError_t launch_zfwd_tc(const Grid& g, const Tables& t, const Work& w, int B,
     allowed = (int)smem;
   }
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
-  return launch_pdl(k_zfwd_tc, (unsigned)(B * 2 * 2 * ntile * tc_zfwd_mtiles(g)), 128, smem, s, g, t.tcW_hi[0],
-                    t.tcW_lo[0], t.tcW_hi[1], t.tcW_lo[1], reinterpret_cast<const float*>(w.Q), w.F, state_doubles(g),
-                    B, w.nsteps, w.step, w.flags, w.err, tc_zfwd_stages(g));
+  return launch_pdl(w.pdl != 0, k_zfwd_tc, (unsigned)(B * 2 * 2 * ntile * tc_zfwd_mtiles(g)), 128, smem, s, g,
+                    t.tcW_hi[0], t.tcW_lo[0], t.tcW_hi[1], t.tcW_lo[1], reinterpret_cast<const float*>(w.Q), w.F,
+                    state_doubles(g), B, w.nsteps, w.step, w.flags, w.err, tc_zfwd_stages(g));
 }
 
 cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const double* X, int B, const int* ns,
@@ -755,9 +755,9 @@ cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const 
   }
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
   const int units = tc_zinv_tile_per_cta(g) ? tc_zinv_mtiles(g, 4) + tc_zinv_mtiles(g, 2) : 2;
-  return launch_pdl(k_zinv_tc, (unsigned)(B * ntile * units), 128, smem, s, g, t.tcA_psi_hi, t.tcA_psi_lo, t.tcA_T_hi,
-                    t.tcA_T_lo, X, state_doubles(g), reinterpret_cast<float*>(w.Z), B, ns, w.step, w.flags, w.err,
-                    tc_zinv_stages(g));
+  return launch_pdl(w.pdl != 0, k_zinv_tc, (unsigned)(B * ntile * units), 128, smem, s, g, t.tcA_psi_hi,
+                    t.tcA_psi_lo, t.tcA_T_hi, t.tcA_T_lo, X, state_doubles(g), reinterpret_cast<float*>(w.Z), B, ns,
+                    w.step, w.flags, w.err, tc_zinv_stages(g));
 }
 
 bool tc_zinv_supported(const Grid& g) { return g.Nz >= 64 && tc_zinv_smem_bytes(g) <= 200 * 1024; }
