@@ -38,6 +38,10 @@ namespace {
 constexpr int kTileN = 64;       // columns per CTA (32 Fourier modes x re/im)
 constexpr int kTileM = 128;      // rows per MMA tile
 constexpr int kChunkFloats = kTileM * 32;   // one 128-row image chunk of 128-byte rows: 16 KB
+// threads of a tensor-core CTA: eight warps; in the epilogue warp w reads the
+// accumulator's lane quarter w % 4 (the quarter a warp may access) and column
+// half w / 4, so twice as many stores are in flight as with four warps
+constexpr int kTcThreads = 256;
 constexpr long long kWaitLimit = 1LL << 24;   // default spin limit of a bounded wait
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -278,7 +282,7 @@ size_t tc_zinv_smem_bytes(const Grid& g) {
 // the four warps read the accumulator and form the fields.
 __host__ __device__ inline bool tc_zinv_tile_per_cta(const Grid& g) { return tc_zinv_kchunks(g) <= 2; }
 
-__global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict__ Ahi_psi,
+__global__ void __launch_bounds__(kTcThreads) k_zinv_tc(Grid g, const float* __restrict__ Ahi_psi,
                                                  const float* __restrict__ Alo_psi, const float* __restrict__ Ahi_T,
                                                  const float* __restrict__ Alo_T, const double* __restrict__ X,
                                                  size_t S, float* __restrict__ Z, int B, const int* nsteps,
@@ -419,12 +423,13 @@ __global__ void __launch_bounds__(128) k_zinv_tc(Grid g, const float* __restrict
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok) break;
     const int rows_per_j = nops, jper = kTileM / nops;
-    const int r = warp * 32 + lane;           // tile row = TMEM lane
+    const int r = (warp & 3) * 32 + lane;     // tile row = TMEM lane
     const int jl = r / rows_per_j, op = r % rows_per_j;
     const int j = t * jper + jl;
-    for (int cc = 0; cc < kTileN; cc += 16) {
+    const int cbeg = (warp >> 2) * (kTileN / 2);
+    for (int cc = cbeg; cc < cbeg + kTileN / 2; cc += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
+      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cc, v);
       float P[4][16];
 #pragma unroll
       for (int qq = 0; qq < 4; ++qq)
@@ -557,7 +562,7 @@ bool tc_zfwd_supported(const Grid& g) { return g.Nz >= 64 && tc_zfwd_smem_bytes(
 
 // CTA per (slice, field, parity, 64-column tile, 128-row tile of W's rows of
 // that parity); the images stream in through the bulk-copy ring of k_zinv_tc.
-__global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict__ Whi0, const float* __restrict__ Wlo0,
+__global__ void __launch_bounds__(kTcThreads) k_zfwd_tc(Grid g, const float* __restrict__ Whi0, const float* __restrict__ Wlo0,
                                                  const float* __restrict__ Whi1, const float* __restrict__ Wlo1,
                                                  const float* __restrict__ Q, double* __restrict__ F, size_t S, int B,
                                                  const int* nsteps, const int* step, int* flags, int* err, int NB) {
@@ -697,10 +702,11 @@ __global__ void __launch_bounds__(128) k_zfwd_tc(Grid g, const float* __restrict
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     double* Fb = F + (size_t)b * S;
-    const int n = 2 * (t * kTileM + warp * 32 + lane) + p;   // tile row = TMEM lane
-    for (int cc = 0; cc < kTileN; cc += 16) {
+    const int n = 2 * (t * kTileM + (warp & 3) * 32 + lane) + p;   // tile row = TMEM lane
+    const int cbeg = (warp >> 2) * (kTileN / 2);
+    for (int cc = cbeg; cc < cbeg + kTileN / 2; cc += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
+      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cc, v);
       if (n >= g.Nz) continue;
 #pragma unroll
       for (int i = 0; i < 16; i += 2) {
@@ -739,7 +745,7 @@ cudaError_t launch_zfwd_tc(const Grid& g, const Tables& t, const Work& w, int B,
     allowed = (int)smem;
   }
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
-  return launch_pdl(w.pdl != 0, k_zfwd_tc, (unsigned)(B * 2 * 2 * ntile * tc_zfwd_mtiles(g)), 128, smem, s, g,
+  return launch_pdl(w.pdl != 0, k_zfwd_tc, (unsigned)(B * 2 * 2 * ntile * tc_zfwd_mtiles(g)), kTcThreads, smem, s, g,
                     t.tcW_hi[0], t.tcW_lo[0], t.tcW_hi[1], t.tcW_lo[1], reinterpret_cast<const float*>(w.Q), w.F,
                     state_doubles(g), B, w.nsteps, w.step, w.flags, w.err, tc_zfwd_stages(g));
 }
@@ -755,7 +761,7 @@ cudaError_t launch_zinv_tc(const Grid& g, const Tables& t, const Work& w, const 
   }
   const int ntile = (2 * g.nm + kTileN - 1) / kTileN;
   const int units = tc_zinv_tile_per_cta(g) ? tc_zinv_mtiles(g, 4) + tc_zinv_mtiles(g, 2) : 2;
-  return launch_pdl(w.pdl != 0, k_zinv_tc, (unsigned)(B * ntile * units), 128, smem, s, g, t.tcA_psi_hi,
+  return launch_pdl(w.pdl != 0, k_zinv_tc, (unsigned)(B * ntile * units), kTcThreads, smem, s, g, t.tcA_psi_hi,
                     t.tcA_psi_lo, t.tcA_T_hi, t.tcA_T_lo, X, state_doubles(g), reinterpret_cast<float*>(w.Z), B, ns,
                     w.step, w.flags, w.err, tc_zinv_stages(g));
 }
