@@ -38,10 +38,12 @@ namespace {
 constexpr int kTileN = 64;       // columns per CTA (32 Fourier modes x re/im)
 constexpr int kTileM = 128;      // rows per MMA tile
 constexpr int kChunkFloats = kTileM * 32;   // one 128-row image chunk of 128-byte rows: 16 KB
-// threads of a tensor-core CTA: eight warps; in the epilogue warp w reads the
-// accumulator's lane quarter w % 4 (the quarter a warp may access) and column
-// half w / 4, so twice as many stores are in flight as with four warps
-constexpr int kTcThreads = 256;
+// threads of a tensor-core CTA: kTcGroups groups of four warps; in the
+// epilogue warp w reads the accumulator's lane quarter w % 4 (the quarter a
+// warp may access) and the column range w / 4 of kTileN / kTcGroups columns,
+// so that kTcGroups times as many stores are in flight as with four warps
+constexpr int kTcGroups = 2;
+constexpr int kTcThreads = 128 * kTcGroups;
 constexpr long long kWaitLimit = 1LL << 24;   // default spin limit of a bounded wait
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -426,8 +428,8 @@ __global__ void __launch_bounds__(kTcThreads) k_zinv_tc(Grid g, const float* __r
     const int r = (warp & 3) * 32 + lane;     // tile row = TMEM lane
     const int jl = r / rows_per_j, op = r % rows_per_j;
     const int j = t * jper + jl;
-    const int cbeg = (warp >> 2) * (kTileN / 2);
-    for (int cc = cbeg; cc < cbeg + kTileN / 2; cc += 16) {
+    const int cbeg = (warp >> 2) * (kTileN / kTcGroups);
+    for (int cc = cbeg; cc < cbeg + kTileN / kTcGroups; cc += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cc, v);
       float P[4][16];
@@ -703,8 +705,8 @@ __global__ void __launch_bounds__(kTcThreads) k_zfwd_tc(Grid g, const float* __r
   if (ok) {
     double* Fb = F + (size_t)b * S;
     const int n = 2 * (t * kTileM + (warp & 3) * 32 + lane) + p;   // tile row = TMEM lane
-    const int cbeg = (warp >> 2) * (kTileN / 2);
-    for (int cc = cbeg; cc < cbeg + kTileN / 2; cc += 16) {
+    const int cbeg = (warp >> 2) * (kTileN / kTcGroups);
+    for (int cc = cbeg; cc < cbeg + kTileN / kTcGroups; cc += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cc, v);
       if (n >= g.Nz) continue;
