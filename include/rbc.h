@@ -365,17 +365,23 @@ int parareal_coarse_sms(parareal_t p);
  * RK443 steps of a batch of B states with candidate launch shapes that leave
  * every result unchanged bit for bit (modes per stage-solve block, modes and
  * n-chunks per z-forward block, the clustered or the one-block-per-row x-FFT
- * kernel and the latter's block size; reduction orders depend on the grid
- * only), by a coordinate search
+ * kernel and the latter's block size and shared-memory layout; reduction
+ * orders depend on the grid only), by a coordinate search
  * from the built-in heuristics, and keeps the fastest for batches of B states
  * on this handle (and on the library's copies of it that Parareal uses).
  * out_ms (may be NULL): the time per step with the heuristics and with the
  * shapes kept.  Synchronous on `stream`; allocates B scratch states for the
  * duration of the call; RBC_EINVAL for B < 1.  rbc_tuned_shapes writes the
- * shapes kept for B (0 / -1: the heuristic) to host out[5] = (solve modes,
- * z-forward modes, z-forward chunks, clustered rows, row-kernel threads).  */
+ * shapes kept for B (0 / -1: the heuristic) to host out[6] = (solve modes,
+ * z-forward modes, z-forward chunks, clustered rows, row-kernel threads,
+ * row-kernel layout: 1 lean, 0 full).  rbc_set_shapes keeps the host array
+ * in[6] (same order and meaning) for batches of B states without timing
+ * anything; RBC_EINVAL if a shape is not valid for the grid (a power of two
+ * up to 16 solve modes or 32 z-forward modes, 1-8 chunks, 256/512/1024 row
+ * threads, a layout that fits).  Any valid shapes give the same bits.      */
 rbc_status rbc_autotune(rbc_t h, int B, double out_ms[2], cudaStream_t stream);
-rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[5]);
+rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[6]);
+rbc_status rbc_set_shapes(rbc_t h, int B, const int in[6]);
 
 /* ---- Instrumentation (outside the paper's method) ----
  * Kernel kinds of one RK443 stage: z-inverse transform, row kernel (x-FFTs and

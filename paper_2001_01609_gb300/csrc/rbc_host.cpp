@@ -1353,6 +1353,11 @@ extern "C" rbc_status rbc_autotune(rbc_t h, int B, double out_ms[2], cudaStream_
     c.rows_threads = th;
     if ((s = trial(c)) != RBC_OK) return s;
   }
+  for (int ln = 0; ln <= 1; ++ln) {             // its shared-memory layout
+    Shapes c = best;
+    c.rows_lean = ln;
+    if ((s = trial(c)) != RBC_OK) return s;
+  }
   for (int tm = 4; tm <= 32; tm *= 2)
     for (int nch = 1; nch <= 8; nch *= 2) {
       Shapes c = best;
@@ -1374,7 +1379,7 @@ extern "C" rbc_status rbc_autotune(rbc_t h, int B, double out_ms[2], cudaStream_
   return RBC_OK;
 }
 
-extern "C" rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[5]) {
+extern "C" rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[6]) {
   if (!h || !out) return fail(RBC_EINVAL, "null argument");
   const auto it = h->tunep->byB.find(B);
   const Shapes sh = it == h->tunep->byB.end() ? Shapes{} : it->second;
@@ -1383,6 +1388,24 @@ extern "C" rbc_status rbc_tuned_shapes(rbc_t h, int B, int out[5]) {
   out[2] = sh.zfwd_nch;
   out[3] = sh.rows_cl;
   out[4] = sh.rows_threads;
+  out[5] = sh.rows_lean;
+  return RBC_OK;
+}
+
+extern "C" rbc_status rbc_set_shapes(rbc_t h, int B, const int in[6]) {
+  if (!h || !in || B < 1) return fail(RBC_EINVAL, "null argument or B < 1");
+  Shapes sh;
+  sh.solve_tms = in[0];
+  sh.zfwd_tm = in[1];
+  sh.zfwd_nch = in[2];
+  sh.rows_cl = in[3];
+  sh.rows_threads = in[4];
+  sh.rows_lean = in[5];
+  if (sh.solve_tms < 0 || sh.zfwd_tm < 0 || sh.zfwd_nch < 0 || sh.rows_cl < -1 || sh.rows_cl > 1 ||
+      sh.rows_threads < 0 || !shapes_valid(h->g, sh, h->g.mixed ? 4 : 8))
+    return fail(RBC_EINVAL, "launch shapes not valid for this grid");
+  h->tunep->byB[B] = sh;
+  h->tunep->gen++;
   return RBC_OK;
 }
 

@@ -117,6 +117,7 @@ struct Shapes {
   int zfwd_nch = 0;    // chunks of the n range per k_zfwd block (1, 2, 4, 8)
   int rows_cl = -1;    // 1: the clustered row kernel, 0: one block per row
   int rows_threads = 0;   // threads of a k_rows block (256, 512 or 1024)
+  int rows_lean = -1;  // 1: k_rows with 5 + 3 shared rows, 0: 5 + 5 (where either fits)
 };
 
 // Per-call workspace pointers (capacity >= B states).

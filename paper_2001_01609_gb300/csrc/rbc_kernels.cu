@@ -388,15 +388,22 @@ __device__ C2<T>* fft_smem(C2<T>* a, C2<T>* b, int N, int na, int sign, const C2
 }
 
 // Shared memory of k_rows: two ping-pong sets of 5 complex rows and the
-// twiddles (11 Mx complex values), or, when that does not fit, two single rows,
-// the twiddles and 9 real fields, with the five inverse FFTs in turn.
+// twiddles (11 Mx complex values); lean: 5 + 3 rows and the twiddles (9 Mx),
+// the inverse FFTs in groups of three and two rows; or, when neither fits, two
+// single rows, the twiddles and 9 real fields, with the five inverse FFTs in turn.
 static size_t rows_bytes_batched(const Grid& g, size_t es) { return (size_t)g.Mx * 11 * 2 * es; }
+static size_t rows_bytes_lean(const Grid& g, size_t es) { return (size_t)g.Mx * 9 * 2 * es; }
 static size_t rows_bytes_serial(const Grid& g, size_t es) { return (size_t)g.Mx * (3 * 2 + 9) * es; }
 static bool rows_batched(const Grid& g, size_t es) { return rows_bytes_batched(g, es) <= 200 * 1024; }
-static size_t rows_smem_for(const Grid& g, size_t es) {
-  return rows_batched(g, es) ? rows_bytes_batched(g, es) : rows_bytes_serial(g, es);
+static size_t rows_smem_for(const Grid& g, size_t es, bool lean) {
+  return rows_batched(g, es) ? (lean ? rows_bytes_lean(g, es) : rows_bytes_batched(g, es)) : rows_bytes_serial(g, es);
 }
-size_t rows_smem_bytes(const Grid& g) { return rows_smem_for(g, 8); }
+size_t rows_smem_bytes(const Grid& g) { return rows_smem_for(g, 8, false); }
+// The lean layout by default where the full one leaves room for a single block
+// per SM and the lean one for two.
+static bool rows_lean_default(const Grid& g, size_t es) {
+  return rows_batched(g, es) && rows_bytes_batched(g, es) > 113 * 1024 && rows_bytes_lean(g, es) <= 113 * 1024;
+}
 
 // Deterministic block sum: the fixed tree red[t] += red[t + s], s = blockDim/2
 // down to 1 (blockDim a power of two, at least 32).  Levels s >= 32 go through
@@ -478,7 +485,8 @@ __device__ double block_sum256(double v, double* red) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* __restrict__ Z, T* __restrict__ Q,
-                          double* __restrict__ wT, int B, int batched, const int* nsteps, int stepidx, int blk) {
+                          double* __restrict__ wT, int B, int batched, int lean, const int* nsteps, int stepidx,
+                          int blk) {
   using V = C2<T>;
   extern __shared__ __align__(16) unsigned char rsm[];
   const int b = blk / g.Mz, j = blk - b * g.Mz;
@@ -488,21 +496,42 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
   const size_t fs = (size_t)g.Mz * nm * 2;
   const T* zrow = Z + (size_t)b * 9 * fs + (size_t)j * nm * 2;
   const V* fld;      // field value at x: real/imag parts of the five packed rows
+  const V* fld3 = nullptr;   // rows 3 and 4 (batched: fld + 3 Mx unless lean)
   V* A;
   V* Bf;
   V* tws;
+  V* P = nullptr;    // free rows after the inverse FFTs: products, scratch, x-mean terms
+  V* P2 = nullptr;
+  T* vU = nullptr;
   T* fr = nullptr;
   if (batched) {
+    // the five packed rows and the FFT scratch: five more rows, or (lean) three,
+    // the inverse FFTs then running in groups of three and two rows (the same
+    // arithmetic per row; less shared memory, more blocks per SM)
     A = reinterpret_cast<V*>(rsm);
     Bf = A + 5 * Mx;
-    tws = Bf + 5 * Mx;
+    tws = Bf + (lean ? 3 : 5) * Mx;
     for (int x = threadIdx.x; x < Mx; x += blockDim.x) tws[x] = ldgc<T>(tw + x);
     for (int it = threadIdx.x; it < 5 * Mx; it += blockDim.x) {
       const int pr = it / Mx, x = it - pr * Mx;
       A[it] = rows_packed<T>(g, zrow, fs, pr, x);
     }
     __syncthreads();
-    fld = fft_smem<T>(A, Bf, Mx, 5, +1, tws);
+    if (!lean) {
+      fld = fft_smem<T>(A, Bf, Mx, 5, +1, tws);
+      fld3 = fld + 3 * Mx;
+      P = (fld == A) ? Bf : A;                 // the five rows not holding the fields
+      vU = reinterpret_cast<T*>(P + Mx);
+      P2 = (P == A) ? Bf : A;                  // a field row, free once the products are formed
+    } else {
+      fld = fft_smem<T>(A, Bf, Mx, 3, +1, tws);
+      V* fr3 = fld == A ? Bf : A;              // rows free after the first group
+      fld3 = fft_smem<T>(A + 3 * Mx, fr3, Mx, 2, +1, tws);
+      // three free rows: the scratch (even pass count) or A[2..4] (odd)
+      P = fld == A ? Bf : A + 2 * Mx;
+      vU = reinterpret_cast<T*>(P + Mx);
+      P2 = P + 2 * Mx;
+    }
   } else {
     A = reinterpret_cast<V*>(rsm);
     Bf = A + Mx;
@@ -520,35 +549,34 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
       __syncthreads();
     }
     fld = nullptr;
+    P = A;
+    P2 = Bf;
+    vU = reinterpret_cast<T*>(P2);            // the scratch row holds the 2 Mx terms
   }
   auto field = [&](int fi, int x) -> T {
     if (fld) {
-      const V v = fld[(fi >> 1) * Mx + x];
+      const int k = fi >> 1;
+      const V v = k < 3 ? fld[k * Mx + x] : fld3[(k - 3) * Mx + x];
       return (fi & 1) ? v.y : v.x;
     }
     return fr[fi * Mx + x];
   };
-  // products into the first row of the buffer not holding the fields
-  V* P = (fld == A) ? Bf : A;
-  V* P2 = (P == A) ? Bf : A;                           // scratch row for the ping-pong
-  // per-point x-mean terms: the rows after P (batched) or the scratch row
-  // (one row at a time, FP64 only: 2 Mx doubles fit in one complex row)
-  double* vU = reinterpret_cast<double*>(batched ? P + Mx : P2);
-  double* vW = vU + Mx;
+  // per-point x-mean terms (in T: each is the FP64 sum's exact input)
+  T* vW = vU + Mx;
   for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
     const T u = field(0, x), w = field(1, x);
     const T nO = fma(u, field(2, x), w * field(3, x));
-    vU[x] = (double)fma(u, field(4, x), w * field(5, x));
+    vU[x] = fma(u, field(4, x), w * field(5, x));
     const T nT = fma(u, field(7, x), w * field(8, x));
-    vW[x] = (double)(w * field(6, x));
+    vW[x] = w * field(6, x);
     P[x] = mk2<T>(nT, nO);
   }
   __syncthreads();
   double nU = 0.0, wt = 0.0;
   if (threadIdx.x < 256)
     for (int x = threadIdx.x; x < Mx; x += 256) {
-      nU += vU[x];
-      wt += vW[x];
+      nU += (double)vU[x];
+      wt += (double)vW[x];
     }
   const double sU = block_sum256(nU, red);
   const double sW = block_sum256(wt, red);
@@ -574,9 +602,9 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_rows(Grid g, const C2<T>* __restrict__ tw, const T* __restrict__ Z,
                                               T* __restrict__ Q, double* __restrict__ wT, int B, int batched,
-                                              const int* nsteps, const int* step) {
+                                              int lean, const int* nsteps, const int* step) {
   pdl_wait();
-  rows_item<T>(g, tw, Z, Q, wT, B, batched, nsteps, nsteps ? *step : 0, blockIdx.x);
+  rows_item<T>(g, tw, Z, Q, wT, B, batched, lean, nsteps, nsteps ? *step : 0, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1177,6 +1205,9 @@ static bool rows_cl_of(const Grid& g, const Work& w, int B, size_t es) {
 static int rows_threads_of(const Work& w) {
   return (w.shapes && w.shapes->rows_threads > 0) ? w.shapes->rows_threads : kRowsThreads;
 }
+static bool rows_lean_of(const Grid& g, const Work& w, size_t es) {
+  return (w.shapes && w.shapes->rows_lean >= 0) ? w.shapes->rows_lean != 0 : rows_lean_default(g, es);
+}
 
 bool shapes_valid(const Grid& g, const Shapes& sh, size_t es) {
   if (sh.solve_tms > 0 && (sh.solve_tms > 16 || (sh.solve_tms & (sh.solve_tms - 1)) ||
@@ -1189,6 +1220,7 @@ bool shapes_valid(const Grid& g, const Shapes& sh, size_t es) {
   if (sh.rows_cl == 1 && rows_cl_bytes(g, es) > 200 * 1024) return false;
   if (sh.rows_threads != 0 && sh.rows_threads != 256 && sh.rows_threads != 512 && sh.rows_threads != 1024)
     return false;
+  if (sh.rows_lean < -1 || sh.rows_lean > 1 || (sh.rows_lean == 1 && !rows_batched(g, es))) return false;
   return true;
 }
 
@@ -1290,12 +1322,12 @@ cudaError_t configure_kernels(const Grid& g) {
   static int a_rows_d = 48 * 1024, a_rows_f = 48 * 1024, a_solve = 48 * 1024;
   static int a_zfwd_d = 48 * 1024, a_zfwd_f = 48 * 1024;
   static int a_rcl_d = 48 * 1024, a_rcl_f = 48 * 1024;
-  cudaError_t e = allow_smem(k_rows<double>, (int)rows_smem_for(g, 8), a_rows_d);
+  cudaError_t e = allow_smem(k_rows<double>, (int)rows_smem_for(g, 8, false), a_rows_d);
   if (e == cudaSuccess && rows_cl_bytes(g, 8) <= 200 * 1024)
     e = allow_smem(k_rows_cl<double>, (int)rows_cl_bytes(g, 8), a_rcl_d);
   if (e == cudaSuccess && rows_cl_bytes(g, 4) <= 200 * 1024)
     e = allow_smem(k_rows_cl<float>, (int)rows_cl_bytes(g, 4), a_rcl_f);
-  if (e == cudaSuccess) e = allow_smem(k_rows<float>, (int)rows_smem_for(g, 4), a_rows_f);
+  if (e == cudaSuccess) e = allow_smem(k_rows<float>, (int)rows_smem_for(g, 4, false), a_rows_f);
   if (e == cudaSuccess)
     e = allow_smem(k_solve, (int)std::max(solve_smem(g, 1), solve_smem(g, 1 << 20)), a_solve);
   if (e == cudaSuccess)
@@ -1326,8 +1358,9 @@ static void launch_transforms_in(const Grid& g, const Tables& t, const T* Bz, co
     launch_pdl(w.pdl != 0, k_rows_cl<T>, (unsigned)(B * g.Mz * kRowsCluster), kRowsThreads, rows_cl_bytes(g, es), s,
                g, tw, Z, Q, w.wT, B, ns, w.step);
   else
-    launch_pdl(w.pdl != 0, k_rows<T>, (unsigned)(B * g.Mz), rows_threads_of(w), rows_smem_for(g, es), s, g, tw, Z, Q,
-               w.wT, B, rows_batched(g, es) ? 1 : 0, ns, w.step);
+    launch_pdl(w.pdl != 0, k_rows<T>, (unsigned)(B * g.Mz), rows_threads_of(w),
+               rows_smem_for(g, es, rows_lean_of(g, w, es)), s, g, tw, Z, Q, w.wT, B, rows_batched(g, es) ? 1 : 0,
+               rows_lean_of(g, w, es) ? 1 : 0, ns, w.step);
   if (pf) pf->end(RBC_KERNEL_ROWS, s, rows_flops(g, B), rows_bytes(g, B, sizeof(T)));
 }
 

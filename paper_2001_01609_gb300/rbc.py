@@ -26,7 +26,7 @@ EXPORTS = [
     "rbc_prolong", "rbc_parareal_correct", "rbc_l2_diff", "parareal_set_schedule", "parareal_coarse_sms",
     "rbc_diag_size", "rbc_diagnostics", "rbc_set_wait_limit", "parareal_set_depth",
     "rbc_step_batch_sampled", "rbc_stat_summary", "parareal_set_sampling", "parareal_stat_means",
-    "rbc_autotune", "rbc_tuned_shapes",
+    "rbc_autotune", "rbc_tuned_shapes", "rbc_set_shapes",
 ]
 KERNEL_NAMES = ["k_zinv", "k_rows", "k_zfwd", "k_solve"]
 
@@ -92,6 +92,7 @@ def load():
         "parareal_stat_means": (I, [P, PD]),
         "rbc_autotune": (I, [P, I, PD, P]),
         "rbc_tuned_shapes": (I, [P, I, PI]),
+        "rbc_set_shapes": (I, [P, I, PI]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -257,10 +258,16 @@ class Propagator:
         return float(out[0]), float(out[1])
 
     def tuned_shapes(self, B):
-        """(solve modes, z-forward modes, z-forward chunks, clustered rows, row threads) kept for B."""
-        out = (ctypes.c_int * 5)()
+        """(solve modes, z-forward modes, z-forward chunks, clustered rows, row threads,
+        lean row layout) kept for B."""
+        out = (ctypes.c_int * 6)()
         _check(load().rbc_tuned_shapes(self.h, int(B), out))
         return tuple(out)
+
+    def set_shapes(self, B, shapes):
+        """rbc_set_shapes: keep these six launch shapes for batches of B states."""
+        arr = (ctypes.c_int * 6)(*[int(v) for v in shapes])
+        _check(load().rbc_set_shapes(self.h, int(B), arr))
 
     def l2_temperature(self, state, stream=None):
         out = np.zeros(1)

@@ -410,7 +410,7 @@ def test_autotuned_shapes_give_identical_bits(rbc, precision, Nx, Nz, B):
     t_heur, t_best = T.autotune(B)
     assert 0 < t_best <= t_heur
     shapes = T.tuned_shapes(B)
-    assert len(shapes) == 5
+    assert len(shapes) == 6
     a, b = F.new_states(B), T.new_states(B)
     for i in range(B):
         F.set_state(a[i], initial_temperature(Nx, Nz, seed=40 + i, amplitude=0.3))
@@ -421,3 +421,31 @@ def test_autotuned_shapes_give_identical_bits(rbc, precision, Nx, Nz, B):
     T.step_batch(b, 4, nb)
     assert torch.equal(a, b) and torch.equal(na, nb)
     assert F.check_diverged() == T.check_diverged() == rbc.RBC_OK
+
+
+@pytest.mark.parametrize("precision,Nx,Nz,B", [(0, 32, 16, 6), (1, 64, 64, 3), (2, 128, 64, 2), (1, 256, 64, 4)])
+def test_pinned_launch_shapes_give_identical_bits(rbc, precision, Nx, Nz, B):
+    """rbc_set_shapes: every valid combination of the row kernel's form, block
+    size and shared-memory layout (full or lean), the solve tile and the
+    z-forward tile gives the bits of the heuristics; invalid shapes are refused."""
+    ref = rbc.Propagator(2e4, 1.0, 2.0, Nx, Nz, 2e-4, precision)
+    a = ref.new_states(B)
+    for i in range(B):
+        ref.set_state(a[i], initial_temperature(Nx, Nz, seed=70 + i, amplitude=0.3))
+    start = a.clone()
+    na = torch.zeros(B, dtype=torch.float64, device="cuda")
+    ref.step_batch(a, 3, na)
+    cases = [(0, 0, 0, 0, 0, 0), (0, 0, 0, 0, 0, 1), (0, 0, 0, 0, 1024, 1), (0, 0, 0, 1, 0, -1),
+             (1, 4, 1, 0, 512, 0), (16, 32, 8, 0, 256, 1), (2, 8, 2, -1, 0, -1)]
+    for sh in cases:
+        T = rbc.Propagator(2e4, 1.0, 2.0, Nx, Nz, 2e-4, precision)
+        T.set_shapes(B, sh)
+        assert T.tuned_shapes(B) == sh
+        b = start.clone()
+        nb = torch.zeros(B, dtype=torch.float64, device="cuda")
+        T.step_batch(b, 3, nb)
+        assert torch.equal(a, b) and torch.equal(na, nb), sh
+        T.close()
+    for bad in ((3, 0, 0, 0, 0, 0), (0, 0, 0, 2, 0, 0), (0, 0, 0, 0, 300, 0), (0, 0, 0, 0, 0, 2)):
+        with pytest.raises(rbc.RBCError):
+            ref.set_shapes(B, bad)
