@@ -137,10 +137,10 @@ class Clocks:
 # coarse: one slice of 128 x 32; the stage-kernel traffic summary in profiles/),
 # valid only while the kernel sources are those that were captured.
 NCU_TRAFFIC_SOURCES = ("paper_2001_01609_gb300/csrc/rbc_kernels.cu", "paper_2001_01609_gb300/csrc/rbc_internal.h")
-NCU_TRAFFIC_SHA256 = "566a2407764a7994c4243b817f66217b74a46d672b9bd3185c433a0d9afda09c"
+NCU_TRAFFIC_SHA256 = "45e789e1c2b16906bb6864b32a5bc06883c991f7c7122409c3fb9bfeffc016ed"
 NCU_TRAFFIC = {
-    "coarse:k_zinv": 128154, "coarse:k_rows": 494848, "coarse:k_zfwd": 116992, "coarse:k_solve": 825920,
-    "fine:k_zinv": 8897690, "fine:k_rows": 56729088, "fine:k_zfwd": 12619776, "fine:k_solve": 23543488,
+    "coarse:k_zinv": 128614, "coarse:k_rows": 487936, "coarse:k_zfwd": 118528, "coarse:k_solve": 827072,
+    "fine:k_zinv": 8896410, "fine:k_rows": 56732211, "fine:k_zfwd": 12641536, "fine:k_solve": 23549248,
 }
 
 
