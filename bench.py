@@ -133,14 +133,15 @@ class Clocks:
 
 # --------------------------------------------------------------------------
 # DRAM bytes (read + write) per launch of the stage kernels: the mean over the
-# four stages of one RK443 step captured with ncu (fine: 32 slices of 256 x 64;
-# coarse: one slice of 128 x 32; the stage-kernel traffic summary in profiles/),
-# valid only while the kernel sources are those that were captured.
+# four stages of one RK443 step captured with ncu (fine: batches of 2 and 32
+# slices of 256 x 64, keyed "kernel@batch"; coarse: one slice of 128 x 32; the
+# stage-kernel traffic summary in profiles/), valid only while the kernel
+# sources are those that were captured.
 NCU_TRAFFIC_SOURCES = ("paper_2001_01609_gb300/csrc/rbc_kernels.cu", "paper_2001_01609_gb300/csrc/rbc_internal.h")
 NCU_TRAFFIC_SHA256 = "45e789e1c2b16906bb6864b32a5bc06883c991f7c7122409c3fb9bfeffc016ed"
 NCU_TRAFFIC = {
     "coarse:k_zinv": 128614, "coarse:k_rows": 487936, "coarse:k_zfwd": 118528, "coarse:k_solve": 827072,
-    "fine:k_zinv": 8896410, "fine:k_rows": 56732211, "fine:k_zfwd": 12641536, "fine:k_solve": 23549248,
+    "fine:k_zinv@32": 8896410, "fine:k_rows@32": 56732211, "fine:k_zfwd@32": 12641536, "fine:k_solve@32": 23549248,
 }
 
 
@@ -445,7 +446,8 @@ def run_gb300(args, w):
     achieved = pk["flops_per"] / (pk["per_ms"] / 1e3) / 1e12
     total_ms = sum(v["ms"] for v in kern.values())
     # the fine kernels are captured at 32 slices; a sampled fine group of another size has no figure
-    traffic = ncu_traffic(dom) if (dom.startswith("coarse:") or kern[dom].get("sampled_batch") == 32) else None
+    # captured per launch at the batch sizes sampled here (coarse: one slice; fine: the first group)
+    traffic = ncu_traffic(dom if dom.startswith("coarse:") else f"{dom}@{kern[dom].get('sampled_batch')}")
     roofline = dict(bound="alu", achieved=achieved, peak=peak_fp64, unit="TFLOP/s", frac=achieved / peak_fp64,
                     traffic=traffic, traffic_source="ncu, one RK443 step, cold cache (profiles/)", kernel=dom, peak_source="derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz",
                     launch_us=1e3 * pk["per_ms"], flops_per_launch=pk["flops_per"],
@@ -468,7 +470,7 @@ def run_gb300(args, w):
                                           "coarse sweep, fine groups and correction sweep overlapped on 3 streams"),
                                 l2="flushed between timed steps (256 MB write)",
                                 autotune={k: dict(heuristic_ms_per_step=v[0], tuned_ms_per_step=v[1],
-                                                  shapes_solve_zfwd_tm_zfwd_nch_rows_cl_rows_threads=list(v[2]))
+                                                  shapes_solve_zfwd_tm_zfwd_nch_rows_cl_rows_threads_rows_lean=list(v[2]))
                                           for k, v in tuned.items()},
                                 parallelism=f"{world} independent problems" if world > 1 else "single GPU"),
                     e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(U0h.numel() * 8),
@@ -740,6 +742,7 @@ def serve(args, name, cfgw, cpu_leg=True, warmup=1):
 NCU_CASES = {
     # name: (Ra, Nx, Nz, dt, B) -- one RK443 step without graphs, for ncu captures
     "fine_b32": (1e6, 256, 64, 1.25e-5, 32),
+    "fine_b2": (1e6, 256, 64, 1.25e-5, 2),       # the first fine group of the Parareal schedule
     "coarse_b1": (1e6, 128, 32, 1.5625e-5, 1),
     "parareal_small": None,   # one Parareal iteration, see run_ncu_case
     "mixed_b8": (1e7, 512, 128, 7.8125e-7, 8),   # RBC_MIXED: tensor-core z transforms

@@ -664,6 +664,18 @@ static rbc_status upload_tables(rbc_t h) {
   add(Pb); add(Pd); add(PDi); add(PL); add(Pi);
   add(Ub); add(Ud); add(UDi); add(UL_); add(Ui);
   add(gram); add(twn); add(Vn); add(Vn1); add(Wn);
+  {
+    // dt * (explicit tableau), then (gamma dt) Pr: the same IEEE products the
+    // stage solve would form per element
+    double ae[5][5], ai[5][5], gm;
+    int ns;
+    scheme_tableau(g.scheme, ae, ai, &ns, &gm);
+    std::vector<double> dtae(26);
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) dtae[i * 5 + j] = g.dt * ae[i][j];
+    dtae[25] = (g.gamma * g.dt) * g.Pr;
+    add(dtae);
+  }
   // FP32 copies of the transform tables, packed two floats per double slot
   auto add_f32 = [&](const std::vector<double>& v) {
     std::vector<double> packed((v.size() + 1) / 2, 0.0);
@@ -717,6 +729,7 @@ static rbc_status upload_tables(rbc_t h) {
   T.Vn = b + offs[i++];
   T.Vn1 = b + offs[i++];
   T.Wn = b + offs[i++];
+  T.dtae = b + offs[i++];
   T.zinv32 = reinterpret_cast<const float*>(b + offs[i++]);
   T.zfwd32 = reinterpret_cast<const float*>(b + offs[i++]);
   T.tw32 = reinterpret_cast<const float2*>(b + offs[i++]);

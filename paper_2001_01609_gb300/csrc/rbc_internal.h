@@ -83,6 +83,9 @@ struct Tables {
   // tensor-core z-forward operands (RBC_MIXED): TF32 hi/lo images of the rows
   // of the forward matrix of each Chebyshev parity, per 128-row tile and K-chunk
   const float *tcW_hi[2], *tcW_lo[2];
+  // [5][5] dt * (explicit tableau entry) and, at [25], (gamma dt) Pr: products
+  // the stage solve would otherwise form per element (same IEEE products, same bits)
+  const double* dtae;
 };
 
 // Error bits a kernel sets for a state (Work::flags) and for the handle (Work::err).

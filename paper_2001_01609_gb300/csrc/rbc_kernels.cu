@@ -827,6 +827,7 @@ struct SolveSmem {
   double* T;    // [nq][W] T_i, kept for the psi coupling; the dense path's solution of each system
   int W;        // columns = 2 * tms
   double Ra;    // Rayleigh number of this slice
+  double cpl;   // ((gamma dt) Pr) Ra of this slice
 };
 
 template <int KIND>
@@ -869,8 +870,7 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
   for (int j = 0; j <= SY::LAM; ++j)
     if (t + j < nq) fv = fma(SY::tapF(g, tb, p, t, j), sm.F[soff(g, f, 2 * (t + j) + p, m) + c], fv);
   if (KIND != KP) fv = -fv;
-  const double dt = g.dt;
-  const int sc = g.scheme, ns = g.ns;
+  const int ns = g.ns;
   const size_t ro = soff(g, f, 2 * t + p, m) + c;
   double r;
   if (stage == 1) {
@@ -878,19 +878,20 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
 #pragma unroll
     for (int j = 0; j <= SY::LAM; ++j)
       if (t + j < nq) mx = fma(SY::tapM(g, tb, p, t, j, m), sm.X[soff(g, f, 2 * (t + j) + p, m) + c], mx);
-    r = fma(dt * c_AE[sc][1][0], fv, mx);
+    r = fma(__ldg(tb.dtae + 5), fv, mx);
 #pragma unroll
     for (int l = 2; l <= 4; ++l)
-      if (l <= ns) R[(size_t)(l - 1) * S + ro] = fma(dt * c_AE[sc][l][0], fv, mx);
+      if (l <= ns) R[(size_t)(l - 1) * S + ro] = fma(__ldg(tb.dtae + l * 5), fv, mx);
   } else {
     double Rl[3];
     const double Ri = *(R + (size_t)(stage - 1) * S + ro);
 #pragma unroll
     for (int l = 0; l < 3; ++l) Rl[l] = (l + 2 > stage && l + 2 <= ns) ? *(R + (size_t)(l + 1) * S + ro) : 0.0;
-    r = fma(dt * c_AE[sc][stage][stage - 1], fv, Ri);
+    r = fma(__ldg(tb.dtae + stage * 5 + stage - 1), fv, Ri);
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      if (l + 2 > stage && l + 2 <= ns) R[(size_t)(l + 1) * S + ro] = fma(dt * c_AE[sc][l + 2][stage - 1], fv, Rl[l]);
+      if (l + 2 > stage && l + 2 <= ns)
+        R[(size_t)(l + 1) * S + ro] = fma(__ldg(tb.dtae + (l + 2) * 5 + stage - 1), fv, Rl[l]);
   }
   sm.r[t * W + col] = r;
   double bv = r;
@@ -900,7 +901,9 @@ __device__ __forceinline__ void solve_rhs(const Grid& g, const Tables& tb, int s
 #pragma unroll
     for (int j = 0; j <= 4; ++j)
       if (t + j < nq) st = fma(__ldg(tb.s4 + (p * nq + t) * 5 + j), sm.T[(t + j) * W + (col ^ 1)], st);
-    const double cpl = (c == 0 ? 1.0 : -1.0) * g.gamma * dt * g.Pr * sm.Ra * (g.kfac * m);
+    // (+-1) gamma dt Pr Ra k with the roundings of that left-to-right product:
+    // the sign is exact, so it may come last
+    const double cpl = (c == 0 ? sm.cpl : -sm.cpl) * (g.kfac * m);
     bv = fma(cpl, st, bv);
   }
   sm.y[(t + SY::D) * W + col] = bv;
@@ -1061,6 +1064,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
   SolveSmem sm;
   sm.W = W;
   sm.Ra = ra ? ra[b] : g.Ra;
+  sm.cpl = __ldg(tb.dtae + 25) * sm.Ra;
   sm.y = sbuf;
   sm.r = sm.y + (size_t)nq * W;
   sm.T = sm.r + (size_t)nq * W;
