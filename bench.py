@@ -138,10 +138,13 @@ class Clocks:
 # stage-kernel traffic summary in profiles/), valid only while the kernel
 # sources are those that were captured.
 NCU_TRAFFIC_SOURCES = ("paper_2001_01609_gb300/csrc/rbc_kernels.cu", "paper_2001_01609_gb300/csrc/rbc_internal.h")
-NCU_TRAFFIC_SHA256 = "45e789e1c2b16906bb6864b32a5bc06883c991f7c7122409c3fb9bfeffc016ed"
+NCU_TRAFFIC_SHA256 = "22b7118df697d4eb8482d503576339da0007e76283fa4a4b32a86554cb01b44e"
 NCU_TRAFFIC = {
-    "coarse:k_zinv": 128614, "coarse:k_rows": 487936, "coarse:k_zfwd": 118528, "coarse:k_solve": 827072,
-    "fine:k_zinv@32": 8896410, "fine:k_rows@32": 56732211, "fine:k_zfwd@32": 12641536, "fine:k_solve@32": 23549248,
+    "coarse:k_zinv": 128666, "coarse:k_rows": 488141, "coarse:k_zfwd": 117248, "coarse:k_solve": 827136,
+    "fine:k_zinv@32": 8884736, "fine:k_rows@32": 56719514, "fine:k_zfwd@32": 12618752, "fine:k_solve@32": 23538624,
+    # batch of 2 with the heuristic shapes (the clustered row kernel; the tuned one-block-per-row
+    # kernel reads and writes the same rows)
+    "fine:k_zinv@2": 661094, "fine:k_rows@2": 3587942, "fine:k_zfwd@2": 821376, "fine:k_solve@2": 2443456,
 }
 
 
@@ -868,7 +871,9 @@ def run_config3_study():
     the transient on 128 x 64, which survives it (t = 0.004, reading R24), is
     prolonged to 1024 x 256; then mixed-precision Parareal to the 1% Nu
     criterion against the serial all-FP64 fine run on the same GPU, over 40
-    fine steps of 7.8125e-8 per slice (coarse 256 x 64, 20 steps of 1.5625e-7)."""
+    fine steps of 7.8125e-8 per slice (coarse 256 x 64, 20 steps of 1.5625e-7):
+    TF32 or BF16 fine operands with the RK443 coarse propagator, and BF16 with
+    the ARS(2,2,2) coarse propagator."""
     import torch
     from paper_2001_01609_gb300 import build
     build.build()
@@ -910,23 +915,34 @@ def run_config3_study():
     ts, _ = timed(serial)
     st_s = F64.check_diverged()
     nu_serial = float(nus[N // 2:].sum().item()) / (T / 2)
-    P = rbc.Parareal(F, G, 0.0, T, N, rbc.CRIT_NU, 0.01)
-    P.set_depth(1)
-    P.set_schedule(32, 8, 2, 1, 32)
-    for Bg in (8, 16, 32):
-        F.autotune(Bg)
-    G.autotune(1)
-    U = F.new_states(N + 1)
-    P.iterate(U0[0], U, 1)
-    tp, (st, k, de, nu) = timed(lambda: P.iterate(U0[0], U, 5))
+    arms = {}
+    # TF32 fine operands with the RK443 coarse propagator; BF16 fine operands with it; BF16 with
+    # the ARS(2,2,2) coarse propagator at the same coarse step (unstable there: it reports
+    # RBC_EDIVERGED in the first coarse sweep)
+    F16 = rbc.Propagator(Ra, 1.0, 2.0, 1024, 256, dtf, precision=rbc.RBC_MIXED_BF16)
+    for name, Fa, Ga in (("parareal_mixed", F, G),
+                         ("parareal_mixed_bf16", F16, G),
+                         ("parareal_mixed_bf16_rk222_coarse", F16,
+                          rbc.Propagator(Ra, 1.0, 2.0, 256, 64, dtc, precision=rbc.RBC_MIXED,
+                                         scheme=rbc.RBC_RK222))):
+        P = rbc.Parareal(Fa, Ga, 0.0, T, N, rbc.CRIT_NU, 0.01)
+        P.set_depth(1)
+        P.set_schedule(32, 8, 2, 1, 32)
+        for Bg in (8, 16, 32):
+            Fa.autotune(Bg)
+        Ga.autotune(1)
+        U = Fa.new_states(N + 1)
+        P.iterate(U0[0], U, 1)
+        tp, (st, k, de, nu) = timed(lambda: P.iterate(U0[0], U, 5))
+        nu_k = float(nu[-1]) if len(nu) else float("nan")
+        arms[name] = dict(s=tp, status=st, iterations=k, defects=list(map(float, de)), nus=list(map(float, nu)),
+                          speedup=ts / tp, nu_rel_err=abs(nu_k - nu_serial) / abs(nu_serial))
+        P.close()
+        del U
     print(json.dumps(dict(study="config3", Ra=Ra, grid="1024x256", coarse_grid="256x64", slices=N,
                           fine_steps_per_slice=nf, dt=dtf, coarse_steps_per_slice=nc, dt_coarse=dtc,
                           start="128x64 transient to t = 0.004 (25600 steps of 1.5625e-7), prolonged",
-                          serial_fp64=dict(s=ts, status=st_s, nu=nu_serial),
-                          parareal_mixed=dict(s=tp, status=st, iterations=k, defects=list(map(float, de)),
-                                              nus=list(map(float, nu)), speedup=ts / tp,
-                                              nu_rel_err=abs(float(nu[-1]) - nu_serial) / abs(nu_serial)))),
-          flush=True)
+                          serial_fp64=dict(s=ts, status=st_s, nu=nu_serial), **arms)), flush=True)
 
 
 COARSE_NC = (625, 1000, 1250, 1600, 2000, 2500, 3125, 4000, 5000, 6250, 8000, 10000, 12500)
