@@ -1074,16 +1074,23 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
   sm.F = Fb;
   sm.X = X0;
   double* Rb = R + (size_t)b * 4 * S;
-  if (stage == 1 && m0 == 0 && p == 1 && threadIdx.x == 0 && nu != nullptr) {
+  if (stage == 1 && m0 == 0 && p == 1 && threadIdx.x < 32 && nu != nullptr) {
     // Nu_V(t_n) (Eq. 9) of the step-start state: wall temperature difference of
     // the mean profile + Clenshaw-Curtis integral of <wT>_x; trapezoid weight.
-    // The odd coefficients read here belong to this block, which overwrites
-    // them only after the barriers below (a one-stage scheme writes X0 here).
-    double cond = 0.0;
-    for (int n = 1; n < g.Nz; n += 2) cond -= 2.0 * *(X0 + soff(g, 0, n, 0));
-    double adv = 0.0;
-    for (int jz = 0; jz < g.Mz; ++jz) adv = fma(__ldg(tb.cc + jz), *(wT + (size_t)b * g.Mz + jz), adv);
-    nu[b] += ((stepidx == 0) ? 0.5 : 1.0) * g.dt * (cond + 0.5 * adv);
+    // The first warp sums it: each lane a strided share of both sums, then a
+    // fixed shuffle tree (the order depends on the grid only). The odd
+    // coefficients read here belong to this block, which overwrites them only
+    // after the barriers below (a one-stage scheme writes X0 here).
+    const int lane = threadIdx.x;
+    double cond = 0.0, adv = 0.0;
+    for (int n = 2 * lane + 1; n < g.Nz; n += 64) cond -= 2.0 * *(X0 + soff(g, 0, n, 0));
+    for (int jz = lane; jz < g.Mz; jz += 32) adv = fma(__ldg(tb.cc + jz), *(wT + (size_t)b * g.Mz + jz), adv);
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      cond += __shfl_down_sync(0xffffffffu, cond, sh);
+      adv += __shfl_down_sync(0xffffffffu, adv, sh);
+    }
+    if (lane == 0) nu[b] += ((stepidx == 0) ? 0.5 : 1.0) * g.dt * (cond + 0.5 * adv);
   }
   bool ok = true;
   for (int sys = 0; sys < 2; ++sys) {
