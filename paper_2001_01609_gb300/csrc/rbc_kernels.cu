@@ -449,23 +449,30 @@ __device__ __forceinline__ C2<T> rows_packed(const Grid& g, const T* zrow, size_
   return c;
 }
 
-// block_sum over the first 256 threads (the others pass nothing and only meet
-// the barriers): the tree of block_sum at 256 threads, whatever blockDim is.
-__device__ double block_sum256(double v, double* red) {
-  if (threadIdx.x < 256) red[threadIdx.x] = v;
+// Two block sums over the first 256 threads at once (the others pass nothing
+// and only meet the barriers): for each value the tree of block_sum at 256
+// threads, whatever blockDim is, with half the barriers of two calls.
+__device__ double2 block_sum256_2(double a, double b, double2* red) {
+  if (threadIdx.x < 256) red[threadIdx.x] = make_double2(a, b);
   __syncthreads();
   for (int s = 128; s >= 32; s >>= 1) {
-    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    if ((int)threadIdx.x < s) {
+      const double2 u = red[threadIdx.x], v = red[threadIdx.x + s];
+      red[threadIdx.x] = make_double2(u.x + v.x, u.y + v.y);
+    }
     __syncthreads();
   }
   if (threadIdx.x < 32) {
-    double x = red[threadIdx.x];
+    double x = red[threadIdx.x].x, y = red[threadIdx.x].y;
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
-    if (threadIdx.x == 0) red[0] = x;
+    for (int s = 16; s > 0; s >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, s);
+      y += __shfl_down_sync(0xffffffffu, y, s);
+    }
+    if (threadIdx.x == 0) red[0] = make_double2(x, y);
   }
   __syncthreads();
-  const double r = red[0];
+  const double2 r = red[0];
   __syncthreads();
   return r;
 }
@@ -492,7 +499,7 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
   const int b = blk / g.Mz, j = blk - b * g.Mz;
   if (b >= B || !slice_active_at(nsteps, stepidx, b)) return;
   const int Mx = g.Mx, nm = g.nm;
-  __shared__ double red[256];
+  __shared__ double2 red[256];
   const size_t fs = (size_t)g.Mz * nm * 2;
   const T* zrow = Z + (size_t)b * 9 * fs + (size_t)j * nm * 2;
   const V* fld;      // field value at x: real/imag parts of the five packed rows
@@ -578,8 +585,8 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
       nU += (double)vU[x];
       wt += (double)vW[x];
     }
-  const double sU = block_sum256(nU, red);
-  const double sW = block_sum256(wt, red);
+  const double2 sUW = block_sum256_2(nU, wt, red);
+  const double sU = sUW.x, sW = sUW.y;
   const V* C = fft_smem<T>(P, P2, Mx, 1, -1, tws);
   const T inv = (T)1 / (T)Mx;
   const T half = (T)0.5 * inv;
@@ -637,7 +644,7 @@ __global__ void __cluster_dims__(kRowsCluster, 1, 1) __launch_bounds__(kRowsThre
   using V = C2<T>;
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char csm[];
-  __shared__ double red[kRowsThreads];
+  __shared__ double2 red[kRowsThreads];
   pdl_wait();
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
@@ -690,8 +697,8 @@ __global__ void __cluster_dims__(kRowsCluster, 1, 1) __launch_bounds__(kRowsThre
     nU += vU[x];
     wt += vW[x];
   }
-  const double sU = block_sum(nU, red);
-  const double sW = block_sum(wt, red);
+  const double2 sUW = block_sum256_2(nU, wt, red);   // kRowsThreads = 256: the same tree
+  const double sU = sUW.x, sW = sUW.y;
   const V* C = fft_smem<T>(P, P2, Mx, 1, -1, tws);
   const T inv = (T)1 / (T)Mx;
   const T half = (T)0.5 * inv;
