@@ -138,13 +138,13 @@ class Clocks:
 # stage-kernel traffic summary in profiles/), valid only while the kernel
 # sources are those that were captured.
 NCU_TRAFFIC_SOURCES = ("paper_2001_01609_gb300/csrc/rbc_kernels.cu", "paper_2001_01609_gb300/csrc/rbc_internal.h")
-NCU_TRAFFIC_SHA256 = "22b7118df697d4eb8482d503576339da0007e76283fa4a4b32a86554cb01b44e"
+NCU_TRAFFIC_SHA256 = "97c5c4329ec732c39e3b62da320babffb365b0fc5e5ac125717337623e176ce7"
 NCU_TRAFFIC = {
-    "coarse:k_zinv": 128666, "coarse:k_rows": 488141, "coarse:k_zfwd": 117248, "coarse:k_solve": 827136,
-    "fine:k_zinv@32": 8884736, "fine:k_rows@32": 56719514, "fine:k_zfwd@32": 12618752, "fine:k_solve@32": 23538624,
+    "coarse:k_zinv": 131891, "coarse:k_rows": 488602, "coarse:k_zfwd": 117440, "coarse:k_solve": 826944,
+    "fine:k_zinv@32": 8915251, "fine:k_rows@32": 56740045, "fine:k_zfwd@32": 12618176, "fine:k_solve@32": 23538944,
     # batch of 2 with the heuristic shapes (the clustered row kernel; the tuned one-block-per-row
     # kernel reads and writes the same rows)
-    "fine:k_zinv@2": 661094, "fine:k_rows@2": 3587942, "fine:k_zfwd@2": 821376, "fine:k_solve@2": 2443456,
+    "fine:k_zinv@2": 661760, "fine:k_rows@2": 3589069, "fine:k_zfwd@2": 822656, "fine:k_solve@2": 2442240,
 }
 
 
