@@ -1011,6 +1011,68 @@ def run_coarse_scheme_study():
           flush=True)
 
 
+def run_config2_study():
+    """Config 2 (Ra 1e7, 512 x 128, 64 slices, mixed precision): Parareal from the
+    seeded IC (the ladder's fine step 7.8125e-7; 100 fine steps per slice, through
+    the initial plume burst) with a 256 x 64 coarse propagator (CF 2, twice the
+    fine step, 50 steps per slice), to the 1% Nu criterion, against the serial
+    all-FP64 fine run on the same GPU; TF32 and BF16 fine operands."""
+    import torch
+    from paper_2001_01609_gb300 import build
+    build.build()
+    from paper_2001_01609_gb300 import rbc
+    from paper_2001_01609_gb300.inputs import initial_temperature
+    Ra, N, nf, nc, dtf = 1e7, 64, 100, 50, 7.8125e-7
+    dtc = nf * dtf / nc
+    T = N * nf * dtf
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, r
+
+    F64 = rbc.Propagator(Ra, 1.0, 2.0, 512, 128, dtf)
+    U0 = F64.new_states(1)
+    F64.set_state(U0[0], initial_temperature(512, 128, seed=2))
+    warm = U0.clone()
+    F64.step_batch(warm, 3)
+    ser = U0.clone()
+    nus = torch.zeros(N, dtype=torch.float64, device="cuda")
+
+    def serial():
+        for n in range(N):
+            F64.step_batch(ser, nf, nus[n:n + 1])
+    ts, _ = timed(serial)
+    st_s = F64.check_diverged()
+    nu_serial = float(nus[N // 2:].sum().item()) / (T / 2)
+    arms = {}
+    for name, prec in (("parareal_mixed", rbc.RBC_MIXED), ("parareal_mixed_bf16", rbc.RBC_MIXED_BF16)):
+        F = rbc.Propagator(Ra, 1.0, 2.0, 512, 128, dtf, precision=prec)
+        G = rbc.Propagator(Ra, 1.0, 2.0, 256, 64, dtc, precision=rbc.RBC_MIXED)
+        P = rbc.Parareal(F, G, 0.0, T, N, rbc.CRIT_NU, 0.01)
+        P.set_depth(1)
+        P.set_schedule(16, 4, 2, 1, 32)
+        for Bg in (4, 8, 16):
+            F.autotune(Bg)
+        G.autotune(1)
+        U = F.new_states(N + 1)
+        P.iterate(U0[0], U, 1)
+        tp, (st, k, de, nu) = timed(lambda: P.iterate(U0[0], U, 6))
+        nu_k = float(nu[-1]) if len(nu) else float("nan")
+        arms[name] = dict(s=tp, status=st, iterations=k, defects=list(map(float, de)), nus=list(map(float, nu)),
+                          speedup=ts / tp, nu_rel_err=abs(nu_k - nu_serial) / abs(nu_serial))
+        P.close()
+        del U, F, G
+    print(json.dumps(dict(study="config2", Ra=Ra, grid="512x128", coarse_grid="256x64", slices=N,
+                          fine_steps_per_slice=nf, dt=dtf, coarse_steps_per_slice=nc, dt_coarse=dtc,
+                          start="seeded IC (config 2)", serial_fp64=dict(s=ts, status=st_s, nu=nu_serial), **arms)),
+          flush=True)
+
+
 def run_ncu_case(name):
     """A small, self-ending case for ncu: one plain (graph-free) RK443 step of a
     batch, or one short Parareal iteration on the bench's grids."""
@@ -1067,7 +1129,7 @@ def main():
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the Parareal-to-tolerance runs")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg of the default line")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), help="run one small step for an ncu capture")
-    ap.add_argument("--study", choices=["coarsening", "statistics", "config3", "coarse_schemes"],
+    ap.add_argument("--study", choices=["coarsening", "statistics", "config2", "config3", "coarse_schemes"],
                     help="the coarsening and slice-count study, or the statistical Parareal run (not bench lines)")
     ap.add_argument("--study-coarse", default="",
                     help="coarse propagators of the coarsening study, e.g. 32x8:3.125e-5,64x16:1.5625e-5")
@@ -1084,6 +1146,9 @@ def main():
         return
     if args.study == "statistics":
         run_statistics_study()
+        return
+    if args.study == "config2":
+        run_config2_study()
         return
     if args.study == "config3":
         run_config3_study()
