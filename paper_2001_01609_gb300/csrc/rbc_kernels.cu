@@ -1066,7 +1066,8 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
   // the state as it was at the start of the failing step
   if (flags[b] & kFlagTimeout) return;
   const int nq = g.nq;
-  const int W = 2 * tms;
+  const int W = 2 * tms;                         // a power of two (tms is)
+  const int lw = __ffs(W) - 1;
   const int ncol = 2 * min(tms, g.nm - m0);
   SolveSmem sm;
   sm.W = W;
@@ -1105,7 +1106,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
     // phase 1
     const int ntmax = nq - 1;
     for (int it = threadIdx.x; it < ntmax * W; it += blockDim.x) {
-      const int t = it / W, col = it - t * W;
+      const int t = it >> lw, col = it & (W - 1);
       if (col >= ncol) continue;
       const int m = m0 + col / 2, c = col & 1;
       if (sys == 0)
@@ -1121,7 +1122,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
       // boundary rows of b: the mean temperature's wall values (Eq. 6) or
       // slopes (Eq. 7) in parity combinations; zero for T at m >= 1, psi and U
       for (int it = threadIdx.x; it < 2 * W; it += blockDim.x) {
-        const int r = it / W, col = it - r * W;
+        const int r = it >> lw, col = it & (W - 1);
         if (col >= ncol) continue;
         const int m = m0 + col / 2, c = col & 1;
         const int D = (sys == 1 && m != 0) ? 2 : 1;
@@ -1130,7 +1131,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
       }
       __syncthreads();
       for (int it = threadIdx.x; it < nq * W; it += blockDim.x) {
-        const int r = it / W, col = it - r * W;
+        const int r = it >> lw, col = it & (W - 1);
         if (col >= ncol) continue;
         const int m = m0 + col / 2, c = col & 1;
         bool o2;
@@ -1161,7 +1162,7 @@ __device__ void solve_item(const Grid& g, const Tables& tb, double* X, double* X
     // phase 4
     if (stage < g.ns) {
       for (int it = threadIdx.x; it < ntmax * W; it += blockDim.x) {
-        const int t = it / W, col = it - t * W;
+        const int t = it >> lw, col = it & (W - 1);
         if (col >= ncol) continue;
         const int m = m0 + col / 2, c = col & 1;
         if (sys == 0)
