@@ -342,7 +342,7 @@ __device__ C2<T>* fft_smem(C2<T>* a, C2<T>* b, int N, int na, int sign, const C2
     const int nb = N / R;
     const int stride = N / (Ns * R);
     for (int it = threadIdx.x; it < na * nb; it += blockDim.x) {
-      const int arr = it / nb, jj = it - arr * nb;
+      const int arr = na == 1 ? 0 : it / nb, jj = it - arr * nb;   // one array: no division
       const V* xa = x + arr * N;
       V* ya = y + arr * N;
       const int k = jj & (Ns - 1);                  // Ns is a power of two (the radix-3 pass is last)
