@@ -519,10 +519,8 @@ __device__ void rows_item(const Grid& g, const C2<T>* __restrict__ tw, const T* 
     Bf = A + 5 * Mx;
     tws = Bf + (lean ? 3 : 5) * Mx;
     for (int x = threadIdx.x; x < Mx; x += blockDim.x) tws[x] = ldgc<T>(tw + x);
-    for (int it = threadIdx.x; it < 5 * Mx; it += blockDim.x) {
-      const int pr = it / Mx, x = it - pr * Mx;
-      A[it] = rows_packed<T>(g, zrow, fs, pr, x);
-    }
+    for (int pr = 0; pr < 5; ++pr)
+      for (int x = threadIdx.x; x < Mx; x += blockDim.x) A[pr * Mx + x] = rows_packed<T>(g, zrow, fs, pr, x);
     __syncthreads();
     if (!lean) {
       fld = fft_smem<T>(A, Bf, Mx, 5, +1, tws);
@@ -744,8 +742,9 @@ __device__ void zfwd_item(const Grid& g, const T* __restrict__ W, const T* __res
   if (b >= B || !slice_active_at(nsteps, stepidx, b)) return;
   const size_t qs = (size_t)g.Mz * g.nm * 2;
   const T* q = Q + (size_t)(b * 2 + f) * qs;
+  const int ltm = __ffs(tm) - 1;             // tm is a power of two
   for (int it = threadIdx.x; it < Mh * tm; it += blockDim.x) {
-    const int jh = it / tm, mi = it - jh * tm, m = m0 + mi;
+    const int jh = it >> ltm, mi = it & (tm - 1), m = m0 + mi;
     V ev = mk2<T>(0, 0), od = mk2<T>(0, 0);
     if (m < g.nm) {
       const V a = ldc<T>(q + ((size_t)jh * g.nm + m) * 2);
