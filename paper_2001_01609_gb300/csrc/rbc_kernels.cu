@@ -332,15 +332,16 @@ __device__ C2<T>* fft_smem(C2<T>* a, C2<T>* b, int N, int na, int sign, const C2
   int p = 0;
   for (int M = N / 3; M > 1; M >>= 1) ++p;
   const int nr = p / 2 + (p & 1) + 1;
-  int Ns = 1;
+  int Ns = 1, lns = 0;                                 // Ns = 2^lns
   V* x = a;
   V* y = b;
   const T s3 = (T)0.86602540378443864676 * (T)sign;   // sign * sqrt(3)/2
   const T sg = (T)sign;
   for (int pass = 0; pass < nr; ++pass) {
     const int R = (pass < p / 2) ? 4 : ((p & 1) && pass == p / 2) ? 2 : 3;
-    const int nb = N / R;
-    const int stride = N / (Ns * R);
+    // N = 3 2^p: N / R and N / (Ns R) by shifts (the radix-3 pass leaves 2^p)
+    const int nb = R == 4 ? N >> 2 : R == 2 ? N >> 1 : 1 << p;
+    const int stride = nb >> lns;
     for (int it = threadIdx.x; it < na * nb; it += blockDim.x) {
       const int arr = na == 1 ? 0 : it / nb, jj = it - arr * nb;   // one array: no division
       const V* xa = x + arr * N;
@@ -383,6 +384,7 @@ __device__ C2<T>* fft_smem(C2<T>* a, C2<T>* b, int N, int na, int sign, const C2
     x = y;
     y = tmp;
     Ns *= R;
+    lns += R == 4 ? 2 : R == 2 ? 1 : 0;                // the radix-3 pass is the last
   }
   return x;
 }
