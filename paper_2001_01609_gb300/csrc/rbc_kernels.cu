@@ -763,8 +763,8 @@ __device__ void zfwd_item(const Grid& g, const T* __restrict__ W, const T* __res
     fold[(size_t)(Mh + jh) * tm + mi] = od;
   }
   __syncthreads();
-  const int ng = blockDim.x / tm;
-  const int mi = threadIdx.x % tm, n0 = threadIdx.x / tm;
+  const int ng = blockDim.x >> ltm;
+  const int mi = threadIdx.x & (tm - 1), n0 = threadIdx.x >> ltm;
   const int m = m0 + mi;
   if (m >= g.nm) return;
   const int nper = (g.Nz + nch - 1) / nch;
