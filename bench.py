@@ -138,13 +138,13 @@ class Clocks:
 # stage-kernel traffic summary in profiles/), valid only while the kernel
 # sources are those that were captured.
 NCU_TRAFFIC_SOURCES = ("paper_2001_01609_gb300/csrc/rbc_kernels.cu", "paper_2001_01609_gb300/csrc/rbc_internal.h")
-NCU_TRAFFIC_SHA256 = "97c5c4329ec732c39e3b62da320babffb365b0fc5e5ac125717337623e176ce7"
+NCU_TRAFFIC_SHA256 = "bccf5326cefa87d23c30c873735b605116d20294072d2c0e5a25ffdcbd076c31"
 NCU_TRAFFIC = {
-    "coarse:k_zinv": 131891, "coarse:k_rows": 488602, "coarse:k_zfwd": 117440, "coarse:k_solve": 826944,
-    "fine:k_zinv@32": 8915251, "fine:k_rows@32": 56740045, "fine:k_zfwd@32": 12618176, "fine:k_solve@32": 23538944,
+    "coarse:k_zinv": 130202, "coarse:k_rows": 483123, "coarse:k_zfwd": 116864, "coarse:k_solve": 826752,
+    "fine:k_zinv@32": 8907264, "fine:k_rows@32": 56720845, "fine:k_zfwd@32": 12620800, "fine:k_solve@32": 23538240,
     # batch of 2 with the heuristic shapes (the clustered row kernel; the tuned one-block-per-row
     # kernel reads and writes the same rows)
-    "fine:k_zinv@2": 661760, "fine:k_rows@2": 3589069, "fine:k_zfwd@2": 822656, "fine:k_solve@2": 2442240,
+    "fine:k_zinv@2": 661350, "fine:k_rows@2": 3586304, "fine:k_zfwd@2": 821824, "fine:k_solve@2": 2441088,
 }
 
 
