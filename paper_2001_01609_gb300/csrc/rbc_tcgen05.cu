@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kTcThreads) k_zinv_tc(Grid g, const float* __r
   const float* Alo = (fsel == 0 ? Alo_psi : Alo_T) + (size_t)t0 * kc * kChunkFloats;
   constexpr uint32_t kChunkBytes = kChunkFloats * 4;   // one image chunk, 16 KB
   const bool bf = g.tcbf16 != 0;
-  const int ke = tc_ke(g), es = 128 / ke;
+  const int ke = tc_ke(g), es = 128 / ke, lke = bf ? 6 : 5;   // ke = 2^lke
   unsigned char* sXhi = base;
   unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
   unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [stage][hi, lo][128 x 128 B]
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kTcThreads) k_zinv_tc(Grid g, const float* __r
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const uint32_t o = (uint32_t)(n / ke) * kTileN * 128 + swz_b(col + e, (n % ke) * es);
+      const uint32_t o = (uint32_t)(n >> lke) * kTileN * 128 + swz_b(col + e, (n & (ke - 1)) * es);
       store_split(bf, (float)v[e], sXhi, sXlo, o);
     }
   }
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(kTcThreads) k_zfwd_tc(Grid g, const float* __r
   const float* Alo = (p == 0 ? Wlo0 : Wlo1) + (size_t)t * kc * kChunkFloats;
   constexpr uint32_t kChunkBytes = kChunkFloats * 4;
   const bool bf = g.tcbf16 != 0;
-  const int ke = tc_ke(g), es = 128 / ke;
+  const int ke = tc_ke(g), es = 128 / ke, lke = bf ? 6 : 5;   // ke = 2^lke
   unsigned char* sXhi = base;
   unsigned char* sXlo = sXhi + (size_t)kc * kTileN * 128;
   unsigned char* sA = sXlo + (size_t)kc * kTileN * 128;   // [stage][hi, lo][128 x 128 B]
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(kTcThreads) k_zfwd_tc(Grid g, const float* __r
     for (int e = 0; e < 4; ++e) {
       float x = 0.f;
       if (jh < Mh && c0 + col + e < 2 * g.nm) x = (jr != jh) ? (p == 0 ? a[e] + c[e] : a[e] - c[e]) : (p == 0 ? a[e] : 0.f);
-      const uint32_t o = (uint32_t)(jh / ke) * kTileN * 128 + swz_b(col + e, (jh % ke) * es);
+      const uint32_t o = (uint32_t)(jh >> lke) * kTileN * 128 + swz_b(col + e, (jh & (ke - 1)) * es);
       store_split(bf, x, sXhi, sXlo, o);
     }
   }
