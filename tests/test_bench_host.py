@@ -48,3 +48,12 @@ def test_study_slices_are_whole_steps():
         for _, _, dtc in s["coarse"]:
             q = T / N / dtc
             assert abs(q - round(q)) < 1e-9 * q
+
+
+def test_traffic_is_keyed_by_the_sampled_batch():
+    # the recorded sources are the committed ones, and every fine entry names its batch
+    assert bench.ncu_traffic("coarse:k_solve") == bench.NCU_TRAFFIC["coarse:k_solve"]
+    for k in bench.NCU_TRAFFIC:
+        assert k.startswith("coarse:") or "@" in k, k
+    assert bench.ncu_traffic("fine:k_rows@2") == bench.NCU_TRAFFIC["fine:k_rows@2"]
+    assert bench.ncu_traffic("fine:k_rows@7") is None
